@@ -1,0 +1,342 @@
+"""Benchmark of the PPPM k-space path on GB300.
+
+One step = one full pass of the k-space path (particle_map + sort, make_rho,
+forward FFT, influence-function multiply with energy/virial, inverse FFTs,
+fieldforce) over the water-like workload: 10,667 rigid 3-site molecules
+(32,001 charges) in a 68 A periodic cube, mesh 64^3, order 5, ik
+differentiation, FP32 spreading/FFT/interpolation with compensated mesh
+accumulation.  Inputs are resident in HBM; the L2 is flushed (256 MiB write)
+before every timed step and each step is timed with CUDA events on the plan's
+stream.  The step runs as one captured CUDA graph.
+
+Also reported on the same line: Mparticles/s, the force error of this FP32C
+form against the FP64 form (same GPU, same inputs), the dominant kernel's
+roofline fraction, the end-to-end rate through the host-buffer C-ABI call,
+the FP64 oracle timed on the host cores, and the same metric for ad / FP64.
+
+--impl reference times the FP64 CPU oracle on the same workload instead.
+Multi-GPU: the path does not shard (one system); N ranks run N independent
+replicas and report the summed throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20
+WORKLOAD = "c2"
+
+
+def workload():
+    from paper_1702_04250_gb300.workloads import config
+
+    return config(WORKLOAD)
+
+
+def metric_name():
+    return "PPPM k-space steps/sec at 1e-4 rel force error vs FP64 form (water-like 32,001 charges, 64^3, P=5, ik, FP32C)"
+
+
+def config_dict(w, extra=None):
+    d = {"workload": "c2 water-like: 10,667 rigid 3-site molecules (32,001 charges), 68 A cube, mesh 64^3, "
+                     "order 5, ik, g_ewald for 1e-4 at r_C = 10 A",
+         "n_charges": int(w.n), "mesh": list(w.mesh), "order": int(w.order), "diff": "ik", "precision": "fp32c",
+         "l2": "flushed (256 MiB write) before every timed step", "graph": True}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([s.strip() for s in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_plan(w, g, mode, prec, graph=True):
+    from paper_1702_04250_gb300 import pppm
+
+    return pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode=mode, precision=prec, qqrd2e=w.qqrd2e, graph=graph)
+
+
+def time_steps(torch, plan, x, q, f, ev, steps, warmup, flush, profile=False):
+    """Returns (total device ms over the timed steps, per-stage ms sums)."""
+    s = plan.stream
+    stage_sum = {k: 0.0 for k in plan.STAGES}
+    plan.set_profiling(profile)
+    for _ in range(warmup):
+        flush.zero_()
+        plan.compute(x, q, f, ev)
+    torch.cuda.synchronize()
+    total = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        with torch.cuda.stream(s):
+            flush.zero_()
+        e0.record(s)
+        plan.compute(x, q, f, ev)
+        e1.record(s)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+        if profile:
+            for k, v in plan.stage_times().items():
+                stage_sum[k] += v
+    plan.set_profiling(False)
+    return total, stage_sum
+
+
+def gpu_arm(args, rank, world):
+    import torch
+
+    from paper_1702_04250_gb300 import build, pppm
+
+    build.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w = workload()
+    q2 = float(np.sum(w.q ** 2))
+    g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, q2, w.box)
+    x32 = torch.tensor(w.x, dtype=torch.float32, device="cuda")
+    q32 = torch.tensor(w.q, dtype=torch.float32, device="cuda")
+    x64 = torch.tensor(w.x, dtype=torch.float64, device="cuda")
+    q64 = torch.tensor(w.q, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    plan = make_plan(w, g, "ik", "fp32c")
+    f = torch.empty((w.n, 3), dtype=torch.float32, device="cuda")
+    ev = torch.zeros(8, dtype=torch.float64, device="cuda")
+    plan.compute(x32, q32, f, ev)
+    plan.sync()
+
+    # accuracy of this form against the FP64 form on the same GPU and inputs
+    p64 = make_plan(w, g, "ik", "fp64", graph=False)
+    f64, ev64 = p64.compute(x32.double(), q32.double())
+    p64.sync()
+    f64n = f64.cpu().numpy()
+    rel_err = math.sqrt(float(np.sum((f.double().cpu().numpy() - f64n) ** 2) / np.sum(f64n ** 2)))
+    e_err = abs(ev[0].item() - ev64[0].item()) / abs(ev64[0].item())
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t_ms, stages = time_steps(torch, plan, x32, q32, f, ev, args.steps, args.warmup, flush, profile=True)
+    clocks_rep = clocks.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = tt.item()
+    ms_per_step = t_ms / args.steps
+    steps_per_s = world * 1000.0 / ms_per_step
+
+    # the same timing without stage events (reported: overhead of profiling)
+    t_plain, _ = time_steps(torch, plan, x32, q32, f, ev, max(20, args.steps // 2), 3, flush, profile=False)
+    ms_plain = t_plain / max(20, args.steps // 2)
+
+    # roofline of the dominant hand-written kernel
+    stage_ms = {k: v / args.steps for k, v in stages.items()}
+    own = {k: stage_ms[k] for k in ("sort", "make_rho", "green", "fieldforce")}
+    dom = max(own, key=own.get)
+    N, M = w.n, int(np.prod(w.mesh))
+    alg_bytes = {
+        "sort": (12 + 4) * N * 2 + (16 + 4 + 4 + 4 + 4) * N,   # x,q read twice; record, anchor, perm, rank writes
+        "make_rho": (16 + 4) * N + 4 * M,                        # sorted records + anchors in, mesh out once
+        "green": (8 * (M // w.mesh[2]) * (w.mesh[2] // 2 + 1)) * (1 + 3) + 4 * (M // w.mesh[2]) * (w.mesh[2] // 2 + 1),
+        "fieldforce": 16 * M + (16 + 4 + 4 + 12) * N,            # float4 field once, records, anchors, perm, forces
+    }[dom]
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / (stage_ms[dom] * 1e-3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+            "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(stage_ms[dom], 5),
+            "stage_ms": {k: round(v, 5) for k, v in stage_ms.items()}}
+
+    # end to end through the host-buffer C-ABI call (pinned host memory)
+    xh = torch.tensor(w.x, dtype=torch.float32).pin_memory()
+    qh = torch.tensor(w.q, dtype=torch.float32).pin_memory()
+    fh = torch.empty((w.n, 3), dtype=torch.float32).pin_memory()
+    evh = torch.empty(8, dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        plan.compute_host_into(w.n, xh.data_ptr(), qh.data_ptr(), fh.data_ptr(), evh.data_ptr())
+    ne = max(20, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        plan.compute_host_into(w.n, xh.data_ptr(), qh.data_ptr(), fh.data_ptr(), evh.data_ptr())
+    e2e_s = (time.perf_counter() - t0) / ne
+
+    # the other forms of the same metric, shorter runs
+    variants = {}
+    for mode, prec, xx, qq in (("ad", "fp32c", x32, q32), ("ik", "fp64", x64, q64), ("ad", "fp64", x64, q64)):
+        pv = make_plan(w, g, mode, prec)
+        fv = torch.empty((w.n, 3), dtype=xx.dtype, device="cuda")
+        tv, _ = time_steps(torch, pv, xx, qq, fv, ev, max(20, args.steps // 4), 3, flush)
+        variants[f"{mode}_{prec}"] = {"steps_per_s": round(1000.0 / (tv / max(20, args.steps // 4)), 1)}
+        pv.close()
+
+    launches_per_step = 5  # particle_map, scatter, make_rho, green, fieldforce (cuFFT and the memset are not ours)
+    line = {
+        "metric": metric_name(), "value": round(steps_per_s, 2), "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32c", "data": "synthetic",
+        "config": config_dict(w, {"parallelism": "replicas" if world > 1 else "single"}),
+        "mparticles_per_s": round(world * N / (ms_per_step * 1e-3) / 1e6, 2),
+        "rel_force_err_vs_fp64": rel_err, "rel_energy_err_vs_fp64": e_err,
+        "ms_per_step_without_stage_events": round(ms_plain, 5),
+        "roofline": roof,
+        "e2e": {"value": round(world / e2e_s, 2), "unit": "steps/s", "h2d_bytes_per_step": int(16 * N),
+                "d2h_bytes_per_step": int(12 * N + 56)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks_rep,
+        "variants": variants,
+    }
+    return line
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(w, budget_s=12.0, max_steps=50):
+    from oracle import OraclePPPM, estimate_g_ewald
+
+    g = estimate_g_ewald(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
+    o = OraclePPPM(w.box, w.mesh, w.order, g, "ik", w.qqrd2e)
+    x = w.x.astype(np.float32).astype(np.float64)
+    q = w.q.astype(np.float32).astype(np.float64)
+    o.compute(x, q)
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_steps and time.perf_counter() - t0 < budget_s:
+        o.compute(x, q)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def cpu_cores_used():
+    # numpy's FFT and bincount run on one thread
+    return 1
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return None
+    w = workload()
+    steps = max(1, args.steps)
+    budget = 60.0
+    rate, n, dt = oracle_rate(w, budget_s=budget, max_steps=steps)
+    return {"impl": "reference", "metric": metric_name(), "value": round(rate, 4), "unit": "steps/s",
+            "n_gpus": world, "steps": n, "warmup": 1, "ms_per_step": round(1000.0 / rate, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(w, {"precision": "fp64 (oracle)"}),
+            "cpu_baseline": {"value": round(rate, 4), "unit": "steps/s", "cores": cpu_cores_used(),
+                             "kind": "oracle", "sample": f"{n} full oracle steps of the workload ({dt:.1f} s)"},
+            "e2e": {"value": round(rate, 4), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        line = reference_arm(args, rank, world)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    line = gpu_arm(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            rate, n, dt = oracle_rate(workload())
+            line["cpu_baseline"] = {"value": round(rate, 4), "unit": "steps/s", "cores": cpu_cores_used(),
+                                    "kind": "oracle",
+                                    "sample": f"{n} full FP64 oracle steps of the same workload ({dt:.1f} s)"}
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * pppm_gb300.h -- C ABI of the GB300 (sm_103a) PPPM k-space particle-mesh path.
+ *
+ * The path is the long-range half of PPPM electrostatics as McDoniel et al.,
+ * "LAMMPS' PPPM Long-Range Solver for the Second Generation Xeon Phi"
+ * (arXiv:1702.04250), define it in Sec. 2.1 (three steps: map charges to a
+ * grid with a stencil; solve Poisson's equation with a forward 3-D FFT and one
+ * (ad) or three (ik) inverse FFTs; map back to the particles with the same
+ * stencil) and Sec. 3.1-3.2 (the Map-Charge and Distribute-Force mapping
+ * functions, the Poisson solver).
+ *
+ * Conventions for every call:
+ *  - Boxes are orthorhombic with the lower corner at the origin; positions
+ *    outside [0, L) are wrapped periodically (not an error).
+ *  - "device" pointers are CUDA device (or managed) memory on the plan's
+ *    device; "host" pointers are ordinary or pinned host memory.
+ *  - Layouts are C order: positions x[n][3], forces f[n][3], charges q[n];
+ *    the element type is double for PPPM_FP64 and float for PPPM_FP32 /
+ *    PPPM_FP32C.  Meshes are [Mx][My][Mz] with z fastest.
+ *  - The caller owns x, q, f and the energy/virial buffer; the plan owns its
+ *    mesh, spectra, Green's function, sort scratch and cuFFT plans.
+ *  - Every call returns a pppm_status; nothing is thrown across the ABI.
+ *    Calls that enqueue GPU work are asynchronous on the plan's stream unless
+ *    stated otherwise; device-side problems (non-finite inputs) are recorded
+ *    in a device error word and reported by pppm_sync().
+ *  - A plan is bound to one device and one stream and is not thread-safe.
+ */
+#ifndef PPPM_GB300_H
+#define PPPM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pppm_plan pppm_plan;
+
+enum pppm_status {
+    PPPM_OK = 0,
+    PPPM_EINVAL = 1,      /* bad argument (sizes, order, mesh smaller than the stencil, ...) */
+    PPPM_ENOMEM = 2,      /* device allocation failed */
+    PPPM_ECUDA = 3,       /* a CUDA runtime call failed */
+    PPPM_ECUFFT = 4,      /* a cuFFT call failed */
+    PPPM_ENONFINITE = 5,  /* a position or charge was NaN/Inf (reported by pppm_sync) */
+    PPPM_ETIMEOUT = 6,    /* a bounded device wait gave up */
+    PPPM_ENOTREADY = 7    /* the requested quantity was not computed by the last call */
+};
+
+/* Differentiation mode (Sec. 2.1 / Sec. 3.1): ik takes the gradient in
+ * k-space (three inverse FFTs, three field components interpolated); ad
+ * interpolates the scalar potential with derivative coefficients. */
+enum pppm_diff { PPPM_IK = 0, PPPM_AD = 1 };
+
+/* Arithmetic of the per-step path.  FP64: everything in double.  FP32:
+ * spreading, FFTs and interpolation in float.  FP32C: as FP32, with the
+ * mesh charge accumulated in compensated (hi + lo) float.  In all three the
+ * Green's function, the ad self-force coefficients and the energy/virial
+ * reductions are computed in double. */
+enum pppm_precision { PPPM_FP64 = 0, PPPM_FP32C = 1, PPPM_FP32 = 2 };
+
+/* Ewald splitting parameter from a target relative force accuracy.
+ * Sec. 2.3 lists the accuracy epsilon and the cutoff r_C as the user's
+ * parameters; the paper does not print the rule, so this solves the
+ * real-space force-error estimate 2 q2 exp(-g^2 rc^2) / sqrt(N rc V) = rel_acc
+ * (q2 = sum q_i^2) for g.  Host only, synchronous.
+ * Returns PPPM_EINVAL if no positive g satisfies it or an argument is <= 0. */
+int pppm_estimate_g(double rel_acc, double r_cut, int64_t n, double q2,
+                    const double box[3], double *g_out);
+
+/* Create a plan (Sec. 2.1 setup before step 1): the order-P assignment
+ * polynomials (Sec. 3.1: product of three 1-D polynomials of order S = P),
+ * the influence function G(k) on the half spectrum, the ad self-force
+ * coefficients, cuFFT plans and all scratch for up to n_max particles.
+ *   box[3]      box edges (> 0)
+ *   n_max       largest particle count pppm_compute will be given (>= 0)
+ *   order       P in 2..7 (stencil of P^3 mesh points)
+ *   mesh[3]     mesh points per dimension, each >= order and <= 1024
+ *   g_ewald     Ewald splitting parameter (> 0)
+ *   diff_mode   PPPM_IK or PPPM_AD
+ *   precision   PPPM_FP64, PPPM_FP32C or PPPM_FP32
+ *   qqrd2e      Coulomb constant C (energies in C * e^2 / length)
+ *   cuda_stream cudaStream_t the plan enqueues on (NULL = legacy default)
+ * Setup is synchronous.  On failure *out is NULL and nothing is leaked. */
+int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order,
+               const int mesh[3], double g_ewald, int diff_mode, int precision,
+               double qqrd2e, void *cuda_stream);
+
+/* Release every resource of the plan (synchronises its stream first). */
+int pppm_destroy(pppm_plan *p);
+
+/* Change the stream the plan enqueues on (drops any captured graph). */
+int pppm_set_stream(pppm_plan *p, void *cuda_stream);
+
+/* One k-space evaluation (Sec. 2.1 steps 1-3; Sec. 3.1 Map-Charge and
+ * Distribute-Force ik/ad; Sec. 3.2 Poisson solver):
+ *   particle_map (wrap, stencil anchor, sort by mesh tile) -> make_rho ->
+ *   forward FFT -> influence-function multiply with energy/virial ->
+ *   3 (ik) / 1 (ad) inverse FFTs -> fieldforce.
+ *   n        particle count, 0 <= n <= n_max
+ *   x        device, [n][3] positions
+ *   q        device, [n] charges
+ *   f        device, [n][3] k-space forces, overwritten (C q E, minus the ad
+ *            self-force correction in ad mode)
+ *   ev       device, 7 doubles or NULL: energy (mesh part minus the self and
+ *            neutralising-background terms) then virial xx yy zz xy xz yz
+ * Asynchronous; inputs must stay valid until the stream reaches the end of
+ * the call.  With graph mode on (pppm_set_graph) the whole step is launched
+ * as one CUDA graph, re-captured whenever n or a pointer changes. */
+int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, double *ev);
+
+/* pppm_compute on HOST buffers: copies x and q to the device, computes, copies
+ * f and the 7 energy/virial doubles back, synchronises and returns the device
+ * status (PPPM_ENONFINITE if an input was not finite).  ev_host may be NULL. */
+int pppm_compute_host(pppm_plan *p, int64_t n, const void *x_host, const void *q_host,
+                      void *f_host, double *ev_host);
+
+/* Synchronise the plan's stream and report (then clear) the device error
+ * word: PPPM_ENONFINITE if a non-finite position or charge was seen by any
+ * compute since the last sync, else PPPM_OK (or PPPM_ECUDA). */
+int pppm_sync(pppm_plan *p);
+
+/* Turn CUDA-graph launch of pppm_compute on (1) or off (0). */
+int pppm_set_graph(pppm_plan *p, int enable);
+
+/* Exact gradients of the PPPM energy (the energy reported by pppm_compute):
+ *   dEdx[i][a] = C q_i sum_p dW(p - u_i)/dx_a phi(p)   (no self-force term)
+ *   dEdq[i]    = C phi(x_i) - 2 C g q_i / sqrt(pi) - C pi Q / (g^2 V)
+ * with phi the mesh potential of this plan's influence function (one extra
+ * inverse FFT in ik mode).  Same element types and ownership as pppm_compute;
+ * dEdx or dEdq may be NULL.  ev as in pppm_compute.  Asynchronous. */
+int pppm_energy_grad(pppm_plan *p, int64_t n, const void *x, const void *q,
+                     void *dEdx, void *dEdq, double *ev);
+
+/* Internal arrays, for checking each stage against an independent
+ * implementation.  Synchronous device-to-device (or device-to-host when
+ * to_host != 0) copy of `bytes` bytes into dst; PPPM_EINVAL if bytes does not
+ * equal the array's size, PPPM_ENOTREADY if the last compute did not make it.
+ *   PPPM_ARR_RHO        mesh charge density, [Mx][My][Mz] of the step's type
+ *   PPPM_ARR_GREEN      G(k), double [Mx][My][Mz/2+1] (unscaled)
+ *   PPPM_ARR_FIELD      ik: E as [Mx][My][Mz][4] (x,y,z,unused); ad: phi [Mx][My][Mz]
+ *   PPPM_ARR_ANCHOR     int32 [n][3] stencil anchor per particle, input order
+ *   PPPM_ARR_TILESTART  int32 [ntiles+1] tile offsets of the sorted order
+ *   PPPM_ARR_PERM       int32 [n] input index of each sorted particle
+ *   PPPM_ARR_SELFFORCE  double [3][2] ad self-force coefficients c[a][n-1]
+ *   PPPM_ARR_ENERGY     double [7] energy and virial of the last call */
+enum pppm_array {
+    PPPM_ARR_RHO = 0, PPPM_ARR_GREEN = 1, PPPM_ARR_FIELD = 2, PPPM_ARR_ANCHOR = 3,
+    PPPM_ARR_TILESTART = 4, PPPM_ARR_PERM = 5, PPPM_ARR_SELFFORCE = 6, PPPM_ARR_ENERGY = 7
+};
+int pppm_get_array(pppm_plan *p, int which, void *dst, size_t bytes, int to_host);
+
+/* Per-stage device timing of pppm_compute with CUDA events recorded on the
+ * plan's stream between stages (also inside a captured graph).  Stages:
+ * [0] particle_map + sort, [1] make_rho (incl. mesh clear), [2] forward FFT,
+ * [3] influence-function multiply + energy/virial, [4] inverse FFT(s),
+ * [5] fieldforce.  pppm_stage_times waits for the last profiled call and
+ * writes milliseconds; PPPM_ENOTREADY if profiling was off for it. */
+int pppm_set_profiling(pppm_plan *p, int enable);
+int pppm_stage_times(pppm_plan *p, float ms[6]);
+
+/* Plan facts: [0..2] mesh, [3] order, [4] ntiles, [5] tile edge B,
+ * [6] diff mode, [7] precision, [8] n_max, [9] last n. */
+int pppm_plan_info(const pppm_plan *p, int64_t info[10]);
+
+/* Static description of a status code (never NULL). */
+const char *pppm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPPM_GB300_H */

@@ -1,0 +1,211 @@
+// Poisson solve in reciprocal space (Sec. 2.1 step 2, Sec. 3.2): between the
+// forward FFT of the mesh charge and the inverse FFT(s), multiply by the
+// influence function G(k) -- for ik also by -i k_a, giving the three field
+// spectra that need three inverse transforms; for ad only G, giving the
+// potential that needs one -- and reduce the energy and virial.
+//
+// The paper does not print G; this is the Hockney-Eastwood optimal form for
+// ik differentiation and the same form without the k.k_m / k^2 factor for ad:
+//   G(k) = [sum_m (k.k_m)/k^2 R(k_m) U^2(k_m)] / [sum_m U^2(k_m)]^2 (ik)
+//   G(k) = [sum_m R(k_m) U^2(k_m)] / [sum_m U^2(k_m)]^2             (ad)
+//   R(k) = 4 pi exp(-k^2/4g^2) / k^2,  U(k) = prod_d sinc^P(k_d h_d / 2),
+//   k_m = k + 2 pi m / h, numerator over |m_d| <= 2.
+// The denominator's per-dimension sum is evaluated exactly as the finite
+// cosine series sum_g M_2P(g) cos(k h g) (Poisson summation).
+//
+// Energy and virial (paper silent; Ewald's reciprocal-space forms with G in
+// place of R):  E = (C/2) vcell^2/V sum_k G|rho_hat|^2 over the full
+// spectrum, W_ab = same sum times [delta_ab - 2(1 + k^2/4g^2) k_a k_b / k^2].
+// Per-thread sums are taken in the step's type, combined in FP64 with warp
+// shuffles, and the last CTA reduces the per-CTA partials in a fixed order.
+#include "pppm_common.cuh"
+
+namespace pppm {
+
+constexpr int GREEN_THREADS = 256;
+
+// ---------------------------------------------------------------------------
+// Setup (FP64): G on the half spectrum and the ad self-force sums
+//   S[a][n-1] = sum_k w(k) G(k) B_a(k_a h_a, n) prod_{b != a} B_b(k_b h_b, 0)
+// where w = 1 for kz = 0 and the z-Nyquist plane, 2 otherwise.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(GREEN_THREADS) k_green_setup(GreenSetup gs, double *__restrict__ G64,
+                                                               double *__restrict__ sf) {
+    __shared__ double sh[6][GREEN_THREADS / 32];
+    const int Mx = gs.M[0], My = gs.M[1], Mzh = gs.Mzh;
+    const int64_t total = (int64_t)Mx * My * Mzh;
+    const int off[3] = {0, Mx, Mx + My};
+    const int len = Mx + My + Mzh;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const double twopi = 2.0 * M_PI;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int iz = (int)(e % Mzh);
+        const int iy = (int)((e / Mzh) % My);
+        const int ix = (int)(e / ((int64_t)Mzh * My));
+        const int idx[3] = {ix, iy, iz};
+        double k[3];
+        for (int d = 0; d < 3; ++d) k[d] = gs.ktab[off[d] + idx[d]];
+        const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        double G = 0.0;
+        if (k2 > 0.0) {
+            double num = 0.0;
+            for (int mx = -2; mx <= 2; ++mx) {
+                const double kmx = k[0] + twopi * mx / gs.h[0];
+                const double axv = gs.atab[(mx + 2) * len + off[0] + ix];
+                if (axv == 0.0) continue;
+                for (int my = -2; my <= 2; ++my) {
+                    const double kmy = k[1] + twopi * my / gs.h[1];
+                    const double ayv = gs.atab[(my + 2) * len + off[1] + iy];
+                    if (ayv == 0.0) continue;
+                    for (int mz = -2; mz <= 2; ++mz) {
+                        const double kmz = k[2] + twopi * mz / gs.h[2];
+                        const double azv = gs.atab[(mz + 2) * len + off[2] + iz];
+                        if (azv == 0.0) continue;
+                        const double km2 = kmx * kmx + kmy * kmy + kmz * kmz;
+                        double t = 4.0 * M_PI * axv * ayv * azv / km2;
+                        if (gs.ik) t *= (k[0] * kmx + k[1] * kmy + k[2] * kmz);
+                        num += t;
+                    }
+                }
+            }
+            const double D = gs.dtab[off[0] + ix] * gs.dtab[off[1] + iy] * gs.dtab[off[2] + iz];
+            double den = D * D;
+            if (gs.ik) den *= k2;
+            G = num / den;
+        }
+        G64[e] = G;
+        const double w = (iz == 0 || (2 * (Mzh - 1) == gs.M[2] && iz == Mzh - 1)) ? 1.0 : 2.0;
+        const double wG = w * G;
+        for (int a = 0; a < 3; ++a) {
+            for (int n = 1; n <= 2; ++n) {
+                double p = wG;
+                for (int d = 0; d < 3; ++d) p *= gs.btab[((d == a) ? n : 0) * len + off[d] + idx[d]];
+                acc[a * 2 + n - 1] += p;
+            }
+        }
+    }
+    for (int c = 0; c < 6; ++c) {
+        const double v = warp_sum(acc[c]);
+        if ((threadIdx.x & 31) == 0) sh[c][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = 0.0;
+        for (int w = 0; w < GREEN_THREADS / 32; ++w) v += sh[threadIdx.x][w];
+        atomicAdd(&sf[threadIdx.x], v);
+    }
+}
+
+void launch_green_setup(const GreenSetup &gs, double *G64, double *sf_sums, cudaStream_t s) {
+    cudaMemsetAsync(sf_sums, 0, 6 * sizeof(double), s);
+    const int64_t total = (int64_t)gs.M[0] * gs.M[1] * gs.Mzh;
+    int nb = (int)std::min<int64_t>((total + GREEN_THREADS - 1) / GREEN_THREADS, 152 * 16);
+    if (nb < 1) nb = 1;
+    k_green_setup<<<nb, GREEN_THREADS, 0, s>>>(gs, G64, sf_sums);
+}
+
+// ---------------------------------------------------------------------------
+// Per step
+// ---------------------------------------------------------------------------
+template <typename R, bool IK>
+__global__ void __launch_bounds__(GREEN_THREADS) k_green(Geom<R> g, const complex_t<R> *__restrict__ rhat,
+                                                         complex_t<R> *__restrict__ spec, GreenBufs b,
+                                                         EnergyConsts ec, double *ev_user) {
+    __shared__ double sh[7][GREEN_THREADS / 32];
+    __shared__ bool last;
+    const int Mx = g.M[0], My = g.M[1], Mzh = g.Mzh;
+    const int64_t total = (int64_t)Mx * My * Mzh;
+    const R *__restrict__ Gs = reinterpret_cast<const R *>(b.Gs);
+    const R *__restrict__ kv = reinterpret_cast<const R *>(b.kvec);
+    const R *__restrict__ kd = reinterpret_cast<const R *>(b.kdiff);
+    const bool evenz = (2 * (Mzh - 1) == g.M[2]);
+    const R i4g2 = (R)ec.inv4g2;
+    R acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int iz = (int)(e % Mzh);
+        const int iy = (int)((e / Mzh) % My);
+        const int ix = (int)(e / ((int64_t)Mzh * My));
+        const complex_t<R> r = rhat[e];
+        const R G = Gs[e];
+        const R pr = G * r.x, pi = G * r.y;
+        if (IK) {
+            // E_a = -i k_a G rho_hat / M  ->  (k_a pi, -k_a pr)
+            const R kx = kd[ix], ky = kd[Mx + iy], kz = kd[Mx + My + iz];
+            complex_t<R> o;
+            o.x = kx * pi; o.y = -kx * pr; spec[e] = o;
+            o.x = ky * pi; o.y = -ky * pr; spec[total + e] = o;
+            o.x = kz * pi; o.y = -kz * pr; spec[2 * total + e] = o;
+        } else {
+            complex_t<R> o;
+            o.x = pr; o.y = pi;
+            spec[e] = o;
+        }
+        const R w = (iz == 0 || (evenz && iz == Mzh - 1)) ? R(1) : R(2);
+        const R s = w * G * (r.x * r.x + r.y * r.y);
+        const R kx = kv[ix], ky = kv[Mx + iy], kz = kv[Mx + My + iz];
+        const R k2 = kx * kx + ky * ky + kz * kz;
+        const R fac = (k2 > R(0)) ? R(2) * (R(1) + k2 * i4g2) / k2 : R(0);
+        const R sf = s * fac;
+        acc[0] += s;
+        acc[1] += s - sf * kx * kx;
+        acc[2] += s - sf * ky * ky;
+        acc[3] += s - sf * kz * kz;
+        acc[4] -= sf * kx * ky;
+        acc[5] -= sf * kx * kz;
+        acc[6] -= sf * ky * kz;
+    }
+    for (int c = 0; c < 7; ++c) {
+        const double v = warp_sum((double)acc[c]);
+        if ((threadIdx.x & 31) == 0) sh[c][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = 0.0;
+        for (int w = 0; w < GREEN_THREADS / 32; ++w) v += sh[threadIdx.x][w];
+        b.part[7 * blockIdx.x + threadIdx.x] = v;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int ticket = atomicAdd(b.counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 7) {
+        double v = 0.0;
+        for (int k = 0; k < (int)gridDim.x; ++k) v += __ldcg(&b.part[7 * k + threadIdx.x]);
+        v *= ec.epref;
+        if (threadIdx.x == 0) {
+            const double Q = __ldcg(&b.qsum[0]), Q2 = __ldcg(&b.qsum[1]);
+            v += ec.eself * Q2 + ec.ebg * Q * Q;
+        }
+        b.ev[threadIdx.x] = v;
+        if (ev_user) ev_user[threadIdx.x] = v;
+    }
+    if (threadIdx.x == 0) *b.counter = 0u;
+}
+
+template <typename R>
+void launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec, const GreenBufs &b,
+                  const EnergyConsts &ec, double *ev_user, cudaStream_t s) {
+    const int64_t total = (int64_t)g.M[0] * g.M[1] * g.Mzh;
+    int nb = (int)std::min<int64_t>((total + GREEN_THREADS * 4 - 1) / (GREEN_THREADS * 4), 152 * 8);
+    if (nb < 1) nb = 1;
+    const auto *rh = reinterpret_cast<const complex_t<R> *>(rho_hat);
+    auto *sp = reinterpret_cast<complex_t<R> *>(spec);
+    if (ik)
+        k_green<R, true><<<nb, GREEN_THREADS, 0, s>>>(g, rh, sp, b, ec, ev_user);
+    else
+        k_green<R, false><<<nb, GREEN_THREADS, 0, s>>>(g, rh, sp, b, ec, ev_user);
+}
+
+template void launch_green<float>(const Geom<float> &, bool, const void *, void *, const GreenBufs &,
+                                  const EnergyConsts &, double *, cudaStream_t);
+template void launch_green<double>(const Geom<double> &, bool, const void *, void *, const GreenBufs &,
+                                   const EnergyConsts &, double *, cudaStream_t);
+
+}  // namespace pppm

@@ -1,0 +1,182 @@
+// particle_map: the "loop over all atoms" that starts every mapping function
+// (Sec. 3.1).  Each particle is wrapped into the box, its stencil anchor and
+// offset delta are computed, and the particles are counting-sorted by the
+// mesh tile of their anchor, so that make_rho and fieldforce see each tile's
+// particles contiguously.
+//
+// Two kernels:
+//  k_particle_map  anchor + tile histogram (atomic ranks), per-block sums of q
+//                  and q^2; the last block to finish reduces those sums and
+//                  turns the histogram into tile offsets (exclusive scan),
+//                  zeroing the histogram for the next step.
+//  k_scatter       writes each particle's (delta, q) record, packed anchor and
+//                  input index at its sorted position.
+#include "pppm_common.cuh"
+
+namespace pppm {
+
+constexpr int MAP_THREADS = 256;
+
+template <typename R>
+__device__ __forceinline__ bool load_particle(const R *__restrict__ x, const R *__restrict__ q,
+                                              int i, R (&xi)[3], R &qi) {
+    xi[0] = x[3 * (int64_t)i + 0];
+    xi[1] = x[3 * (int64_t)i + 1];
+    xi[2] = x[3 * (int64_t)i + 2];
+    qi = q[i];
+    const bool ok = isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]) && isfinite(qi);
+    if (!ok) {  // keep the kernels in bounds; the host reports PPPM_ENONFINITE
+        xi[0] = xi[1] = xi[2] = R(0);
+        qi = R(0);
+    }
+    return ok;
+}
+
+template <typename R>
+__device__ __forceinline__ void anchors(const Geom<R> &g, const R (&xi)[3], int (&a)[3], R (&d)[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        grid_anchor<R>(xi[k], g.L[k], g.iL[k], g.ih[k], g.ih_lo[k], g.M[k], g.P, a[k], d[k]);
+}
+
+template <typename R>
+__device__ __forceinline__ int tile_index(const Geom<R> &g, const int (&a)[3]) {
+    return (tile_of(a[0], g.T[0], g.M[0]) * g.T[1] + tile_of(a[1], g.T[1], g.M[1])) * g.T[2] +
+           tile_of(a[2], g.T[2], g.M[2]);
+}
+
+__device__ double block_sum(double v, double *sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;  // valid in thread 0
+}
+
+template <typename R>
+__global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, const R *__restrict__ x,
+                                                              const R *__restrict__ q, SortBufs b) {
+    __shared__ double sh[32];
+    __shared__ int sh_scan[MAP_THREADS / 32];
+    __shared__ bool last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double qs = 0.0, qq = 0.0;
+    if (i < n) {
+        R xi[3], qi;
+        if (!load_particle<R>(x, q, i, xi, qi)) atomicOr(b.err, 1);
+        int a[3];
+        R d[3];
+        anchors<R>(g, xi, a, d);
+        b.rank[i] = atomicAdd(&b.tile_count[tile_index<R>(g, a)], 1);
+        b.anchor[i] = pack_anchor(a[0], a[1], a[2]);
+        qs = (double)qi;
+        qq = qs * qs;
+    }
+    __threadfence();  // histogram atomics are visible before this block's ticket
+    const double s1 = block_sum(qs, sh);
+    const double s2 = block_sum(qq, sh);
+    if (threadIdx.x == 0) {
+        b.blk[2 * blockIdx.x] = s1;
+        b.blk[2 * blockIdx.x + 1] = s2;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(b.counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+
+    // ---- last block: totals of q and q^2 --------------------------------
+    double t1 = 0.0, t2 = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        t1 += __ldcg(&b.blk[2 * k]);
+        t2 += __ldcg(&b.blk[2 * k + 1]);
+    }
+    t1 = block_sum(t1, sh);
+    t2 = block_sum(t2, sh);
+    if (threadIdx.x == 0) {
+        b.qsum[0] = t1;
+        b.qsum[1] = t2;
+    }
+
+    // ---- last block: exclusive scan of the tile histogram ---------------
+    const int nt = g.ntiles;
+    const int chunk = (nt + blockDim.x - 1) / blockDim.x;
+    const int lo = min(nt, (int)threadIdx.x * chunk), hi = min(nt, lo + chunk);
+    int local = 0;
+    for (int k = lo; k < hi; ++k) local += __ldcg(&b.tile_count[k]);
+    // block exclusive scan of `local`
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) sh_scan[w] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            const int v = sh_scan[k];
+            sh_scan[k] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    int run = sh_scan[w] + incl - local;
+    for (int k = lo; k < hi; ++k) {
+        const int c = __ldcg(&b.tile_count[k]);
+        b.tile_start[k] = run;
+        run += c;
+        b.tile_count[k] = 0;
+    }
+    if (hi == nt && lo < hi) b.tile_start[nt] = run;
+    if (nt == 0 && threadIdx.x == 0) b.tile_start[0] = 0;
+    if (threadIdx.x == 0) *b.counter = 0u;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(MAP_THREADS) k_scatter(Geom<R> g, int n, const R *__restrict__ x,
+                                                         const R *__restrict__ q, SortBufs b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    R xi[3], qi;
+    load_particle<R>(x, q, i, xi, qi);
+    int a[3];
+    R d[3];
+    anchors<R>(g, xi, a, d);
+    const uint32_t packed = b.anchor[i];  // same computation as k_particle_map
+    int s[3];
+    unpack_anchor(packed, s[0], s[1], s[2]);
+    const int dest = b.tile_start[tile_index<R>(g, s)] + b.rank[i];
+    vec4_t<R> r;
+    r.x = d[0];
+    r.y = d[1];
+    r.z = d[2];
+    r.w = qi;
+    reinterpret_cast<vec4_t<R> *>(b.rec)[dest] = r;
+    b.cell[dest] = packed;
+    b.perm[dest] = i;
+}
+
+template <typename R>
+void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const SortBufs &b,
+                 cudaStream_t s) {
+    const int nb = (int)((n + MAP_THREADS - 1) / MAP_THREADS);
+    k_particle_map<R><<<nb, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b);
+    k_scatter<R><<<nb, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b);
+}
+
+template void launch_sort<float>(const Geom<float> &, int64_t, const float *, const float *,
+                                 const SortBufs &, cudaStream_t);
+template void launch_sort<double>(const Geom<double> &, int64_t, const double *, const double *,
+                                  const SortBufs &, cudaStream_t);
+
+}  // namespace pppm

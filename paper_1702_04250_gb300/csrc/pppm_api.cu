@@ -1,0 +1,637 @@
+// C-ABI layer: plan set-up (Sec. 2.1/2.3 parameters: order, mesh, g_ewald,
+// differentiation mode), per-step enqueue of the three PPPM steps, CUDA-graph
+// capture of a whole step, the host-buffer variant, and read-back of internal
+// arrays for stage-by-stage checking.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pppm_common.cuh"
+
+using namespace pppm;
+
+struct pppm_plan {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int P = 0, mode = 0, prec = 0;
+    bool fp64 = false, comp = false, ik = true;
+    int M[3] = {0, 0, 0}, Mzh = 0;
+    int64_t Mtot = 0, Mhalf = 0;
+    int T[3] = {0, 0, 0}, ntiles = 0;
+    double box[3] = {0, 0, 0}, h[3] = {0, 0, 0}, g = 0, C = 0, V = 0, vcell = 0;
+    int64_t n_max = 0, n_last = -1;
+    Geom<float> gf{};
+    Geom<double> gd{};
+    SortBufs sb{};
+    GreenBufs gb{};
+    EnergyConsts ec{};
+    void *rho = nullptr, *rho_hat = nullptr, *spec = nullptr, *field = nullptr;
+    double *G64 = nullptr;
+    void *Gs = nullptr, *kvec = nullptr, *kdiff = nullptr;
+    double *green_part = nullptr;
+    unsigned int *counters = nullptr;  // [0] map, [1] green
+    double *ev = nullptr;              // [8]
+    double *d_sf = nullptr;            // [6] setup sums
+    double sf[6] = {0, 0, 0, 0, 0, 0};
+    cufftHandle r2c = 0, c2r = 0, c2r1 = 0;
+    bool have_r2c = false, have_c2r = false, have_c2r1 = false;
+    bool field_is_field = false, have_rho = false;
+    void *hx = nullptr, *hq = nullptr, *hf = nullptr;  // device staging for the host path
+    double *hev = nullptr;
+    bool prof_on = false, prof_valid = false;
+    cudaEvent_t prof[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool graph_on = false;
+    bool gkey_prof = false;
+    cudaGraphExec_t gexec = nullptr;
+    const void *gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int64_t gkey_n = -1;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return PPPM_OK;
+    if (e == cudaErrorMemoryAllocation) return PPPM_ENOMEM;
+    return PPPM_ECUDA;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+#define CKF(call)                                  \
+    do {                                           \
+        cufftResult r_ = (call);                   \
+        if (r_ != CUFFT_SUCCESS) return PPPM_ECUFFT; \
+    } while (0)
+
+template <typename T>
+int dmalloc(pppm_plan *p, T **ptr, size_t bytes) {
+    void *v = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PPPM_ENOMEM;
+    }
+    p->allocs.push_back(v);
+    *ptr = reinterpret_cast<T *>(v);
+    return PPPM_OK;
+}
+
+__global__ void k_scale_green(const double *__restrict__ G, float *__restrict__ out32,
+                              double *__restrict__ out64, int64_t n, double s) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = G[i] * s;
+        if (out32) out32[i] = (float)v;
+        if (out64) out64[i] = v;
+    }
+}
+
+template <typename R>
+void fill_geom(pppm_plan *p, Geom<R> &g, const double coef[MAXP][MAXP], const double dcoef[MAXP][MAXP]) {
+    for (int d = 0; d < 3; ++d) {
+        g.M[d] = p->M[d];
+        g.T[d] = p->T[d];
+        g.L[d] = (R)p->box[d];
+        g.iL[d] = (R)(1.0 / p->box[d]);
+        const double ih = (double)p->M[d] / p->box[d];
+        g.ih[d] = (R)ih;
+        g.ih_lo[d] = (R)(ih - (double)(R)ih);
+        g.h[d] = (R)p->h[d];
+    }
+    g.Mzh = p->Mzh;
+    g.ntiles = p->ntiles;
+    g.P = p->P;
+    g.rlo = (p->P - 1) / 2;
+    g.ivcell = (R)(1.0 / p->vcell);
+    for (int k = 0; k < MAXP; ++k)
+        for (int l = 0; l < MAXP; ++l) {
+            g.coef[k][l] = (R)coef[k][l];
+            g.dcoef[k][l] = (R)dcoef[k][l];
+        }
+}
+
+void release(pppm_plan *p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (auto &e : p->prof)
+        if (e) cudaEventDestroy(e);
+    if (p->have_r2c) cufftDestroy(p->r2c);
+    if (p->have_c2r) cufftDestroy(p->c2r);
+    if (p->have_c2r1) cufftDestroy(p->c2r1);
+    for (void *v : p->allocs) cudaFree(v);
+    delete p;
+}
+
+int build_tables_and_green(pppm_plan *p) {
+    const int Mx = p->M[0], My = p->M[1], Mz = p->M[2], Mzh = p->Mzh;
+    const int len = Mx + My + Mzh;
+    const int dimlen[3] = {Mx, My, Mzh};
+    const int off[3] = {0, Mx, Mx + My};
+    std::vector<double> ktab(len), kdiff(len), atab(5 * (size_t)len), dtab(len), btab(3 * (size_t)len);
+    double m2p[MAXP + 1];
+    spline2p_at_integers(p->P, m2p);
+    for (int d = 0; d < 3; ++d) {
+        for (int i = 0; i < dimlen[d]; ++i) {
+            const double kappa = grid_kappa(i, p->M[d]);  // k h
+            const double k = kappa / p->h[d];
+            ktab[off[d] + i] = k;
+            kdiff[off[d] + i] = (2 * i == p->M[d]) ? 0.0 : k;  // Nyquist derivative dropped
+            for (int m = -2; m <= 2; ++m) {
+                const double km = k + 2.0 * M_PI * m / p->h[d];
+                const double u = alias_cross(kappa + 2.0 * M_PI * m, 0, p->P, 0);  // U1^2 at this alias
+                atab[(size_t)(m + 2) * len + off[d] + i] = std::exp(-km * km / (4.0 * p->g * p->g)) * u;
+            }
+            double D = m2p[0];
+            for (int gg = 1; gg < p->P; ++gg) D += 2.0 * m2p[gg] * std::cos(kappa * gg);
+            dtab[off[d] + i] = D;
+            for (int n = 0; n <= 2; ++n) btab[(size_t)n * len + off[d] + i] = alias_cross(kappa, n, p->P, 50);
+        }
+    }
+    double *d_ktab, *d_atab, *d_dtab, *d_btab;
+    int rc;
+    if ((rc = dmalloc(p, &d_ktab, sizeof(double) * len))) return rc;
+    if ((rc = dmalloc(p, &d_atab, sizeof(double) * 5 * len))) return rc;
+    if ((rc = dmalloc(p, &d_dtab, sizeof(double) * len))) return rc;
+    if ((rc = dmalloc(p, &d_btab, sizeof(double) * 3 * len))) return rc;
+    CK(cudaMemcpy(d_ktab, ktab.data(), sizeof(double) * len, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_atab, atab.data(), sizeof(double) * 5 * len, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_dtab, dtab.data(), sizeof(double) * len, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_btab, btab.data(), sizeof(double) * 3 * len, cudaMemcpyHostToDevice));
+    GreenSetup gs{};
+    for (int d = 0; d < 3; ++d) {
+        gs.M[d] = p->M[d];
+        gs.h[d] = p->h[d];
+    }
+    gs.Mzh = Mzh;
+    gs.P = p->P;
+    gs.ik = p->ik;
+    gs.g = p->g;
+    gs.ktab = d_ktab;
+    gs.atab = d_atab;
+    gs.dtab = d_dtab;
+    gs.btab = d_btab;
+    launch_green_setup(gs, p->G64, p->d_sf, p->stream);
+    CK(cudaGetLastError());
+    double sums[6];
+    CK(cudaMemcpyAsync(sums, p->d_sf, sizeof(sums), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    for (int a = 0; a < 3; ++a)
+        for (int n = 1; n <= 2; ++n)
+            p->sf[a * 2 + n - 1] = 2.0 * M_PI * n * p->C / (p->h[a] * p->V) * sums[a * 2 + n - 1];
+    // step-type copies: G / M, wavenumbers
+    const double sc = 1.0 / (double)p->Mtot;
+    k_scale_green<<<256, 256, 0, p->stream>>>(p->G64, p->fp64 ? nullptr : (float *)p->Gs,
+                                               p->fp64 ? (double *)p->Gs : nullptr, p->Mhalf, sc);
+    CK(cudaGetLastError());
+    if (p->fp64) {
+        CK(cudaMemcpy(p->kvec, ktab.data(), sizeof(double) * len, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->kdiff, kdiff.data(), sizeof(double) * len, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> a(len), b(len);
+        for (int i = 0; i < len; ++i) {
+            a[i] = (float)ktab[i];
+            b[i] = (float)kdiff[i];
+        }
+        CK(cudaMemcpy(p->kvec, a.data(), sizeof(float) * len, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->kdiff, b.data(), sizeof(float) * len, cudaMemcpyHostToDevice));
+    }
+    CK(cudaStreamSynchronize(p->stream));
+    return PPPM_OK;
+}
+
+int make_ffts(pppm_plan *p) {
+    const cufftType tr2c = p->fp64 ? CUFFT_D2Z : CUFFT_R2C;
+    const cufftType tc2r = p->fp64 ? CUFFT_Z2D : CUFFT_C2R;
+    CKF(cufftPlan3d(&p->r2c, p->M[0], p->M[1], p->M[2], tr2c));
+    p->have_r2c = true;
+    CKF(cufftSetStream(p->r2c, p->stream));
+    CKF(cufftPlan3d(&p->c2r1, p->M[0], p->M[1], p->M[2], tc2r));
+    p->have_c2r1 = true;
+    CKF(cufftSetStream(p->c2r1, p->stream));
+    if (p->ik) {
+        // three field spectra -> one interleaved (Ex, Ey, Ez, pad) real array
+        int n[3] = {p->M[0], p->M[1], p->M[2]};
+        int inembed[3] = {p->M[0], p->M[1], p->Mzh};
+        int onembed[3] = {p->M[0], p->M[1], p->M[2]};
+        CKF(cufftPlanMany(&p->c2r, 3, n, inembed, 1, (int)p->Mhalf, onembed, 4, 1, tc2r, 3));
+        p->have_c2r = true;
+        CKF(cufftSetStream(p->c2r, p->stream));
+    }
+    return PPPM_OK;
+}
+
+int exec_r2c(pppm_plan *p) {
+    if (p->fp64) CKF(cufftExecD2Z(p->r2c, (cufftDoubleReal *)p->rho, (cufftDoubleComplex *)p->rho_hat));
+    else CKF(cufftExecR2C(p->r2c, (cufftReal *)p->rho, (cufftComplex *)p->rho_hat));
+    return PPPM_OK;
+}
+
+int exec_c2r(pppm_plan *p, bool all3) {
+    cufftHandle h = (all3 && p->ik) ? p->c2r : p->c2r1;
+    if (p->fp64) CKF(cufftExecZ2D(h, (cufftDoubleComplex *)p->spec, (cufftDoubleReal *)p->field));
+    else CKF(cufftExecC2R(h, (cufftComplex *)p->spec, (cufftReal *)p->field));
+    return PPPM_OK;
+}
+
+// kind 0: forces, 1: energy gradient
+template <typename R>
+int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const void *q, void *f, void *dq,
+              double *ev, int kind) {
+    cudaStream_t s = p->stream;
+    const bool prof = p->prof_on && kind == 0;
+    auto mark = [&](int i) {
+        if (prof) cudaEventRecord(p->prof[i], s);
+    };
+    mark(0);
+    launch_sort<R>(g, n, (const R *)x, (const R *)q, p->sb, s);
+    mark(1);
+    launch_make_rho<R>(g, n, p->sb, (R *)p->rho, p->comp, s);
+    mark(2);
+    int rc;
+    if ((rc = exec_r2c(p))) return rc;
+    mark(3);
+    const bool ik_spec = (kind == 0) && p->ik;
+    launch_green<R>(g, ik_spec, p->rho_hat, p->spec, p->gb, p->ec, ev, s);
+    mark(4);
+    if ((rc = exec_c2r(p, ik_spec))) return rc;
+    mark(5);
+    if (kind == 0) {
+        launch_fieldforce<R>(g, p->ik, n, p->sb, (const R *)p->field, (R *)f, (R)p->C, p->sf, s);
+    } else {
+        const double gself = -2.0 * p->C * p->g / std::sqrt(M_PI);
+        const double gbg = -p->C * M_PI / (p->g * p->g * p->V);
+        launch_energy_grad<R>(g, n, p->sb, (const R *)p->field, (R *)f, (R *)dq, (R)p->C, p->sb.qsum, gself,
+                              gbg, s);
+    }
+    mark(6);
+    p->prof_valid = prof;
+    CK(cudaGetLastError());
+    return PPPM_OK;
+}
+
+int enqueue(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, void *dq, double *ev, int kind) {
+    if (n == 0) {
+        CK(cudaMemsetAsync(p->ev, 0, 8 * sizeof(double), p->stream));
+        if (ev) CK(cudaMemsetAsync(ev, 0, 7 * sizeof(double), p->stream));
+        CK(cudaMemsetAsync(p->rho, 0, (p->fp64 ? 8 : 4) * (size_t)p->Mtot, p->stream));
+        return PPPM_OK;
+    }
+    if (p->fp64) return enqueue_t<double>(p, p->gd, n, x, q, f, dq, ev, kind);
+    return enqueue_t<float>(p, p->gf, n, x, q, f, dq, ev, kind);
+}
+
+bool valid_ptr_arg(int64_t n, const void *ptr) { return n == 0 || ptr != nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+const char *pppm_strerror(int s) {
+    switch (s) {
+        case PPPM_OK: return "ok";
+        case PPPM_EINVAL: return "invalid argument";
+        case PPPM_ENOMEM: return "device allocation failed";
+        case PPPM_ECUDA: return "CUDA runtime error";
+        case PPPM_ECUFFT: return "cuFFT error";
+        case PPPM_ENONFINITE: return "non-finite position or charge";
+        case PPPM_ETIMEOUT: return "device wait timed out";
+        case PPPM_ENOTREADY: return "quantity not computed by the last call";
+        default: return "unknown status";
+    }
+}
+
+int pppm_estimate_g(double rel_acc, double r_cut, int64_t n, double q2, const double box[3], double *g_out) {
+    if (!box || !g_out || !(rel_acc > 0) || !(r_cut > 0) || n <= 0 || !(q2 > 0)) return PPPM_EINVAL;
+    if (!(box[0] > 0 && box[1] > 0 && box[2] > 0)) return PPPM_EINVAL;
+    const double V = box[0] * box[1] * box[2];
+    const double arg = rel_acc * std::sqrt((double)n * r_cut * V) / (2.0 * q2);
+    if (!(arg > 0.0 && arg < 1.0)) return PPPM_EINVAL;
+    *g_out = std::sqrt(-std::log(arg)) / r_cut;
+    return PPPM_OK;
+}
+
+int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, const int mesh[3], double g_ewald,
+               int diff_mode, int precision, double qqrd2e, void *cuda_stream) {
+    if (!out) return PPPM_EINVAL;
+    *out = nullptr;
+    if (!box || !mesh || n_max < 0 || n_max > (int64_t)1 << 30) return PPPM_EINVAL;
+    if (order < 2 || order > MAXP) return PPPM_EINVAL;
+    if (!(g_ewald > 0) || !std::isfinite(g_ewald) || !std::isfinite(qqrd2e)) return PPPM_EINVAL;
+    if (diff_mode != PPPM_IK && diff_mode != PPPM_AD) return PPPM_EINVAL;
+    if (precision != PPPM_FP64 && precision != PPPM_FP32C && precision != PPPM_FP32) return PPPM_EINVAL;
+    for (int d = 0; d < 3; ++d) {
+        if (!(box[d] > 0) || !std::isfinite(box[d])) return PPPM_EINVAL;
+        if (mesh[d] < order || mesh[d] > MAX_MESH) return PPPM_EINVAL;  // stencil must fit the mesh
+    }
+    pppm_plan *p = new (std::nothrow) pppm_plan();
+    if (!p) return PPPM_ENOMEM;
+    int rc = PPPM_OK;
+    cudaGetDevice(&p->device);
+    p->stream = (cudaStream_t)cuda_stream;
+    p->P = order;
+    p->mode = diff_mode;
+    p->ik = diff_mode == PPPM_IK;
+    p->prec = precision;
+    p->fp64 = precision == PPPM_FP64;
+    p->comp = precision == PPPM_FP32C;
+    p->g = g_ewald;
+    p->C = qqrd2e;
+    p->n_max = n_max;
+    for (int d = 0; d < 3; ++d) {
+        p->M[d] = mesh[d];
+        p->box[d] = box[d];
+        p->h[d] = box[d] / mesh[d];
+        p->T[d] = (mesh[d] + TILE_B - 1) / TILE_B;
+    }
+    p->Mzh = mesh[2] / 2 + 1;
+    p->Mtot = (int64_t)mesh[0] * mesh[1] * mesh[2];
+    p->Mhalf = (int64_t)mesh[0] * mesh[1] * p->Mzh;
+    p->ntiles = p->T[0] * p->T[1] * p->T[2];
+    p->V = box[0] * box[1] * box[2];
+    p->vcell = p->h[0] * p->h[1] * p->h[2];
+
+    double coef[MAXP][MAXP], dcoef[MAXP][MAXP];
+    stencil_polynomials(order, coef, dcoef);
+    fill_geom<float>(p, p->gf, coef, dcoef);
+    fill_geom<double>(p, p->gd, coef, dcoef);
+
+    const size_t rs = p->fp64 ? 8 : 4;
+    const int64_t nm = std::max<int64_t>(n_max, 1);
+    const int nblk_map = (int)((nm + 255) / 256);
+    const int nblk_green = 152 * 8;
+    do {
+        if ((rc = dmalloc(p, &p->sb.anchor, 4 * nm))) break;
+        if ((rc = dmalloc(p, &p->sb.rank, 4 * nm))) break;
+        if ((rc = dmalloc(p, &p->sb.tile_count, 4 * (size_t)p->ntiles))) break;
+        if ((rc = dmalloc(p, &p->sb.tile_start, 4 * ((size_t)p->ntiles + 1)))) break;
+        if ((rc = dmalloc(p, &p->sb.perm, 4 * nm))) break;
+        if ((rc = dmalloc(p, &p->sb.rec, 4 * rs * nm))) break;
+        if ((rc = dmalloc(p, &p->sb.cell, 4 * nm))) break;
+        if ((rc = dmalloc(p, &p->sb.blk, sizeof(double) * 2 * nblk_map))) break;
+        if ((rc = dmalloc(p, &p->counters, 4 * sizeof(unsigned int)))) break;
+        if ((rc = dmalloc(p, &p->sb.qsum, 2 * sizeof(double)))) break;
+        if ((rc = dmalloc(p, &p->sb.err, 4 * sizeof(int)))) break;
+        if ((rc = dmalloc(p, &p->rho, rs * p->Mtot))) break;
+        if ((rc = dmalloc(p, &p->rho_hat, 2 * rs * p->Mhalf))) break;
+        if ((rc = dmalloc(p, &p->spec, 2 * rs * p->Mhalf * (p->ik ? 3 : 1)))) break;
+        if ((rc = dmalloc(p, &p->field, rs * p->Mtot * (p->ik ? 4 : 1)))) break;
+        if ((rc = dmalloc(p, &p->G64, sizeof(double) * p->Mhalf))) break;
+        if ((rc = dmalloc(p, &p->Gs, rs * p->Mhalf))) break;
+        const size_t len = (size_t)p->M[0] + p->M[1] + p->Mzh;
+        if ((rc = dmalloc(p, &p->kvec, rs * len))) break;
+        if ((rc = dmalloc(p, &p->kdiff, rs * len))) break;
+        if ((rc = dmalloc(p, &p->green_part, sizeof(double) * 7 * nblk_green))) break;
+        if ((rc = dmalloc(p, &p->ev, 8 * sizeof(double)))) break;
+        if ((rc = dmalloc(p, &p->d_sf, 6 * sizeof(double)))) break;
+        if ((rc = dmalloc(p, &p->hx, 3 * rs * nm))) break;
+        if ((rc = dmalloc(p, &p->hq, rs * nm))) break;
+        if ((rc = dmalloc(p, &p->hf, 3 * rs * nm))) break;
+        if ((rc = dmalloc(p, &p->hev, 8 * sizeof(double)))) break;
+    } while (0);
+    if (rc) {
+        release(p);
+        return rc;
+    }
+    p->sb.counter = p->counters;
+    p->gb.G64 = p->G64;
+    p->gb.Gs = p->Gs;
+    p->gb.kvec = p->kvec;
+    p->gb.kdiff = p->kdiff;
+    p->gb.part = p->green_part;
+    p->gb.counter = p->counters + 1;
+    p->gb.qsum = p->sb.qsum;
+    p->gb.ev = p->ev;
+    p->ec.epref = 0.5 * p->C * p->vcell * p->vcell / p->V * (double)p->Mtot;
+    p->ec.inv4g2 = 1.0 / (4.0 * p->g * p->g);
+    p->ec.eself = -p->C * p->g / std::sqrt(M_PI);
+    p->ec.ebg = -p->C * M_PI / (2.0 * p->g * p->g * p->V);
+
+    auto fail = [&](int code) {
+        release(p);
+        return code;
+    };
+    if (cudaMemsetAsync(p->sb.tile_count, 0, 4 * (size_t)p->ntiles, p->stream) != cudaSuccess ||
+        cudaMemsetAsync(p->counters, 0, 4 * sizeof(unsigned int), p->stream) != cudaSuccess ||
+        cudaMemsetAsync(p->sb.err, 0, 4 * sizeof(int), p->stream) != cudaSuccess ||
+        cudaMemsetAsync(p->ev, 0, 8 * sizeof(double), p->stream) != cudaSuccess)
+        return fail(PPPM_ECUDA);
+    cudaError_t pe = p->fp64 ? prepare_make_rho<double>(order, false) : prepare_make_rho<float>(order, p->comp);
+    if (pe != cudaSuccess) return fail(PPPM_ECUDA);
+    if ((rc = build_tables_and_green(p))) return fail(rc);
+    if ((rc = make_ffts(p))) return fail(rc);
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(PPPM_ECUDA);
+    *out = p;
+    return PPPM_OK;
+}
+
+int pppm_destroy(pppm_plan *p) {
+    if (!p) return PPPM_EINVAL;
+    release(p);
+    return PPPM_OK;
+}
+
+int pppm_set_stream(pppm_plan *p, void *cuda_stream) {
+    if (!p) return PPPM_EINVAL;
+    p->stream = (cudaStream_t)cuda_stream;
+    if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+        p->gkey_n = -1;
+    }
+    if (p->have_r2c) CKF(cufftSetStream(p->r2c, p->stream));
+    if (p->have_c2r) CKF(cufftSetStream(p->c2r, p->stream));
+    if (p->have_c2r1) CKF(cufftSetStream(p->c2r1, p->stream));
+    return PPPM_OK;
+}
+
+int pppm_set_graph(pppm_plan *p, int enable) {
+    if (!p) return PPPM_EINVAL;
+    p->graph_on = enable != 0;
+    if (!p->graph_on && p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+        p->gkey_n = -1;
+    }
+    return PPPM_OK;
+}
+
+int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, double *ev) {
+    if (!p || n < 0 || n > p->n_max) return PPPM_EINVAL;
+    if (!valid_ptr_arg(n, x) || !valid_ptr_arg(n, q) || !valid_ptr_arg(n, f)) return PPPM_EINVAL;
+    p->n_last = n;
+    p->field_is_field = true;
+    p->have_rho = true;
+    if (!p->graph_on) return enqueue(p, n, x, q, f, nullptr, ev, 0);
+    const void *key[5] = {x, q, f, ev, nullptr};
+    bool same = p->gexec && p->gkey_n == n && p->gkey_prof == p->prof_on;
+    for (int i = 0; i < 5 && same; ++i) same = key[i] == p->gkey[i];
+    if (!same) {
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue(p, n, x, q, f, nullptr, ev, 0);
+        cudaError_t ee = cudaStreamEndCapture(p->stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        CK(ee);
+        cudaError_t ie = cudaGraphInstantiate(&p->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+        for (int i = 0; i < 5; ++i) p->gkey[i] = key[i];
+        p->gkey_n = n;
+        p->gkey_prof = p->prof_on;
+    }
+    CK(cudaGraphLaunch(p->gexec, p->stream));
+    p->prof_valid = p->prof_on;
+    return PPPM_OK;
+}
+
+int pppm_sync(pppm_plan *p) {
+    if (!p) return PPPM_EINVAL;
+    CK(cudaStreamSynchronize(p->stream));
+    int err = 0;
+    CK(cudaMemcpy(&err, p->sb.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        CK(cudaMemset(p->sb.err, 0, sizeof(int)));
+        return PPPM_ENONFINITE;
+    }
+    return PPPM_OK;
+}
+
+int pppm_compute_host(pppm_plan *p, int64_t n, const void *x_host, const void *q_host, void *f_host,
+                      double *ev_host) {
+    if (!p || n < 0 || n > p->n_max) return PPPM_EINVAL;
+    if (!valid_ptr_arg(n, x_host) || !valid_ptr_arg(n, q_host) || !valid_ptr_arg(n, f_host)) return PPPM_EINVAL;
+    const size_t rs = p->fp64 ? 8 : 4;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(p->hx, x_host, 3 * rs * n, cudaMemcpyHostToDevice, p->stream));
+        CK(cudaMemcpyAsync(p->hq, q_host, rs * n, cudaMemcpyHostToDevice, p->stream));
+    }
+    int rc = pppm_compute(p, n, p->hx, p->hq, p->hf, p->hev);
+    if (rc) return rc;
+    if (n > 0) CK(cudaMemcpyAsync(f_host, p->hf, 3 * rs * n, cudaMemcpyDeviceToHost, p->stream));
+    if (ev_host) CK(cudaMemcpyAsync(ev_host, p->hev, 7 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    return pppm_sync(p);
+}
+
+int pppm_energy_grad(pppm_plan *p, int64_t n, const void *x, const void *q, void *dEdx, void *dEdq, double *ev) {
+    if (!p || n < 0 || n > p->n_max) return PPPM_EINVAL;
+    if (!valid_ptr_arg(n, x) || !valid_ptr_arg(n, q)) return PPPM_EINVAL;
+    p->n_last = n;
+    p->field_is_field = false;
+    p->have_rho = true;
+    return enqueue(p, n, x, q, dEdx, dEdq, ev, 1);
+}
+
+int pppm_get_array(pppm_plan *p, int which, void *dst, size_t bytes, int to_host) {
+    if (!p || !dst) return PPPM_EINVAL;
+    const size_t rs = p->fp64 ? 8 : 4;
+    const cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(cudaStreamSynchronize(p->stream));
+    switch (which) {
+        case PPPM_ARR_RHO:
+            if (bytes != rs * (size_t)p->Mtot) return PPPM_EINVAL;
+            if (!p->have_rho) return PPPM_ENOTREADY;
+            CK(cudaMemcpy(dst, p->rho, bytes, kind));
+            return PPPM_OK;
+        case PPPM_ARR_GREEN:
+            if (bytes != 8 * (size_t)p->Mhalf) return PPPM_EINVAL;
+            CK(cudaMemcpy(dst, p->G64, bytes, kind));
+            return PPPM_OK;
+        case PPPM_ARR_FIELD: {
+            const size_t want = rs * (size_t)p->Mtot * ((p->ik && p->field_is_field) ? 4 : 1);
+            if (bytes != want) return PPPM_EINVAL;
+            if (p->n_last < 0) return PPPM_ENOTREADY;
+            CK(cudaMemcpy(dst, p->field, bytes, kind));
+            return PPPM_OK;
+        }
+        case PPPM_ARR_ANCHOR: {
+            if (p->n_last < 0) return PPPM_ENOTREADY;
+            const int64_t n = p->n_last;
+            if (bytes != 12 * (size_t)n) return PPPM_EINVAL;
+            std::vector<uint32_t> packed(n);
+            std::vector<int32_t> a(3 * n);
+            if (n) CK(cudaMemcpy(packed.data(), p->sb.anchor, 4 * n, cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < n; ++i) {
+                int u, v, w;
+                unpack_anchor(packed[i], u, v, w);
+                a[3 * i] = u;
+                a[3 * i + 1] = v;
+                a[3 * i + 2] = w;
+            }
+            if (n) CK(cudaMemcpy(dst, a.data(), bytes, to_host ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice));
+            return PPPM_OK;
+        }
+        case PPPM_ARR_TILESTART:
+            if (bytes != 4 * ((size_t)p->ntiles + 1)) return PPPM_EINVAL;
+            if (p->n_last < 0) return PPPM_ENOTREADY;
+            CK(cudaMemcpy(dst, p->sb.tile_start, bytes, kind));
+            return PPPM_OK;
+        case PPPM_ARR_PERM:
+            if (p->n_last < 0) return PPPM_ENOTREADY;
+            if (bytes != 4 * (size_t)p->n_last) return PPPM_EINVAL;
+            if (bytes) CK(cudaMemcpy(dst, p->sb.perm, bytes, kind));
+            return PPPM_OK;
+        case PPPM_ARR_SELFFORCE:
+            if (bytes != sizeof(p->sf)) return PPPM_EINVAL;
+            CK(cudaMemcpy(dst, p->sf, bytes, to_host ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice));
+            return PPPM_OK;
+        case PPPM_ARR_ENERGY:
+            if (bytes != 7 * sizeof(double)) return PPPM_EINVAL;
+            CK(cudaMemcpy(dst, p->ev, bytes, kind));
+            return PPPM_OK;
+        default:
+            return PPPM_EINVAL;
+    }
+}
+
+int pppm_set_profiling(pppm_plan *p, int enable) {
+    if (!p) return PPPM_EINVAL;
+    if (enable && !p->prof[0]) {
+        for (auto &e : p->prof) CK(cudaEventCreate(&e));
+    }
+    p->prof_on = enable != 0;
+    p->prof_valid = false;
+    return PPPM_OK;
+}
+
+int pppm_stage_times(pppm_plan *p, float ms[6]) {
+    if (!p || !ms) return PPPM_EINVAL;
+    if (!p->prof_valid || !p->prof[0]) return PPPM_ENOTREADY;
+    CK(cudaEventSynchronize(p->prof[6]));
+    for (int i = 0; i < 6; ++i) CK(cudaEventElapsedTime(&ms[i], p->prof[i], p->prof[i + 1]));
+    return PPPM_OK;
+}
+
+int pppm_plan_info(const pppm_plan *p, int64_t info[10]) {
+    if (!p || !info) return PPPM_EINVAL;
+    info[0] = p->M[0];
+    info[1] = p->M[1];
+    info[2] = p->M[2];
+    info[3] = p->P;
+    info[4] = p->ntiles;
+    info[5] = TILE_B;
+    info[6] = p->mode;
+    info[7] = p->prec;
+    info[8] = p->n_max;
+    info[9] = p->n_last;
+    return PPPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,205 @@
+// Internal definitions shared by the PPPM kernels and the C-ABI layer.
+//
+// Stencil convention (the order-P charge-assignment stencil of Sec. 3.1,
+// "product of three polynomials of order equal to the stencil size"):
+//   u = x_wrapped / h (grid coordinate), anchor n = floor(u + 1/2) for odd P
+//   and floor(u) for even P, delta = n - u.  The P stencil points are
+//   n - rlo + k (k = 0..P-1, rlo = (P-1)/2, wrapped mod M) with weight
+//   W_k(delta) = sum_l coef[k][l] delta^l, the order-P B-spline restricted to
+//   the unit piece that point k sees.
+//
+// Tiles: each mesh dimension of M points is cut into T = ceil(M/B) tiles with
+// boundaries floor(t*M/T); every tile is between floor(M/T) and B points wide,
+// which is >= 4 > rlo for the supported sizes, so a particle only reaches the
+// 27 tiles around the tile of its anchor.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include "../../include/pppm_gb300.h"
+
+namespace pppm {
+
+constexpr int MAXP = 7;
+constexpr int TILE_B = 8;           // tile edge in mesh points
+constexpr int MAX_MESH = 1024;
+
+// ---------------------------------------------------------------------------
+// Geometry and per-order constants passed to kernels by value.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Geom {
+    int M[3];
+    int Mzh;            // Mz/2 + 1
+    int T[3];           // tiles per dimension
+    int ntiles;
+    int P, rlo;
+    R L[3], iL[3];
+    R ih[3];            // 1/h, and its rounding remainder (float path only)
+    R ih_lo[3];
+    R ivcell;           // 1 / (hx hy hz)
+    R h[3];
+    R coef[MAXP][MAXP];   // coef[k][l]: weight of stencil point k, power l of delta
+    R dcoef[MAXP][MAXP];  // d/ddelta of the same polynomials
+};
+
+template <typename R> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_32a; };
+template <typename R> using vec4_t = typename Vec4<R>::type;
+
+template <typename R> struct Complex;
+template <> struct Complex<float> { using type = cufftComplex; };
+template <> struct Complex<double> { using type = cufftDoubleComplex; };
+template <typename R> using complex_t = typename Complex<R>::type;
+
+__host__ __device__ inline int tile_of(int n, int T, int M) { return ((n + 1) * T - 1) / M; }
+__host__ __device__ inline int tile_origin(int t, int T, int M) { return (t * M) / T; }
+
+__host__ __device__ inline uint32_t pack_anchor(int a, int b, int c) {
+    return (uint32_t)a | ((uint32_t)b << 10) | ((uint32_t)c << 20);
+}
+__host__ __device__ inline void unpack_anchor(uint32_t v, int &a, int &b, int &c) {
+    a = (int)(v & 1023u);
+    b = (int)((v >> 10) & 1023u);
+    c = (int)((v >> 20) & 1023u);
+}
+
+// Rounded arithmetic that the compiler may not contract, so that two kernels
+// computing the same anchor from the same position agree bit for bit.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Wrap one coordinate into [0, L) and return the anchor (wrapped to [0, M))
+// and delta = n - u (n unwrapped).  The float path carries 1/h as hi + lo so
+// that delta keeps ~1e-7 absolute accuracy even for u ~ 1000.
+template <typename R>
+__device__ __forceinline__ void grid_anchor(R x, R L, R iL, R ih, R ih_lo, int M, int P,
+                                            int &n_out, R &delta) {
+    R t = floor(mul_rn(x, iL));
+    R xw = fma_rn(-t, L, x);
+    if (xw < R(0)) xw = add_rn(xw, L);
+    if (xw >= L) xw = add_rn(xw, -L);
+    if (xw >= L || xw < R(0)) xw = R(0);
+    R uh = mul_rn(xw, ih);
+    R ul = add_rn(fma_rn(xw, ih, -uh), mul_rn(xw, ih_lo));
+    R nf = (P & 1) ? floor(add_rn(add_rn(uh, R(0.5)), ul)) : floor(add_rn(uh, ul));
+    delta = add_rn(add_rn(nf, -uh), -ul);
+    int n = (int)nf;
+    if (n >= M) n -= M;
+    if (n < 0) n += M;
+    n_out = n;
+}
+
+// Horner evaluation of stencil weight k at delta.
+template <typename R, int P>
+__device__ __forceinline__ R weight(const R (&c)[MAXP][MAXP], int k, R d) {
+    R w = c[k][P - 1];
+#pragma unroll
+    for (int l = P - 2; l >= 0; --l) w = fma_rn(w, d, c[k][l]);
+    return w;
+}
+template <typename R, int P>
+__device__ __forceinline__ R dweight(const R (&c)[MAXP][MAXP], int k, R d) {
+    R w = c[k][P - 2];
+#pragma unroll
+    for (int l = P - 3; l >= 0; --l) w = fma_rn(w, d, c[k][l]);
+    return w;
+}
+
+// Warp reduction of a double (full warp).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side coefficient/table builders (coeffs.cpp): independent exact
+// arithmetic, no device code.
+// ---------------------------------------------------------------------------
+// coef[k][l], dcoef[k][l] of the order-P stencil in delta (see top comment).
+void stencil_polynomials(int P, double coef[MAXP][MAXP], double dcoef[MAXP][MAXP]);
+// M_{2P}(g) for g = 0..P (values at the integers of the order-2P B-spline).
+void spline2p_at_integers(int P, double out[MAXP + 1]);
+// Grid-unit wavenumber of mesh index m (Nyquist index taken as -M/2).
+double grid_kappa(int m, int M);
+// sum_{|m| <= mmax} U1(kappa + 2 pi m) U1(kappa + 2 pi (m - n)), U1 = sinc^P(./2).
+double alias_cross(double kappa, int n, int P, int mmax);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (one per .cu file), all enqueue on `s`.
+// ---------------------------------------------------------------------------
+struct SortBufs {
+    uint32_t *anchor;      // [n] packed wrapped anchor, input order
+    int *rank;             // [n] rank within its tile
+    int *tile_count;       // [ntiles], zero between steps
+    int *tile_start;       // [ntiles + 1]
+    int *perm;             // [n] sorted -> input index
+    void *rec;             // [n] vec4 (delta_x, delta_y, delta_z, q/vcell or q), sorted
+    uint32_t *cell;        // [n] packed anchor, sorted
+    double *blk;           // [2 * nblk] per-block sum q, sum q^2
+    unsigned int *counter; // [1] last-block ticket
+    double *qsum;          // [2] sum q, sum q^2
+    int *err;              // [1] device error word
+};
+
+template <typename R>
+void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const SortBufs &b,
+                 cudaStream_t s);
+
+template <typename R>
+cudaError_t prepare_make_rho(int P, bool compensated);  // once per process/device, before capture
+template <typename R>
+void launch_make_rho(const Geom<R> &g, int64_t n, const SortBufs &b, R *rho, bool compensated,
+                     cudaStream_t s);
+
+struct GreenBufs {
+    const double *G64;     // [Mx*My*Mzh] unscaled G
+    const void *Gs;        // [Mx*My*Mzh] G / M in the step type
+    const void *kvec;      // [Mx + My + Mzh] wavenumbers (step type), Nyquist negative
+    const void *kdiff;     // same with the Nyquist entries zeroed (ik differentiation)
+    double *part;          // [7 * nblk] per-block partial energy/virial
+    unsigned int *counter; // [1]
+    const double *qsum;    // [2]
+    double *ev;            // [8] energy + virial
+};
+struct EnergyConsts {
+    double epref;  // (C/2) vcell^2 / V * M  (energy of sum w Gs |rho_hat|^2)
+    double inv4g2;
+    double eself;  // -C g / sqrt(pi), times sum q^2
+    double ebg;    // -C pi / (2 g^2 V), times Q^2
+};
+
+template <typename R>
+void launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec,
+                  const GreenBufs &b, const EnergyConsts &ec, double *ev_user, cudaStream_t s);
+
+template <typename R>
+void launch_fieldforce(const Geom<R> &g, bool ik, int64_t n, const SortBufs &b, const R *field,
+                       R *f, R qC, const double *sf_coeff, cudaStream_t s);
+
+template <typename R>
+void launch_energy_grad(const Geom<R> &g, int64_t n, const SortBufs &b, const R *phi, R *dEdx,
+                        R *dEdq, R C, const double *qsum, double gself, double gbg,
+                        cudaStream_t s);
+
+// Setup: G(k) in FP64 over the half spectrum and the ad self-force sums.
+struct GreenSetup {
+    int M[3], Mzh, P;
+    bool ik;
+    double h[3], g;
+    const double *ktab;    // [Mx + My + Mzh] FP64 wavenumbers (Nyquist negative)
+    const double *atab;    // [5][Mx + My + Mzh] exp(-km^2/4g^2) U^2(km) for alias m = -2..2
+    const double *dtab;    // [Mx + My + Mzh] per-dimension denominator sum U^2
+    const double *btab;    // [3 n][Mx + My + Mzh] self-force alias sums, n = 0,1,2
+};
+void launch_green_setup(const GreenSetup &gs, double *G64, double *sf_sums, cudaStream_t s);
+
+}  // namespace pppm

@@ -1,0 +1,231 @@
+"""Python binding of the C ABI in include/pppm_gb300.h (argument marshalling only).
+
+Every step of the k-space path runs in the CUDA library; this module passes
+raw device pointers of torch tensors and the current CUDA stream.  It raises
+if the library has not been built -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpppm_gb300.so")
+
+PPPM_OK, PPPM_EINVAL, PPPM_ENOMEM, PPPM_ECUDA, PPPM_ECUFFT, PPPM_ENONFINITE, PPPM_ETIMEOUT, PPPM_ENOTREADY = range(8)
+MODES = {"ik": 0, "ad": 1}
+PRECISIONS = {"fp64": 0, "fp32c": 1, "fp32": 2}
+ARRAYS = {"rho": 0, "green": 1, "field": 2, "anchor": 3, "tilestart": 4, "perm": 5, "selfforce": 6, "energy": 7}
+
+_lib = None
+
+
+class PPPMError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} (status {status})")
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run python -m paper_1702_04250_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        dptr = ctypes.POINTER(ctypes.c_double)
+        L.pppm_strerror.restype = ctypes.c_char_p
+        L.pppm_strerror.argtypes = [i32]
+        L.pppm_estimate_g.argtypes = [dbl, dbl, i64, dbl, dptr, dptr]
+        L.pppm_setup.argtypes = [ctypes.POINTER(vp), dptr, i64, i32, ctypes.POINTER(i32), dbl, i32, i32, dbl, vp]
+        L.pppm_destroy.argtypes = [vp]
+        L.pppm_set_stream.argtypes = [vp, vp]
+        L.pppm_set_graph.argtypes = [vp, i32]
+        L.pppm_compute.argtypes = [vp, i64, vp, vp, vp, vp]
+        L.pppm_compute_host.argtypes = [vp, i64, vp, vp, vp, vp]
+        L.pppm_sync.argtypes = [vp]
+        L.pppm_energy_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.pppm_get_array.argtypes = [vp, i32, vp, ctypes.c_size_t, i32]
+        L.pppm_plan_info.argtypes = [vp, ctypes.POINTER(i64)]
+        L.pppm_set_profiling.argtypes = [vp, i32]
+        L.pppm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        for name in ("pppm_estimate_g", "pppm_setup", "pppm_destroy", "pppm_set_stream", "pppm_set_graph",
+                     "pppm_compute", "pppm_compute_host", "pppm_sync", "pppm_energy_grad", "pppm_get_array",
+                     "pppm_plan_info", "pppm_set_profiling", "pppm_stage_times"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().pppm_strerror(int(status)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != PPPM_OK:
+        raise PPPMError(rc, what)
+
+
+def _d3(v):
+    return (ctypes.c_double * 3)(*[float(a) for a in v])
+
+
+def estimate_g(rel_acc: float, r_cut: float, n: int, q2: float, box) -> float:
+    out = ctypes.c_double()
+    _check(lib().pppm_estimate_g(float(rel_acc), float(r_cut), int(n), float(q2), _d3(box), ctypes.byref(out)),
+           "pppm_estimate_g")
+    return out.value
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else int(t.data_ptr()))
+
+
+class PPPM:
+    """One plan: box, order, mesh, g_ewald, differentiation mode, precision."""
+
+    def __init__(self, box, n_max, order, mesh, g_ewald, mode="ik", precision="fp32c", qqrd2e=1.0,
+                 stream=None, graph=False, device=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.box = tuple(float(b) for b in box)
+        self.mesh = tuple(int(m) for m in mesh)
+        self.order = int(order)
+        self.g_ewald = float(g_ewald)
+        self.mode = mode
+        self.precision = precision
+        self.qqrd2e = float(qqrd2e)
+        self.n_max = int(n_max)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        if stream is None:
+            stream = torch.cuda.Stream(device=self.device) if graph else torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().pppm_setup(ctypes.byref(h), _d3(box), self.n_max, self.order,
+                                    (ctypes.c_int * 3)(*self.mesh), self.g_ewald, MODES[mode],
+                                    PRECISIONS[precision], self.qqrd2e, ctypes.c_void_p(stream.cuda_stream)),
+                   "pppm_setup")
+        self._h = h
+        self.ev = torch.zeros(8, dtype=torch.float64, device=self.device)
+        if graph:
+            _check(lib().pppm_set_graph(self._h, 1), "pppm_set_graph")
+
+    # -- lifetime -------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pppm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        a = (ctypes.c_int64 * 10)()
+        _check(lib().pppm_plan_info(self._h, a), "pppm_plan_info")
+        keys = ("Mx", "My", "Mz", "order", "ntiles", "tile", "mode", "precision", "n_max", "n_last")
+        return dict(zip(keys, list(a)))
+
+    # -- compute --------------------------------------------------------
+    def _prep(self, x, q):
+        torch = self.torch
+        x = torch.as_tensor(x, device=self.device, dtype=self.dtype).contiguous()
+        q = torch.as_tensor(q, device=self.device, dtype=self.dtype).contiguous()
+        if x.dim() != 2 or x.shape[1] != 3 or q.shape != (x.shape[0],):
+            raise ValueError("x must be [n, 3] and q [n]")
+        return x, q
+
+    def compute(self, x, q, f=None, ev=None):
+        """Forces [n, 3] and the 7 energy/virial doubles (device tensors)."""
+        x, q = self._prep(x, q)
+        n = x.shape[0]
+        if f is None:
+            f = self.torch.empty((n, 3), dtype=self.dtype, device=self.device)
+        if ev is None:
+            ev = self.ev
+        _check(lib().pppm_compute(self._h, n, _ptr(x), _ptr(q), _ptr(f), _ptr(ev)), "pppm_compute")
+        return f, ev[:7]
+
+    def compute_host(self, x, q):
+        """Host arrays in, host arrays out (copies inside the call)."""
+        npdt = np.float64 if self.precision == "fp64" else np.float32
+        x = np.ascontiguousarray(x, dtype=npdt)
+        q = np.ascontiguousarray(q, dtype=npdt)
+        f = np.empty_like(x)
+        ev = np.zeros(7, dtype=np.float64)
+        rc = lib().pppm_compute_host(self._h, x.shape[0], x.ctypes.data_as(ctypes.c_void_p),
+                                     q.ctypes.data_as(ctypes.c_void_p), f.ctypes.data_as(ctypes.c_void_p),
+                                     ev.ctypes.data_as(ctypes.c_void_p))
+        _check(rc, "pppm_compute_host")
+        return f, ev
+
+    def compute_host_into(self, n, x_ptr, q_ptr, f_ptr, ev_ptr):
+        """pppm_compute_host on caller-provided host pointers (e.g. pinned tensors)."""
+        rc = lib().pppm_compute_host(self._h, int(n), ctypes.c_void_p(x_ptr), ctypes.c_void_p(q_ptr),
+                                     ctypes.c_void_p(f_ptr), ctypes.c_void_p(ev_ptr))
+        _check(rc, "pppm_compute_host")
+
+    def energy_grad(self, x, q):
+        """(dE/dx [n, 3], dE/dq [n], energy/virial) of the PPPM energy."""
+        x, q = self._prep(x, q)
+        n = x.shape[0]
+        dx = self.torch.empty((n, 3), dtype=self.dtype, device=self.device)
+        dq = self.torch.empty((n,), dtype=self.dtype, device=self.device)
+        _check(lib().pppm_energy_grad(self._h, n, _ptr(x), _ptr(q), _ptr(dx), _ptr(dq), _ptr(self.ev)),
+               "pppm_energy_grad")
+        return dx, dq, self.ev[:7]
+
+    STAGES = ("sort", "make_rho", "fft_fwd", "green", "fft_inv", "fieldforce")
+
+    def set_profiling(self, enable: bool = True):
+        _check(lib().pppm_set_profiling(self._h, int(bool(enable))), "pppm_set_profiling")
+
+    def stage_times(self) -> dict:
+        a = (ctypes.c_float * 6)()
+        _check(lib().pppm_stage_times(self._h, a), "pppm_stage_times")
+        return dict(zip(self.STAGES, [float(v) for v in a]))
+
+    def sync(self):
+        _check(lib().pppm_sync(self._h), "pppm_sync")
+
+    def sync_status(self) -> int:
+        return int(lib().pppm_sync(self._h))
+
+    # -- inspection -----------------------------------------------------
+    def get_array(self, name: str) -> np.ndarray:
+        inf = self.info()
+        Mx, My, Mz = inf["Mx"], inf["My"], inf["Mz"]
+        rdt = np.float64 if self.precision == "fp64" else np.float32
+        n = inf["n_last"]
+        if name == "rho":
+            out = np.empty((Mx, My, Mz), dtype=rdt)
+        elif name == "green":
+            out = np.empty((Mx, My, Mz // 2 + 1), dtype=np.float64)
+        elif name == "field":
+            out = np.empty((Mx, My, Mz, 4), dtype=rdt) if self.mode == "ik" else np.empty((Mx, My, Mz), dtype=rdt)
+        elif name == "phi":
+            out = np.empty((Mx, My, Mz), dtype=rdt)
+            name = "field"
+        elif name == "anchor":
+            out = np.empty((max(n, 0), 3), dtype=np.int32)
+        elif name == "tilestart":
+            out = np.empty(inf["ntiles"] + 1, dtype=np.int32)
+        elif name == "perm":
+            out = np.empty(max(n, 0), dtype=np.int32)
+        elif name == "selfforce":
+            out = np.empty((3, 2), dtype=np.float64)
+        elif name == "energy":
+            out = np.empty(7, dtype=np.float64)
+        else:
+            raise KeyError(name)
+        _check(lib().pppm_get_array(self._h, ARRAYS[name], out.ctypes.data_as(ctypes.c_void_p), out.nbytes, 1),
+               f"pppm_get_array({name})")
+        return out

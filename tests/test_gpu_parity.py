@@ -1,0 +1,304 @@
+"""GPU path vs the FP64 oracle, through the C ABI.
+
+Tolerances (relative RMS for forces, relative for energy, norm-relative for
+the virial): FP64 1e-6, FP32 / FP32C 1e-4.  Integer outputs (stencil anchors,
+the sort) are compared exactly; where several orders are valid (particles of
+one tile) only validity is checked.  FP32 runs feed the oracle the same
+float32-rounded inputs, so the comparison measures the arithmetic only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import (OraclePPPM, estimate_g_ewald, influence_ad, influence_ik, make_rho, poisson_ad,
+                    poisson_ik, stencil, wrap_positions)
+from paper_1702_04250_gb300.workloads import batch_systems, config, uniform_alternating, water_like
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-6, "fp32c": 1e-4, "fp32": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_04250_gb300 import build
+
+    build.build()
+    return t
+
+
+def rel_rms(a, b):
+    return math.sqrt(float(np.sum((a - b) ** 2)) / max(float(np.sum(b ** 2)), 1e-300))
+
+
+def g_of(w):
+    return estimate_g_ewald(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
+
+
+def run(torch, box, mesh, order, g, mode, prec, x, q, C=1.0, **kw):
+    from paper_1702_04250_gb300 import pppm
+
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = pppm.PPPM(box, max(len(q), 1), order, mesh, g, mode=mode, precision=prec, qqrd2e=C, **kw)
+    xt = torch.tensor(np.asarray(x), dtype=dt, device="cuda")
+    qt = torch.tensor(np.asarray(q), dtype=dt, device="cuda")
+    f, ev = plan.compute(xt, qt)
+    plan.sync()
+    return plan, f.double().cpu().numpy(), ev.cpu().numpy().copy()
+
+
+def oracle_inputs(x, q, prec):
+    if prec == "fp64":
+        return np.asarray(x, np.float64), np.asarray(q, np.float64)
+    return np.asarray(x, np.float32).astype(np.float64), np.asarray(q, np.float32).astype(np.float64)
+
+
+def check_all(f, ev, ref, prec, label=""):
+    tol = TOL[prec]
+    ferr = rel_rms(f, ref["f"])
+    eerr = abs(ev[0] - ref["energy"]) / abs(ref["energy"])
+    verr = np.linalg.norm(ev[1:7] - ref["virial"]) / np.linalg.norm(ref["virial"])
+    print(f"{label} {prec}: force {ferr:.2e} energy {eerr:.2e} virial {verr:.2e}")
+    assert ferr <= tol, ferr
+    assert eerr <= tol, eerr
+    assert verr <= tol, verr
+    return ferr, eerr, verr
+
+
+# ---------------------------------------------------------------------------
+# stage by stage, FP64, c1 (16^3 mesh = 2x2x2 tiles)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c1_fp64_ik(torch):
+    w = config("c1")
+    g = g_of(w)
+    plan, f, ev = run(torch, w.box, w.mesh, w.order, g, "ik", "fp64", w.x, w.q, w.qqrd2e)
+    o = OraclePPPM(w.box, w.mesh, w.order, g, "ik", w.qqrd2e)
+    ref = o.compute(w.x, w.q, keep=True)
+    return w, g, plan, f, ev, o, ref
+
+
+def test_anchor_and_sort(c1_fp64_ik):
+    w, g, plan, *_ = c1_fp64_ik
+    h = np.array(w.box) / np.array(w.mesh)
+    u = wrap_positions(w.x, w.box) / h
+    ref = np.stack([stencil(u[:, d], w.order, w.mesh[d])[0][:, (w.order - 1) // 2] for d in range(3)], axis=1)
+    got = plan.get_array("anchor")
+    np.testing.assert_array_equal(got, ref)
+    perm = plan.get_array("perm")
+    assert np.array_equal(np.sort(perm), np.arange(w.n))
+    ts = plan.get_array("tilestart")
+    assert ts[0] == 0 and ts[-1] == w.n and np.all(np.diff(ts) >= 0)
+    inf = plan.info()
+    T = [(m + inf["tile"] - 1) // inf["tile"] for m in w.mesh]
+    tile = lambda a, d: ((a + 1) * T[d] - 1) // w.mesh[d]
+    tid = (tile(ref[:, 0], 0) * T[1] + tile(ref[:, 1], 1)) * T[2] + tile(ref[:, 2], 2)
+    sorted_tiles = tid[perm]
+    owner = np.repeat(np.arange(len(ts) - 1), np.diff(ts))
+    np.testing.assert_array_equal(sorted_tiles, owner)
+
+
+def test_rho_green_field(c1_fp64_ik):
+    w, g, plan, f, ev, o, ref = c1_fp64_ik
+    rho = plan.get_array("rho")
+    assert np.abs(rho - ref["rho"]).max() <= 1e-12 * np.abs(ref["rho"]).max()
+    G = plan.get_array("green")
+    assert np.abs(G - o.G).max() <= 1e-12 * np.abs(o.G).max()
+    E = plan.get_array("field")
+    for a in range(3):
+        assert np.abs(E[..., a] - ref["fields"][a]).max() <= 1e-10 * np.abs(ref["fields"][a]).max()
+
+
+def test_c1_fp64_ik_end_to_end(c1_fp64_ik):
+    w, g, plan, f, ev, o, ref = c1_fp64_ik
+    ferr, eerr, verr = check_all(f, ev, ref, "fp64", "c1 ik")
+    assert ferr < 1e-10  # FP64 should agree to round-off
+
+
+def test_c1_fp64_ad_stages(torch):
+    w = config("c1")
+    g = g_of(w)
+    plan, f, ev = run(torch, w.box, w.mesh, w.order, g, "ad", "fp64", w.x, w.q, w.qqrd2e)
+    o = OraclePPPM(w.box, w.mesh, w.order, g, "ad", w.qqrd2e)
+    ref = o.compute(w.x, w.q, keep=True)
+    G = plan.get_array("green")
+    assert np.abs(G - o.G).max() <= 1e-12 * np.abs(o.G).max()
+    sf = plan.get_array("selfforce")
+    np.testing.assert_allclose(sf, o.sf, rtol=1e-9, atol=1e-12 * np.abs(o.sf).max())
+    phi = plan.get_array("phi")
+    assert np.abs(phi - ref["phi"]).max() <= 1e-10 * np.abs(ref["phi"]).max()
+    ferr, *_ = check_all(f, ev, ref, "fp64", "c1 ad")
+    assert ferr < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# the water-like 64^3 system (512 tiles), both modes, all precisions
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c2_refs():
+    w = config("c2")
+    g = g_of(w)
+    refs = {}
+    for mode in ("ik", "ad"):
+        o = OraclePPPM(w.box, w.mesh, w.order, g, mode, w.qqrd2e)
+        refs[(mode, "fp64")] = o.compute(w.x, w.q)
+        x32, q32 = oracle_inputs(w.x, w.q, "fp32")
+        refs[(mode, "fp32")] = o.compute(x32, q32)
+    return w, g, refs
+
+
+@pytest.mark.parametrize("mode", ["ik", "ad"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32"])
+def test_c2_parity(torch, c2_refs, mode, prec):
+    w, g, refs = c2_refs
+    plan, f, ev = run(torch, w.box, w.mesh, w.order, g, mode, prec, w.x, w.q, w.qqrd2e)
+    ref = refs[(mode, "fp64" if prec == "fp64" else "fp32")]
+    check_all(f, ev, ref, prec, f"c2 {mode}")
+
+
+def test_fp32c_is_not_worse_than_fp32(torch, c2_refs):
+    w, g, refs = c2_refs
+    ref = refs[("ik", "fp32")]
+    errs = {}
+    for prec in ("fp32", "fp32c"):
+        plan, f, ev = run(torch, w.box, w.mesh, w.order, g, "ik", prec, w.x, w.q, w.qqrd2e)
+        plan.compute(torch.tensor(w.x, dtype=torch.float32, device="cuda"),
+                     torch.tensor(w.q, dtype=torch.float32, device="cuda"))
+        rho = plan.get_array("rho").astype(np.float64)
+        rref = make_rho(*oracle_inputs(w.x, w.q, "fp32"), w.box, w.mesh, w.order)
+        errs[prec] = np.sqrt(np.mean((rho - rref) ** 2)) / np.sqrt(np.mean(rref ** 2))
+    print("mesh rho rel RMS", errs)
+    assert errs["fp32c"] <= errs["fp32"] * 1.05
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("P", [2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("mode", ["ik", "ad"])
+def test_orders_on_ragged_mesh(torch, P, mode):
+    """Non-cubic box, mesh 20 x 17 x 12 (uneven tiles, odd Mz/2+1 handling),
+    positions partly outside the box, a non-neutral charge set."""
+    r = np.random.default_rng(100 + P)
+    box = (13.0, 11.5, 9.0)
+    mesh = (20, 17, 12)
+    n = 700
+    x = r.uniform(-5.0, 20.0, (n, 3))
+    q = r.normal(size=n)
+    g = 0.55
+    plan, f, ev = run(torch, box, mesh, P, g, mode, "fp64", x, q, 2.0)
+    ref = OraclePPPM(box, mesh, P, g, mode, 2.0).compute(x, q)
+    check_all(f, ev, ref, "fp64", f"P={P} {mode}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_tiny_and_degenerate(torch, prec):
+    box, mesh, P, g = (10.0, 10.0, 10.0), (8, 8, 8), 7, 0.6
+    # mesh 8 with P=7: the stencil nearly wraps onto itself; single tile
+    for n in (1, 2, 5):
+        r = np.random.default_rng(n)
+        x = r.uniform(0, 10, (n, 3))
+        q = np.ones(n) if n == 1 else r.normal(size=n)
+        for mode in ("ik", "ad"):
+            plan, f, ev = run(torch, box, mesh, P, g, mode, prec, x, q)
+            xo, qo = oracle_inputs(x, q, prec)
+            ref = OraclePPPM(box, mesh, P, g, mode, 1.0).compute(xo, qo)
+            tol = TOL[prec]
+            # a lone charge in ik feels no force: compare absolutely
+            scale = max(np.abs(ref["f"]).max(), 1e-3)
+            assert np.abs(f - ref["f"]).max() <= tol * scale * 10
+            assert abs(ev[0] - ref["energy"]) <= tol * abs(ref["energy"])
+
+
+def test_empty_input(torch):
+    from paper_1702_04250_gb300 import pppm
+
+    plan = pppm.PPPM((10.0, 10.0, 10.0), 16, 5, (16, 16, 16), 0.4, mode="ik", precision="fp64")
+    x = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    q = torch.zeros((0,), dtype=torch.float64, device="cuda")
+    f, ev = plan.compute(x, q)
+    plan.sync()
+    assert f.shape == (0, 3)
+    assert np.all(ev.cpu().numpy() == 0.0)
+
+
+def test_nonfinite_input_reports_status(torch):
+    from paper_1702_04250_gb300 import pppm
+
+    plan = pppm.PPPM((10.0, 10.0, 10.0), 16, 5, (16, 16, 16), 0.4, mode="ik", precision="fp32c")
+    x = torch.rand((16, 3), device="cuda") * 10
+    x[3, 1] = float("nan")
+    q = torch.ones(16, device="cuda")
+    plan.compute(x, q)
+    assert plan.sync_status() == pppm.PPPM_ENONFINITE
+    # the error word is cleared and the plan stays usable
+    x[3, 1] = 1.0
+    f, ev = plan.compute(x, q)
+    assert plan.sync_status() == pppm.PPPM_OK
+    assert torch.isfinite(f).all()
+
+
+def test_n_above_plan_capacity_is_rejected(torch):
+    from paper_1702_04250_gb300 import pppm
+
+    plan = pppm.PPPM((10.0, 10.0, 10.0), 4, 5, (16, 16, 16), 0.4)
+    x = torch.rand((8, 3), device="cuda")
+    with pytest.raises(pppm.PPPMError):
+        plan.compute(x, torch.ones(8, device="cuda"))
+
+
+def test_graph_mode_and_host_path_match(torch, c2_refs):
+    w, g, refs = c2_refs
+    from paper_1702_04250_gb300 import pppm
+
+    x = torch.tensor(w.x, dtype=torch.float32, device="cuda")
+    q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
+    plain = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, "ik", "fp32c", w.qqrd2e)
+    f0, ev0 = plain.compute(x, q)
+    plain.sync()
+    graph = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, "ik", "fp32c", w.qqrd2e, graph=True)
+    for _ in range(3):
+        f1, ev1 = graph.compute(x, q)
+    graph.sync()
+    assert rel_rms(f1.double().cpu().numpy(), f0.double().cpu().numpy()) < 1e-5
+    fh, evh = plain.compute_host(w.x.astype(np.float32), w.q.astype(np.float32))
+    assert rel_rms(fh.astype(np.float64), f0.double().cpu().numpy()) < 1e-5
+    check_all(fh.astype(np.float64), evh, refs[("ik", "fp32")], "fp32c", "c2 host path")
+
+
+def test_fp64_repeatable(torch, c2_refs):
+    w, g, refs = c2_refs
+    outs = []
+    for _ in range(3):
+        _, f, ev = run(torch, w.box, w.mesh, w.order, g, "ad", "fp64", w.x, w.q, w.qqrd2e)
+        outs.append((f, ev))
+    for f, ev in outs[1:]:
+        assert rel_rms(f, outs[0][0]) < 1e-12
+        assert abs(ev[0] - outs[0][1][0]) < 1e-12 * abs(outs[0][1][0])
+
+
+# ---------------------------------------------------------------------------
+# energy gradients (the autograd backward)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["ik", "ad"])
+def test_energy_gradients_match_oracle(torch, mode):
+    r = np.random.default_rng(7)
+    box, mesh, P, g = (12.0, 12.0, 12.0), (16, 16, 16), 5, 0.45
+    n = 500
+    x = r.uniform(0, 12, (n, 3))
+    q = r.normal(size=n)
+    from paper_1702_04250_gb300 import pppm
+
+    plan = pppm.PPPM(box, n, P, mesh, g, mode=mode, precision="fp64", qqrd2e=3.0)
+    dx, dq, ev = plan.energy_grad(torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda"))
+    plan.sync()
+    o = OraclePPPM(box, mesh, P, g, mode, 3.0)
+    rdx, rdq = o.energy_gradients(x, q)
+    assert rel_rms(dx.cpu().numpy(), rdx) < 1e-10
+    assert rel_rms(dq.cpu().numpy(), rdq) < 1e-10
+    assert abs(ev[0].item() - o.compute(x, q)["energy"]) < 1e-10 * abs(ev[0].item())
