@@ -83,15 +83,17 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce(Geom<R> g, SortBufs b
     R e0 = 0, e1 = 0, e2 = 0, e3 = 0;
     if (live && k < P) {
         const int iz = wrap1(az - g.rlo + k, Mz);
+        int yoff[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) yoff[c] = wrap1(ay - g.rlo + c, My) * Mz + iz;
 #pragma unroll
         for (int a = 0; a < P; ++a) {
-            const int ix = wrap1(ax - g.rlo + a, g.M[0]);
+            const int xoff = wrap1(ax - g.rlo + a, g.M[0]) * (My * Mz);
 #pragma unroll
             for (int c = 0; c < P; ++c) {
-                const int iy = wrap1(ay - g.rlo + c, My);
-                const int64_t p = ((int64_t)ix * My + iy) * Mz + iz;
+                const int p = xoff + yoff[c];
                 if (MODE == 0) {
-                    const vec4_t<R> v = ld4(field + 4 * p);
+                    const vec4_t<R> v = ld4(field + 4 * (int64_t)p);
                     const R w = wx[a] * wy[c];
                     e0 += w * v.x;
                     e1 += w * v.y;

@@ -17,7 +17,8 @@
 // place of R):  E = (C/2) vcell^2/V sum_k G|rho_hat|^2 over the full
 // spectrum, W_ab = same sum times [delta_ab - 2(1 + k^2/4g^2) k_a k_b / k^2].
 // Per-thread sums are taken in the step's type, combined in FP64 with warp
-// shuffles, and the last CTA reduces the per-CTA partials in a fixed order.
+// shuffles; one small kernel reduces the per-CTA partials in a fixed order
+// (on a side branch of the step graph, off the critical path).
 #include "pppm_common.cuh"
 
 namespace pppm {
@@ -111,101 +112,132 @@ void launch_green_setup(const GreenSetup &gs, double *G64, double *sf_sums, cuda
 template <typename R, bool IK>
 __global__ void __launch_bounds__(GREEN_THREADS) k_green(Geom<R> g, const complex_t<R> *__restrict__ rhat,
                                                          complex_t<R> *__restrict__ spec, GreenBufs b,
-                                                         EnergyConsts ec, double *ev_user) {
+                                                         EnergyConsts ec) {
     __shared__ double sh[7][GREEN_THREADS / 32];
-    __shared__ bool last;
     const int Mx = g.M[0], My = g.M[1], Mzh = g.Mzh;
-    const int64_t total = (int64_t)Mx * My * Mzh;
+    const int rows = Mx * My;
+    const int total = rows * Mzh;
     const R *__restrict__ Gs = reinterpret_cast<const R *>(b.Gs);
     const R *__restrict__ kv = reinterpret_cast<const R *>(b.kvec);
     const R *__restrict__ kd = reinterpret_cast<const R *>(b.kdiff);
     const bool evenz = (2 * (Mzh - 1) == g.M[2]);
     const R i4g2 = (R)ec.inv4g2;
+    const int lane = threadIdx.x & 31;
+    const int wrow = threadIdx.x >> 5;
     R acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int iz = (int)(e % Mzh);
-        const int iy = (int)((e / Mzh) % My);
-        const int ix = (int)(e / ((int64_t)Mzh * My));
-        const complex_t<R> r = rhat[e];
-        const R G = Gs[e];
-        const R pr = G * r.x, pi = G * r.y;
-        if (IK) {
-            // E_a = -i k_a G rho_hat / M  ->  (k_a pi, -k_a pr)
-            const R kx = kd[ix], ky = kd[Mx + iy], kz = kd[Mx + My + iz];
-            complex_t<R> o;
-            o.x = kx * pi; o.y = -kx * pr; spec[e] = o;
-            o.x = ky * pi; o.y = -ky * pr; spec[total + e] = o;
-            o.x = kz * pi; o.y = -kz * pr; spec[2 * total + e] = o;
-        } else {
-            complex_t<R> o;
-            o.x = pr; o.y = pi;
-            spec[e] = o;
+    // one thread per spectrum element in z-rows: row = (kx, ky), lanes along kz
+    const int zlanes = (Mzh >= 32) ? 32 : Mzh;
+    const int rows_per_cta = GREEN_THREADS / 32;
+    for (int row = blockIdx.x * rows_per_cta + wrow; row < rows; row += gridDim.x * rows_per_cta) {
+        const int ix = row / My, iy = row - ix * My;
+        const R kx = kv[ix], ky = kv[Mx + iy];
+        const R dkx = kd[ix], dky = kd[Mx + iy];
+        const R kxy2 = kx * kx + ky * ky;
+        for (int iz = lane; iz < Mzh && lane < zlanes; iz += 32) {
+            const int e = row * Mzh + iz;
+            const complex_t<R> r = rhat[e];
+            const R G = Gs[e];
+            const R pr = G * r.x, pi = G * r.y;
+            if (IK) {
+                // E_a = -i k_a G rho_hat / M  ->  (k_a pi, -k_a pr)
+                const R dkz = kd[Mx + My + iz];
+                complex_t<R> o;
+                o.x = dkx * pi; o.y = -dkx * pr; spec[e] = o;
+                o.x = dky * pi; o.y = -dky * pr; spec[total + e] = o;
+                o.x = dkz * pi; o.y = -dkz * pr; spec[2 * total + e] = o;
+            } else {
+                complex_t<R> o;
+                o.x = pr; o.y = pi;
+                spec[e] = o;
+            }
+            const R w = (iz == 0 || (evenz && iz == Mzh - 1)) ? R(1) : R(2);
+            const R s = w * G * (r.x * r.x + r.y * r.y);
+            const R kz = kv[Mx + My + iz];
+            const R k2 = kxy2 + kz * kz;
+            const R fac = (k2 > R(0)) ? R(2) * (R(1) + k2 * i4g2) / k2 : R(0);
+            const R sf = s * fac;
+            acc[0] += s;
+            acc[1] += s - sf * kx * kx;
+            acc[2] += s - sf * ky * ky;
+            acc[3] += s - sf * kz * kz;
+            acc[4] -= sf * kx * ky;
+            acc[5] -= sf * kx * kz;
+            acc[6] -= sf * ky * kz;
         }
-        const R w = (iz == 0 || (evenz && iz == Mzh - 1)) ? R(1) : R(2);
-        const R s = w * G * (r.x * r.x + r.y * r.y);
-        const R kx = kv[ix], ky = kv[Mx + iy], kz = kv[Mx + My + iz];
-        const R k2 = kx * kx + ky * ky + kz * kz;
-        const R fac = (k2 > R(0)) ? R(2) * (R(1) + k2 * i4g2) / k2 : R(0);
-        const R sf = s * fac;
-        acc[0] += s;
-        acc[1] += s - sf * kx * kx;
-        acc[2] += s - sf * ky * ky;
-        acc[3] += s - sf * kz * kz;
-        acc[4] -= sf * kx * ky;
-        acc[5] -= sf * kx * kz;
-        acc[6] -= sf * ky * kz;
     }
     for (int c = 0; c < 7; ++c) {
-        const double v = warp_sum((double)acc[c]);
-        if ((threadIdx.x & 31) == 0) sh[c][threadIdx.x >> 5] = v;
+        const R v = warp_sum_t<R>(acc[c]);
+        if (lane == 0) sh[c][wrow] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < 7) {
         double v = 0.0;
         for (int w = 0; w < GREEN_THREADS / 32; ++w) v += sh[threadIdx.x][w];
         b.part[7 * blockIdx.x + threadIdx.x] = v;
-        __threadfence();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned int ticket = atomicAdd(b.counter, 1u);
-        last = (ticket == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (threadIdx.x < 7) {
-        double v = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) v += __ldcg(&b.part[7 * k + threadIdx.x]);
-        v *= ec.epref;
-        if (threadIdx.x == 0) {
-            const double Q = __ldcg(&b.qsum[0]), Q2 = __ldcg(&b.qsum[1]);
-            v += ec.eself * Q2 + ec.ebg * Q * Q;
-        }
-        b.ev[threadIdx.x] = v;
-        if (ev_user) ev_user[threadIdx.x] = v;
-    }
-    if (threadIdx.x == 0) *b.counter = 0u;
 }
 
 template <typename R>
-void launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec, const GreenBufs &b,
-                  const EnergyConsts &ec, double *ev_user, cudaStream_t s) {
-    const int64_t total = (int64_t)g.M[0] * g.M[1] * g.Mzh;
-    int nb = (int)std::min<int64_t>((total + GREEN_THREADS * 4 - 1) / (GREEN_THREADS * 4), 152 * 8);
-    if (nb < 1) nb = 1;
+int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec, const GreenBufs &b,
+                 const EnergyConsts &ec, cudaStream_t s) {
+    const int rows = g.M[0] * g.M[1];
+    const int per_cta = GREEN_THREADS / 32;
+    // one z-row per warp while that fits in 152 x 8 CTAs (the partials buffer)
+    int nb = (rows + per_cta - 1) / per_cta;
+    nb = std::min(std::max(nb, 1), 152 * 8);
     const auto *rh = reinterpret_cast<const complex_t<R> *>(rho_hat);
     auto *sp = reinterpret_cast<complex_t<R> *>(spec);
     if (ik)
-        k_green<R, true><<<nb, GREEN_THREADS, 0, s>>>(g, rh, sp, b, ec, ev_user);
+        k_green<R, true><<<nb, GREEN_THREADS, 0, s>>>(g, rh, sp, b, ec);
     else
-        k_green<R, false><<<nb, GREEN_THREADS, 0, s>>>(g, rh, sp, b, ec, ev_user);
+        k_green<R, false><<<nb, GREEN_THREADS, 0, s>>>(g, rh, sp, b, ec);
+    return nb;
 }
 
-template void launch_green<float>(const Geom<float> &, bool, const void *, void *, const GreenBufs &,
-                                  const EnergyConsts &, double *, cudaStream_t);
-template void launch_green<double>(const Geom<double> &, bool, const void *, void *, const GreenBufs &,
-                                   const EnergyConsts &, double *, cudaStream_t);
+// warp c < 7 sums energy/virial component c over the green partials, warp 7
+// sums q and q^2 over the particle_map partials; fixed order, one CTA.
+__global__ void __launch_bounds__(256) k_energy_final(GreenBufs b, EnergyConsts ec, int gn, int mn,
+                                                      double *ev_user) {
+    __shared__ double qs[2];
+    __shared__ double comp[7];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w == 7) {
+        double a = 0.0, c = 0.0;
+        for (int k = lane; k < mn; k += 32) {
+            a += b.map_part[2 * k];
+            c += b.map_part[2 * k + 1];
+        }
+        a = warp_sum(a);
+        c = warp_sum(c);
+        if (lane == 0) {
+            qs[0] = a;
+            qs[1] = c;
+            b.qsum[0] = a;
+            b.qsum[1] = c;
+        }
+    } else {
+        double v = 0.0;
+        for (int k = lane; k < gn; k += 32) v += b.part[7 * k + w];
+        v = warp_sum(v);
+        if (lane == 0) comp[w] = v * ec.epref;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = comp[threadIdx.x];
+        if (threadIdx.x == 0) v += ec.eself * qs[1] + ec.ebg * qs[0] * qs[0];
+        b.ev[threadIdx.x] = v;
+        if (ev_user) ev_user[threadIdx.x] = v;
+    }
+}
+
+void launch_energy_final(const GreenBufs &b, const EnergyConsts &ec, int green_nblk, int map_nblk,
+                         double *ev_user, cudaStream_t s) {
+    k_energy_final<<<1, 256, 0, s>>>(b, ec, green_nblk, map_nblk, ev_user);
+}
+
+template int launch_green<float>(const Geom<float> &, bool, const void *, void *, const GreenBufs &,
+                                 const EnergyConsts &, cudaStream_t);
+template int launch_green<double>(const Geom<double> &, bool, const void *, void *, const GreenBufs &,
+                                  const EnergyConsts &, cudaStream_t);
 
 }  // namespace pppm

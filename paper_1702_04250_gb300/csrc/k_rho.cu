@@ -7,32 +7,46 @@
 // into a private shared-memory brick that covers the tile plus its P-1 halo
 // (the paper's thread-private grid copies, "rethread"), then adds the brick
 // to the global mesh once.  Within a warp, 8 lanes serve one particle: lane k
-// owns stencil row offset k along z (unit stride) and lanes k >= P carry zero
-// weight -- the paper's padding of the 7-long inner loop to 8 ("simd8").
-// Consecutive lanes therefore hit consecutive shared-memory words.
+// owns stencil offset k along z (unit stride) and lanes k >= P carry no work
+// -- the paper's padding of the 7-long inner loop to 8 ("simd8").
 //
-// FP32C keeps a compensated (hi, lo) pair per brick point: the rounding error
-// of every shared atomic add is recovered exactly with TwoSum from the value
-// the atomic returns and accumulated in lo.
+// Accumulators (ACC):
+//  ACC_NATIVE  atomics in the step type (FP64, FP32).  On sm_103a shared
+//              float/double atomic adds are compare-and-swap loops whose
+//              round trip serialises each thread's updates.
+//  ACC_FIXED   FP32C: error-free accumulation in two 32-bit integer words per
+//              brick point, hi = sum floor(v s) and lo = sum of the 16-bit
+//              rounded fractions, with s = 2^(S-16) chosen per tile from the
+//              bound sum|q_j| / vcell on any point's sum.  Integer shared
+//              atomics are native and need no return value, and the sum is
+//              exact (independent of order) to 2^-45 of that bound -- the
+//              hi/lo compensation carried in integers.  lo is folded into hi
+//              every 32768 particles, so neither word can overflow.
 #include "pppm_common.cuh"
 
 namespace pppm {
 
-constexpr int RHO_THREADS = 128;
+constexpr int RHO_THREADS = 256;
 constexpr int GROUP = 8;
+constexpr int ACC_NATIVE = 0, ACC_FIXED = 1;
+constexpr int LO_CHUNK = 32768;
 
-template <typename R, int P, bool COMP>
+__device__ __forceinline__ float absval(float v) { return fabsf(v); }
+__device__ __forceinline__ double absval(double v) { return fabs(v); }
+
+template <typename R, int P, int ACC>
 __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b, R *__restrict__ rho) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *acc = reinterpret_cast<R *>(smem_raw);
+    __shared__ float sh_red[RHO_THREADS / 32];
 
     const int tile = blockIdx.x;
+    const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
+    if (threadIdx.x == 0) b.tile_count[tile] = 0;  // histogram is clean for the next step
+    if (start == end) return;
+
     const int tz = tile % g.T[2];
     const int ty = (tile / g.T[2]) % g.T[1];
     const int tx = tile / (g.T[2] * g.T[1]);
-    const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
-    if (start == end) return;
-
     const int ox = tile_origin(tx, g.T[0], g.M[0]);
     const int oy = tile_origin(ty, g.T[1], g.M[1]);
     const int oz = tile_origin(tz, g.T[2], g.M[2]);
@@ -40,112 +54,168 @@ __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b,
     const int Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - oy + P - 1;
     const int Ez = tile_origin(tz + 1, g.T[2], g.M[2]) - oz + P - 1;
     const int vol = Ex * Ey * Ez;
-    R *lo = acc + vol;
 
-    for (int e = threadIdx.x; e < (COMP ? 2 : 1) * vol; e += blockDim.x) acc[e] = R(0);
+    R *accr = reinterpret_cast<R *>(smem_raw);
+    int *acch = reinterpret_cast<int *>(smem_raw);
+    unsigned int *accl = reinterpret_cast<unsigned int *>(smem_raw) + vol;
+    const R *__restrict__ recp = reinterpret_cast<const R *>(b.rec);
+
+    // fixed-point scale: hi unit = 2^-(S-16), S = 46 - ceil(log2(bound))
+    float fs = 1.0f, ifs = 1.0f;
+    if (ACC == ACC_FIXED) {
+        float part = 0.0f;
+        for (int j = start + threadIdx.x; j < end; j += blockDim.x)
+            part += absval((float)reinterpret_cast<const vec4_t<R> *>(recp)[j].w);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0) sh_red[threadIdx.x >> 5] = part;
+        __syncthreads();
+        float bound = 0.0f;
+#pragma unroll
+        for (int w = 0; w < RHO_THREADS / 32; ++w) bound += sh_red[w];
+        bound = bound * (float)g.ivcell * 1.0001f + 1e-30f;
+        int e2;
+        frexpf(bound, &e2);            // bound < 2^e2
+        fs = ldexpf(1.0f, 30 - e2);    // |sum v fs| < 2^30
+        ifs = ldexpf(1.0f, e2 - 30);
+    }
+
+    {
+        const int words = (ACC == ACC_FIXED ? 2 * vol : vol * (int)(sizeof(R) / 4));
+        int *w = reinterpret_cast<int *>(smem_raw);
+        for (int e = threadIdx.x; e < words; e += blockDim.x) w[e] = 0;
+    }
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
     const int k = lane & (GROUP - 1);            // z stencil offset of this lane
+    const int gbase = lane & ~(GROUP - 1);
     const int grp = threadIdx.x / GROUP;         // particle slot in the CTA
     const int ngrp = blockDim.x / GROUP;
-    const R *__restrict__ recp = reinterpret_cast<const R *>(b.rec);
+    const R qscale = (ACC == ACC_FIXED) ? (R)(g.ivcell * (R)fs) : g.ivcell;
 
-    // warp-uniform trip count: all 32 lanes take part in the shuffles
-    for (int base = start; base < end; base += ngrp) {
-        const int j = base + grp;
-        const bool live = j < end;
-        R dx = R(0), dy = R(0), dz = R(0), qv = R(0);
-        int ax = 0, ay = 0, az = 0;
-        if (live) {
-            const vec4_t<R> r = reinterpret_cast<const vec4_t<R> *>(recp)[j];
-            dx = r.x; dy = r.y; dz = r.z; qv = r.w * g.ivcell;
-            unpack_anchor(b.cell[j], ax, ay, az);
-            ax -= ox; ay -= oy; az -= oz;        // local anchor in [0, tile size)
-        }
-        // lane k < P evaluates the three weights of stencil offset k
-        R wx = R(0), wy = R(0), wz = R(0);
-        if (k < P) {
-            wx = weight<R, P>(g.coef, k, dx);
-            wy = weight<R, P>(g.coef, k, dy);
-            wz = weight<R, P>(g.coef, k, dz);
-        }
-        R wxq[P], wyk[P];
+    for (int chunk = start; chunk < end; chunk += LO_CHUNK) {
+        const int cend = min(end, chunk + LO_CHUNK);
+        // warp-uniform trip count: all 32 lanes take part in the shuffles
+        for (int base = chunk; base < cend; base += ngrp) {
+            const int j = base + grp;
+            const bool live = j < cend;
+            R dx = R(0), dy = R(0), dz = R(0), qv = R(0);
+            int ax = 0, ay = 0, az = 0;
+            if (live) {
+                const vec4_t<R> r = reinterpret_cast<const vec4_t<R> *>(recp)[j];
+                dx = r.x; dy = r.y; dz = r.z; qv = r.w * qscale;
+                unpack_anchor(b.cell[j], ax, ay, az);
+                ax -= ox; ay -= oy; az -= oz;        // local anchor in [0, tile size)
+            }
+            // lane k < P evaluates the three weights of stencil offset k
+            R wx = R(0), wy = R(0), wz = R(0);
+            if (k < P) {
+                wx = weight<R, P>(g.coef, k, dx);
+                wy = weight<R, P>(g.coef, k, dy);
+                wz = weight<R, P>(g.coef, k, dz);
+            }
+            R wxq[P], wyk[P];
 #pragma unroll
-        for (int t = 0; t < P; ++t) {
-            wxq[t] = __shfl_sync(0xffffffffu, wx, (lane & ~(GROUP - 1)) + t) * qv;
-            wyk[t] = __shfl_sync(0xffffffffu, wy, (lane & ~(GROUP - 1)) + t);
-        }
-        if (live && k < P) {
-            R *row = acc + ((ax * Ey + ay) * Ez + az + k);
+            for (int t = 0; t < P; ++t) {
+                wxq[t] = __shfl_sync(0xffffffffu, wx, gbase + t) * qv;
+                wyk[t] = __shfl_sync(0xffffffffu, wy, gbase + t);
+            }
+            if (live && k < P) {
+                const int row = (ax * Ey + ay) * Ez + az + k;
 #pragma unroll
-            for (int a = 0; a < P; ++a) {
-                const R wa = wxq[a] * wz;
+                for (int a = 0; a < P; ++a) {
+                    const R wa = wxq[a] * wz;
 #pragma unroll
-                for (int c = 0; c < P; ++c) {
-                    const R v = wa * wyk[c];
-                    R *p = row + (a * Ey + c) * Ez;
-                    if (COMP) {
-                        const R old = atomicAdd(p, v);
-                        const R s = old + v;
-                        const R bb = s - old;
-                        const R err = (old - (s - bb)) + (v - bb);
-                        atomicAdd(p + vol, err);
-                    } else {
-                        atomicAdd(p, v);
+                    for (int c = 0; c < P; ++c) {
+                        const R v = wa * wyk[c];
+                        const int e = row + (a * Ey + c) * Ez;
+                        if (ACC == ACC_FIXED) {
+                            const float t = (float)v;
+                            const float fl = floorf(t);
+                            atomicAdd(&acch[e], (int)fl);
+                            atomicAdd(&accl[e], __float2uint_rn((t - fl) * 65536.0f));
+                        } else {
+                            atomicAdd(&accr[e], v);
+                        }
                     }
                 }
             }
         }
+        if (ACC == ACC_FIXED && cend < end) {  // fold lo into hi before it can overflow
+            __syncthreads();
+            for (int e = threadIdx.x; e < vol; e += blockDim.x) {
+                acch[e] += (int)(accl[e] >> 16);
+                accl[e] &= 0xffffu;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
-    // flush the brick (tile + halo) into the global mesh
-    const int bx0 = ox - g.rlo, by0 = oy - g.rlo, bz0 = oz - g.rlo;
-    for (int e = threadIdx.x; e < vol; e += blockDim.x) {
-        R v = acc[e];
-        if (COMP) v = v + lo[e];
-        if (v == R(0)) continue;
-        const int ez = e % Ez, ey = (e / Ez) % Ey, ex = e / (Ez * Ey);
-        int gx = bx0 + ex, gy = by0 + ey, gz = bz0 + ez;
-        gx = (gx + 2 * g.M[0]) % g.M[0];
-        gy = (gy + 2 * g.M[1]) % g.M[1];
-        gz = (gz + 2 * g.M[2]) % g.M[2];
-        atomicAdd(&rho[((int64_t)gx * g.M[1] + gy) * g.M[2] + gz], v);
+    // flush the brick (tile + halo) into the global mesh: 16 lanes per z row
+    // (Ez <= 14), 16 rows per pass; every wrap is a single conditional since
+    // the brick is never wider than the mesh plus one period.
+    const int lz = threadIdx.x & 15, ry = threadIdx.x >> 4;
+    if (lz < Ez) {
+        int gz = oz - g.rlo + lz;
+        gz += (gz < 0) ? g.M[2] : 0;
+        gz -= (gz >= g.M[2]) ? g.M[2] : 0;
+        for (int ex = 0; ex < Ex; ++ex) {
+            int gx = ox - g.rlo + ex;
+            gx += (gx < 0) ? g.M[0] : 0;
+            gx -= (gx >= g.M[0]) ? g.M[0] : 0;
+            for (int ey = ry; ey < Ey; ey += RHO_THREADS / 16) {
+                int gy = oy - g.rlo + ey;
+                gy += (gy < 0) ? g.M[1] : 0;
+                gy -= (gy >= g.M[1]) ? g.M[1] : 0;
+                const int e = (ex * Ey + ey) * Ez + lz;
+                R v;
+                if (ACC == ACC_FIXED) {
+                    // normalise in integers (exact), then one FP32 rounding
+                    const int h = acch[e] + (int)(accl[e] >> 16);
+                    v = (R)(fmaf((float)(accl[e] & 0xffffu), 1.0f / 65536.0f, (float)h) * ifs);
+                } else {
+                    v = accr[e];
+                }
+                if (v != R(0)) atomicAdd(&rho[(gx * g.M[1] + gy) * g.M[2] + gz], v);
+            }
+        }
     }
 }
 
 template <typename R, int P>
-static size_t brick_bytes(bool comp) {
+static size_t brick_bytes(int acc) {
     const int E = TILE_B + P - 1;
-    return (size_t)E * E * E * sizeof(R) * (comp ? 2 : 1);
+    return (size_t)E * E * E * (acc == ACC_FIXED ? 8 : sizeof(R));
 }
 
 template <typename R, int P>
-static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, bool comp, cudaStream_t s) {
-    const size_t bytes = brick_bytes<R, P>(comp);
-    if (comp)
-        k_make_rho<R, P, true><<<g.ntiles, RHO_THREADS, bytes, s>>>(g, b, rho);
+static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, int acc, cudaStream_t s) {
+    const size_t bytes = brick_bytes<R, P>(acc);
+    if (acc == ACC_FIXED)
+        k_make_rho<R, P, ACC_FIXED><<<g.ntiles, RHO_THREADS, bytes, s>>>(g, b, rho);
     else
-        k_make_rho<R, P, false><<<g.ntiles, RHO_THREADS, bytes, s>>>(g, b, rho);
+        k_make_rho<R, P, ACC_NATIVE><<<g.ntiles, RHO_THREADS, bytes, s>>>(g, b, rho);
 }
 
 template <typename R, int P>
-static cudaError_t prepare_p(bool comp) {
-    const int bytes = (int)brick_bytes<R, P>(comp);
-    if (comp) return cudaFuncSetAttribute(k_make_rho<R, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return cudaFuncSetAttribute(k_make_rho<R, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+static cudaError_t prepare_p(int acc) {
+    const int bytes = (int)brick_bytes<R, P>(acc);
+    if (acc == ACC_FIXED)
+        return cudaFuncSetAttribute(k_make_rho<R, P, ACC_FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_make_rho<R, P, ACC_NATIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <typename R>
 cudaError_t prepare_make_rho(int P, bool comp) {
+    const int acc = comp ? ACC_FIXED : ACC_NATIVE;
     switch (P) {
-        case 2: return prepare_p<R, 2>(comp);
-        case 3: return prepare_p<R, 3>(comp);
-        case 4: return prepare_p<R, 4>(comp);
-        case 5: return prepare_p<R, 5>(comp);
-        case 6: return prepare_p<R, 6>(comp);
-        case 7: return prepare_p<R, 7>(comp);
+        case 2: return prepare_p<R, 2>(acc);
+        case 3: return prepare_p<R, 3>(acc);
+        case 4: return prepare_p<R, 4>(acc);
+        case 5: return prepare_p<R, 5>(acc);
+        case 6: return prepare_p<R, 6>(acc);
+        case 7: return prepare_p<R, 7>(acc);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -154,13 +224,14 @@ template <typename R>
 void launch_make_rho(const Geom<R> &g, int64_t n, const SortBufs &b, R *rho, bool comp, cudaStream_t s) {
     cudaMemsetAsync(rho, 0, sizeof(R) * (size_t)g.M[0] * g.M[1] * g.M[2], s);
     if (n == 0) return;
+    const int acc = comp ? ACC_FIXED : ACC_NATIVE;
     switch (g.P) {
-        case 2: launch_p<R, 2>(g, b, rho, comp, s); break;
-        case 3: launch_p<R, 3>(g, b, rho, comp, s); break;
-        case 4: launch_p<R, 4>(g, b, rho, comp, s); break;
-        case 5: launch_p<R, 5>(g, b, rho, comp, s); break;
-        case 6: launch_p<R, 6>(g, b, rho, comp, s); break;
-        case 7: launch_p<R, 7>(g, b, rho, comp, s); break;
+        case 2: launch_p<R, 2>(g, b, rho, acc, s); break;
+        case 3: launch_p<R, 3>(g, b, rho, acc, s); break;
+        case 4: launch_p<R, 4>(g, b, rho, acc, s); break;
+        case 5: launch_p<R, 5>(g, b, rho, acc, s); break;
+        case 6: launch_p<R, 6>(g, b, rho, acc, s); break;
+        case 7: launch_p<R, 7>(g, b, rho, acc, s); break;
         default: break;
     }
 }

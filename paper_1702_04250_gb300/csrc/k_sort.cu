@@ -5,17 +5,21 @@
 // particles contiguously.
 //
 // Two kernels:
-//  k_particle_map  anchor + tile histogram (atomic ranks), per-block sums of q
-//                  and q^2; the last block to finish reduces those sums and
-//                  turns the histogram into tile offsets (exclusive scan),
-//                  zeroing the histogram for the next step.
-//  k_scatter       writes each particle's (delta, q) record, packed anchor and
-//                  input index at its sorted position.
+//  k_particle_map  anchor + tile histogram (atomic ranks) and per-block sums
+//                  of q and q^2.  With more than SMALL_TILES tiles the last
+//                  block to finish turns the histogram into tile offsets
+//                  (exclusive scan).
+//  k_scatter       with at most SMALL_TILES tiles every block first scans the
+//                  histogram in shared memory (no grid-wide step in between);
+//                  then each particle's (delta, q) record, packed anchor and
+//                  input index are written at its sorted position.
+// make_rho clears each tile's histogram entry for the next step.
 #include "pppm_common.cuh"
 
 namespace pppm {
 
 constexpr int MAP_THREADS = 256;
+constexpr int SMALL_TILES = 4096;  // histogram scanned per scatter block up to this many tiles
 
 template <typename R>
 __device__ __forceinline__ bool load_particle(const R *__restrict__ x, const R *__restrict__ q,
@@ -45,28 +49,28 @@ __device__ __forceinline__ int tile_index(const Geom<R> &g, const int (&a)[3]) {
            tile_of(a[2], g.T[2], g.M[2]);
 }
 
-__device__ double block_sum(double v, double *sh) {
-    v = warp_sum(v);
+// Block sum: warps reduce in the step type, the per-warp values in FP64.
+template <typename R>
+__device__ double block_sum(R v, double *sh) {
+    v = warp_sum_t<R>(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
-    if (l == 0) sh[w] = v;
+    if (l == 0) sh[w] = (double)v;
     __syncthreads();
     double r = 0.0;
-    if (threadIdx.x < 32) {
-        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
-        r = warp_sum(r);
-    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
     return r;  // valid in thread 0
 }
 
 template <typename R>
 __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, const R *__restrict__ x,
-                                                              const R *__restrict__ q, SortBufs b) {
+                                                              const R *__restrict__ q, SortBufs b, int big) {
     __shared__ double sh[32];
     __shared__ int sh_scan[MAP_THREADS / 32];
     __shared__ bool last;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double qs = 0.0, qq = 0.0;
+    R qs = R(0), qq = R(0);
     if (i < n) {
         R xi[3], qi;
         if (!load_particle<R>(x, q, i, xi, qi)) atomicOr(b.err, 1);
@@ -75,15 +79,21 @@ __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, 
         anchors<R>(g, xi, a, d);
         b.rank[i] = atomicAdd(&b.tile_count[tile_index<R>(g, a)], 1);
         b.anchor[i] = pack_anchor(a[0], a[1], a[2]);
-        qs = (double)qi;
-        qq = qs * qs;
+        qs = qi;
+        qq = qi * qi;
     }
-    __threadfence();  // histogram atomics are visible before this block's ticket
-    const double s1 = block_sum(qs, sh);
-    const double s2 = block_sum(qq, sh);
+    // per-block sums of q and q^2, reduced later off the critical path
+    const double s1 = block_sum<R>(qs, sh);
+    const double s2 = block_sum<R>(qq, sh);
     if (threadIdx.x == 0) {
         b.blk[2 * blockIdx.x] = s1;
         b.blk[2 * blockIdx.x + 1] = s2;
+    }
+    if (!big) return;  // small tile counts: k_scatter scans the histogram itself
+
+    // the histogram atomics returned their ranks, so they are complete at L2
+    // before this block takes its ticket
+    if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int ticket = atomicAdd(b.counter, 1u);
         last = (ticket == gridDim.x - 1);
@@ -92,26 +102,12 @@ __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, 
     if (!last) return;
     __threadfence();
 
-    // ---- last block: totals of q and q^2 --------------------------------
-    double t1 = 0.0, t2 = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
-        t1 += __ldcg(&b.blk[2 * k]);
-        t2 += __ldcg(&b.blk[2 * k + 1]);
-    }
-    t1 = block_sum(t1, sh);
-    t2 = block_sum(t2, sh);
-    if (threadIdx.x == 0) {
-        b.qsum[0] = t1;
-        b.qsum[1] = t2;
-    }
-
     // ---- last block: exclusive scan of the tile histogram ---------------
     const int nt = g.ntiles;
     const int chunk = (nt + blockDim.x - 1) / blockDim.x;
     const int lo = min(nt, (int)threadIdx.x * chunk), hi = min(nt, lo + chunk);
     int local = 0;
     for (int k = lo; k < hi; ++k) local += __ldcg(&b.tile_count[k]);
-    // block exclusive scan of `local`
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int incl = local;
 #pragma unroll
@@ -135,16 +131,60 @@ __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, 
         const int c = __ldcg(&b.tile_count[k]);
         b.tile_start[k] = run;
         run += c;
-        b.tile_count[k] = 0;
     }
     if (hi == nt && lo < hi) b.tile_start[nt] = run;
-    if (nt == 0 && threadIdx.x == 0) b.tile_start[0] = 0;
     if (threadIdx.x == 0) *b.counter = 0u;
+}
+
+// Block-wide exclusive scan of the tile histogram into shared memory
+// (small tile counts only): every block of k_scatter does it redundantly, so
+// no grid-wide step sits between the histogram and the scatter.
+__device__ void scan_tiles_smem(const int *__restrict__ count, int nt, int *sh_start, int *sh_warp) {
+    const int chunk = (nt + blockDim.x - 1) / blockDim.x;
+    const int lo = min(nt, (int)threadIdx.x * chunk), hi = min(nt, lo + chunk);
+    int local = 0;
+    for (int k = lo; k < hi; ++k) local += count[k];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) sh_warp[w] = incl;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = (lane < (int)(blockDim.x >> 5)) ? sh_warp[lane] : 0;
+        int iv = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, iv, o);
+            if (lane >= o) iv += t;
+        }
+        if (lane < (int)(blockDim.x >> 5)) sh_warp[lane] = iv - v;
+    }
+    __syncthreads();
+    int run = sh_warp[w] + incl - local;
+    for (int k = lo; k < hi; ++k) {
+        sh_start[k] = run;
+        run += count[k];
+    }
+    if (hi == nt && lo < hi) sh_start[nt] = run;
+    __syncthreads();
 }
 
 template <typename R>
 __global__ void __launch_bounds__(MAP_THREADS) k_scatter(Geom<R> g, int n, const R *__restrict__ x,
-                                                         const R *__restrict__ q, SortBufs b) {
+                                                         const R *__restrict__ q, SortBufs b, int big) {
+    __shared__ int sh_start[SMALL_TILES + 1];
+    __shared__ int sh_warp[MAP_THREADS / 32];
+    const int *starts = b.tile_start;
+    if (!big) {
+        scan_tiles_smem(b.tile_count, g.ntiles, sh_start, sh_warp);
+        if (blockIdx.x == 0)
+            for (int k = threadIdx.x; k <= g.ntiles; k += blockDim.x) b.tile_start[k] = sh_start[k];
+        starts = sh_start;
+    }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     R xi[3], qi;
@@ -155,7 +195,7 @@ __global__ void __launch_bounds__(MAP_THREADS) k_scatter(Geom<R> g, int n, const
     const uint32_t packed = b.anchor[i];  // same computation as k_particle_map
     int s[3];
     unpack_anchor(packed, s[0], s[1], s[2]);
-    const int dest = b.tile_start[tile_index<R>(g, s)] + b.rank[i];
+    const int dest = starts[tile_index<R>(g, s)] + b.rank[i];
     vec4_t<R> r;
     r.x = d[0];
     r.y = d[1];
@@ -170,8 +210,9 @@ template <typename R>
 void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const SortBufs &b,
                  cudaStream_t s) {
     const int nb = (int)((n + MAP_THREADS - 1) / MAP_THREADS);
-    k_particle_map<R><<<nb, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b);
-    k_scatter<R><<<nb, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b);
+    const int big = g.ntiles > SMALL_TILES;
+    k_particle_map<R><<<nb, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, big);
+    k_scatter<R><<<nb, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, big);
 }
 
 template void launch_sort<float>(const Geom<float> &, int64_t, const float *, const float *,

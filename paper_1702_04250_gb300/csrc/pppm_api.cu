@@ -42,6 +42,8 @@ struct pppm_plan {
     bool field_is_field = false, have_rho = false;
     void *hx = nullptr, *hq = nullptr, *hf = nullptr;  // device staging for the host path
     double *hev = nullptr;
+    cudaStream_t side = nullptr;       // energy/virial reduction branch
+    cudaEvent_t fork = nullptr, join = nullptr;
     bool prof_on = false, prof_valid = false;
     cudaEvent_t prof[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool graph_on = false;
@@ -126,6 +128,9 @@ void release(pppm_plan *p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     for (auto &e : p->prof)
         if (e) cudaEventDestroy(e);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->join) cudaEventDestroy(p->join);
+    if (p->side) cudaStreamDestroy(p->side);
     if (p->have_r2c) cufftDestroy(p->r2c);
     if (p->have_c2r) cufftDestroy(p->c2r);
     if (p->have_c2r1) cufftDestroy(p->c2r1);
@@ -250,8 +255,16 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
               double *ev, int kind) {
     cudaStream_t s = p->stream;
     const bool prof = p->prof_on && kind == 0;
+    // External records stay real timing records inside a captured graph
+    // (a plain record during capture only becomes a dependency edge).
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (prof) CK(cudaStreamIsCapturing(s, &cap));
     auto mark = [&](int i) {
-        if (prof) cudaEventRecord(p->prof[i], s);
+        if (!prof) return;
+        if (cap == cudaStreamCaptureStatusActive)
+            cudaEventRecordWithFlags(p->prof[i], s, cudaEventRecordExternal);
+        else
+            cudaEventRecord(p->prof[i], s);
     };
     mark(0);
     launch_sort<R>(g, n, (const R *)x, (const R *)q, p->sb, s);
@@ -262,8 +275,18 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
     if ((rc = exec_r2c(p))) return rc;
     mark(3);
     const bool ik_spec = (kind == 0) && p->ik;
-    launch_green<R>(g, ik_spec, p->rho_hat, p->spec, p->gb, p->ec, ev, s);
+    const int gn = launch_green<R>(g, ik_spec, p->rho_hat, p->spec, p->gb, p->ec, s);
     mark(4);
+    const int mn = (int)((n + 255) / 256);
+    if (kind == 0) {
+        // the final energy/virial sum runs beside the inverse FFTs and fieldforce
+        CK(cudaEventRecord(p->fork, s));
+        CK(cudaStreamWaitEvent(p->side, p->fork, 0));
+        launch_energy_final(p->gb, p->ec, gn, mn, ev, p->side);
+        CK(cudaEventRecord(p->join, p->side));
+    } else {
+        launch_energy_final(p->gb, p->ec, gn, mn, ev, s);  // dE/dq needs sum q first
+    }
     if ((rc = exec_c2r(p, ik_spec))) return rc;
     mark(5);
     if (kind == 0) {
@@ -275,6 +298,7 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
                               gbg, s);
     }
     mark(6);
+    if (kind == 0) CK(cudaStreamWaitEvent(s, p->join, 0));
     p->prof_valid = prof;
     CK(cudaGetLastError());
     return PPPM_OK;
@@ -411,6 +435,7 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     p->gb.part = p->green_part;
     p->gb.counter = p->counters + 1;
     p->gb.qsum = p->sb.qsum;
+    p->gb.map_part = p->sb.blk;
     p->gb.ev = p->ev;
     p->ec.epref = 0.5 * p->C * p->vcell * p->vcell / p->V * (double)p->Mtot;
     p->ec.inv4g2 = 1.0 / (4.0 * p->g * p->g);
@@ -425,6 +450,10 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         cudaMemsetAsync(p->counters, 0, 4 * sizeof(unsigned int), p->stream) != cudaSuccess ||
         cudaMemsetAsync(p->sb.err, 0, 4 * sizeof(int), p->stream) != cudaSuccess ||
         cudaMemsetAsync(p->ev, 0, 8 * sizeof(double), p->stream) != cudaSuccess)
+        return fail(PPPM_ECUDA);
+    if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) != cudaSuccess)
         return fail(PPPM_ECUDA);
     cudaError_t pe = p->fp64 ? prepare_make_rho<double>(order, false) : prepare_make_rho<float>(order, p->comp);
     if (pe != cudaSuccess) return fail(PPPM_ECUDA);

@@ -119,6 +119,15 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+// Warp reduction in the step's type: on GB300 the FP64 pipe is ~2 DFMA per
+// clock per SM, so FP32 paths reduce within the warp in FP32 and combine only
+// the per-warp values in FP64.
+template <typename R>
+__device__ __forceinline__ R warp_sum_t(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // ---------------------------------------------------------------------------
 // Host-side coefficient/table builders (coeffs.cpp): independent exact
@@ -166,8 +175,9 @@ struct GreenBufs {
     const void *kvec;      // [Mx + My + Mzh] wavenumbers (step type), Nyquist negative
     const void *kdiff;     // same with the Nyquist entries zeroed (ik differentiation)
     double *part;          // [7 * nblk] per-block partial energy/virial
-    unsigned int *counter; // [1]
-    const double *qsum;    // [2]
+    unsigned int *counter; // [1] (unused since the final sum moved to k_energy_final)
+    double *qsum;          // [2] sum q, sum q^2 (written by k_energy_final)
+    const double *map_part;// [2 * map_nblk] per-block sum q, sum q^2 of k_particle_map
     double *ev;            // [8] energy + virial
 };
 struct EnergyConsts {
@@ -177,9 +187,14 @@ struct EnergyConsts {
     double ebg;    // -C pi / (2 g^2 V), times Q^2
 };
 
+// Returns the number of CTAs launched (the count of energy/virial partials).
 template <typename R>
-void launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec,
-                  const GreenBufs &b, const EnergyConsts &ec, double *ev_user, cudaStream_t s);
+int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec,
+                 const GreenBufs &b, const EnergyConsts &ec, cudaStream_t s);
+// Final energy/virial (and sum q, sum q^2) from the per-CTA partials, in a
+// fixed order; one CTA.  ev_user may be NULL.
+void launch_energy_final(const GreenBufs &b, const EnergyConsts &ec, int green_nblk, int map_nblk,
+                         double *ev_user, cudaStream_t s);
 
 template <typename R>
 void launch_fieldforce(const Geom<R> &g, bool ik, int64_t n, const SortBufs &b, const R *field,

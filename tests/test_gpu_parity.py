@@ -215,6 +215,27 @@ def test_tiny_and_degenerate(torch, prec):
             assert abs(ev[0] - ref["energy"]) <= tol * abs(ref["energy"])
 
 
+@pytest.mark.parametrize("prec", ["fp32c", "fp32", "fp64"])
+def test_dense_tile(torch, prec):
+    """70,000 charges packed into one mesh tile: the FP32C fixed-point brick
+    folds its low words twice (every 32,768 particles), and every precision
+    must still match the oracle's mesh and forces."""
+    r = np.random.default_rng(31)
+    box, mesh, P, g = (20.0, 20.0, 20.0), (20, 20, 20), 5, 0.5
+    n = 70000
+    x = 3.0 + r.uniform(0.0, 1.5, (n, 3))
+    q = r.normal(size=n)
+    plan, f, ev = run(torch, box, mesh, P, g, "ik", prec, x, q)
+    xo, qo = oracle_inputs(x, q, prec)
+    o = OraclePPPM(box, mesh, P, g, "ik", 1.0)
+    ref = o.compute(xo, qo, keep=True)
+    rho = plan.get_array("rho").astype(np.float64)
+    rerr = np.sqrt(np.mean((rho - ref["rho"]) ** 2)) / np.sqrt(np.mean(ref["rho"] ** 2))
+    print(prec, "dense tile rho rel RMS", rerr)
+    assert rerr < (1e-12 if prec == "fp64" else 1e-5)
+    check_all(f, ev, ref, prec, "dense tile")
+
+
 def test_empty_input(torch):
     from paper_1702_04250_gb300 import pppm
 
