@@ -155,9 +155,12 @@ int pppm_get_array(pppm_plan *p, int which, void *dst, size_t bytes, int to_host
  * plan's stream between stages (also inside a captured graph).  Stages:
  * [0] particle_map + sort, [1] make_rho (incl. mesh clear), [2] forward FFT,
  * [3] influence-function multiply + energy/virial, [4] inverse FFT(s),
- * [5] fieldforce.  pppm_stage_times waits for the last profiled call and
- * writes milliseconds; PPPM_ENOTREADY if profiling was off for it. */
-int pppm_set_profiling(pppm_plan *p, int enable);
+ * [5] fieldforce.  `stages` is a bitmask (bit s times stage s; 0 = off,
+ * 0x3f = all); each event adds a few microseconds to a graph launch, so
+ * time only the stages you need.  pppm_stage_times waits for the last
+ * profiled call and writes milliseconds (-1 for stages not timed);
+ * PPPM_ENOTREADY if profiling was off for it. */
+int pppm_set_profiling(pppm_plan *p, int stages);
 int pppm_stage_times(pppm_plan *p, float ms[6]);
 
 /* Plan facts: [0..2] mesh, [3] order, [4] ntiles, [5] tile edge B,

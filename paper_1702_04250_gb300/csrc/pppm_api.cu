@@ -44,10 +44,10 @@ struct pppm_plan {
     double *hev = nullptr;
     cudaStream_t side = nullptr;       // energy/virial reduction branch
     cudaEvent_t fork = nullptr, join = nullptr;
-    bool prof_on = false, prof_valid = false;
+    int prof_mask = 0, prof_valid = 0;  // stages timed; stages timed by the last call
     cudaEvent_t prof[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool graph_on = false;
-    bool gkey_prof = false;
+    int gkey_prof = 0;
     cudaGraphExec_t gexec = nullptr;
     const void *gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int64_t gkey_n = -1;
@@ -254,13 +254,16 @@ template <typename R>
 int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const void *q, void *f, void *dq,
               double *ev, int kind) {
     cudaStream_t s = p->stream;
-    const bool prof = p->prof_on && kind == 0;
+    const int pmask = (kind == 0) ? p->prof_mask : 0;
+    const bool prof = pmask != 0;
     // External records stay real timing records inside a captured graph
     // (a plain record during capture only becomes a dependency edge).
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (prof) CK(cudaStreamIsCapturing(s, &cap));
+    // boundary i opens stage i and closes stage i - 1
     auto mark = [&](int i) {
-        if (!prof) return;
+        const bool need = ((pmask >> i) & 1) || (i > 0 && ((pmask >> (i - 1)) & 1));
+        if (!need) return;
         if (cap == cudaStreamCaptureStatusActive)
             cudaEventRecordWithFlags(p->prof[i], s, cudaEventRecordExternal);
         else
@@ -299,7 +302,7 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
     }
     mark(6);
     if (kind == 0) CK(cudaStreamWaitEvent(s, p->join, 0));
-    p->prof_valid = prof;
+    p->prof_valid = pmask;
     CK(cudaGetLastError());
     return PPPM_OK;
 }
@@ -503,7 +506,7 @@ int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f,
     p->have_rho = true;
     if (!p->graph_on) return enqueue(p, n, x, q, f, nullptr, ev, 0);
     const void *key[5] = {x, q, f, ev, nullptr};
-    bool same = p->gexec && p->gkey_n == n && p->gkey_prof == p->prof_on;
+    bool same = p->gexec && p->gkey_n == n && p->gkey_prof == p->prof_mask;
     for (int i = 0; i < 5 && same; ++i) same = key[i] == p->gkey[i];
     if (!same) {
         if (p->gexec) {
@@ -524,10 +527,10 @@ int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f,
         CK(ie);
         for (int i = 0; i < 5; ++i) p->gkey[i] = key[i];
         p->gkey_n = n;
-        p->gkey_prof = p->prof_on;
+        p->gkey_prof = p->prof_mask;
     }
     CK(cudaGraphLaunch(p->gexec, p->stream));
-    p->prof_valid = p->prof_on;
+    p->prof_valid = p->prof_mask;
     return PPPM_OK;
 }
 
@@ -635,16 +638,21 @@ int pppm_set_profiling(pppm_plan *p, int enable) {
     if (enable && !p->prof[0]) {
         for (auto &e : p->prof) CK(cudaEventCreate(&e));
     }
-    p->prof_on = enable != 0;
-    p->prof_valid = false;
+    p->prof_mask = enable & 0x3f;
+    p->prof_valid = 0;
     return PPPM_OK;
 }
 
 int pppm_stage_times(pppm_plan *p, float ms[6]) {
     if (!p || !ms) return PPPM_EINVAL;
     if (!p->prof_valid || !p->prof[0]) return PPPM_ENOTREADY;
-    CK(cudaEventSynchronize(p->prof[6]));
-    for (int i = 0; i < 6; ++i) CK(cudaEventElapsedTime(&ms[i], p->prof[i], p->prof[i + 1]));
+    for (int i = 0; i < 6; ++i) {
+        ms[i] = -1.0f;
+        if ((p->prof_valid >> i) & 1) {
+            CK(cudaEventSynchronize(p->prof[i + 1]));
+            CK(cudaEventElapsedTime(&ms[i], p->prof[i], p->prof[i + 1]));
+        }
+    }
     return PPPM_OK;
 }
 

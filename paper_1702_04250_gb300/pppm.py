@@ -185,8 +185,15 @@ class PPPM:
 
     STAGES = ("sort", "make_rho", "fft_fwd", "green", "fft_inv", "fieldforce")
 
-    def set_profiling(self, enable: bool = True):
-        _check(lib().pppm_set_profiling(self._h, int(bool(enable))), "pppm_set_profiling")
+    def set_profiling(self, stages=True):
+        """True/False for all/no stages, or an iterable of stage names."""
+        if stages is True:
+            mask = 0x3F
+        elif not stages:
+            mask = 0
+        else:
+            mask = sum(1 << self.STAGES.index(s) for s in stages)
+        _check(lib().pppm_set_profiling(self._h, mask), "pppm_set_profiling")
 
     def stage_times(self) -> dict:
         a = (ctypes.c_float * 6)()
