@@ -167,6 +167,30 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * [6] diff mode, [7] precision, [8] n_max, [9] last n. */
 int pppm_plan_info(const pppm_plan *p, int64_t info[10]);
 
+/* Mesh charge density without any device allocation (particle_map, sort and
+ * make_rho as in pppm_compute, FP32 arithmetic).  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc where they
+ * need the mesh -- a host engine that owns all device memory through its own
+ * pool, code running under stream capture, or a step loop that must not pay
+ * the device-wide synchronisation of cudaMalloc/cudaFree.
+ *   box[3], mesh[3], order   as for pppm_setup (order 2..7, mesh >= order)
+ *   precision               PPPM_FP32 or PPPM_FP32C
+ *   n                       0 <= n <= 65536
+ *   x, q                    device, float [n][3] and [n]
+ *   rho                     device, float [Mx][My][Mz], overwritten
+ *   cuda_stream             stream to enqueue on (NULL = legacy default)
+ * Limits: at most 65536 particles and ceil(Mx/8)*ceil(My/8)*ceil(Mz/8) <= 4096
+ * mesh tiles (e.g. up to 128^3); larger sizes return PPPM_EINVAL before any
+ * GPU work.  The sort scratch is one fixed ~2.1 MiB device array compiled
+ * into the library, held on every device that loads it until exit, and shared
+ * by all calls: it keeps the previous call's contents (the call clears what
+ * must start at zero), and calls that overlap on the GPU race -- serialise
+ * them.  The first call on a device looks the array's address up; make it
+ * before any stream capture.  Allocates nothing.  Asynchronous. */
+int pppm_make_rho_noalloc(const double box[3], const int mesh[3], int order, int precision,
+                          int64_t n, const float *x, const float *q, float *rho,
+                          void *cuda_stream);
+
 /* Static description of a status code (never NULL). */
 const char *pppm_strerror(int status);
 
