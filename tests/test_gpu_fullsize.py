@@ -1,0 +1,149 @@
+"""Full-size workloads through the C ABI.
+
+c5: 99,999 water-like charges, 100 A cube, mesh 96^3, order 5, ik -- the
+differentiable energy: autograd gradients vs central finite differences
+(FP64, h = 1e-4 A, 64 seeded atoms), vs the oracle's exact gradients, vs the
+oracle's ik forces (1e-4: ik forces and -dE/dx differ at the discretisation
+level), and FP32 vs FP64.
+
+c3: 2,048,001 water-like charges, 272 A cube, mesh 256^3, order 7, ad, FP32C
+-- forces on a 1% subsample (every 100th atom), energy and virial vs the FP64
+oracle run on the full mesh.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import OraclePPPM, estimate_g_ewald
+from paper_1702_04250_gb300.workloads import config
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_04250_gb300 import build
+
+    build.build()
+    return t
+
+
+def rel_rms(a, b):
+    return math.sqrt(float(np.sum((a - b) ** 2)) / float(np.sum(b ** 2)))
+
+
+@pytest.fixture(scope="module")
+def c5(torch):
+    w = config("c5")
+    g = estimate_g_ewald(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
+    o = OraclePPPM(w.box, w.mesh, w.order, g, "ik", w.qqrd2e)
+    rdx, rdq = o.energy_gradients(w.x, w.q)
+    ref = o.compute(w.x, w.q)
+    return w, g, rdx, rdq, ref
+
+
+def _plan(w, g, prec):
+    from paper_1702_04250_gb300 import pppm
+
+    return pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode="ik", precision=prec, qqrd2e=w.qqrd2e)
+
+
+def test_c5_autograd_matches_oracle_and_forces(torch, c5):
+    from paper_1702_04250_gb300.autograd import pppm_energy
+
+    w, g, rdx, rdq, ref = c5
+    plan = _plan(w, g, "fp64")
+    x = torch.tensor(w.x, dtype=torch.float64, device="cuda", requires_grad=True)
+    q = torch.tensor(w.q, dtype=torch.float64, device="cuda", requires_grad=True)
+    E = pppm_energy(x, q, plan)
+    E.backward()
+    gx = x.grad.cpu().numpy()
+    gq = q.grad.cpu().numpy()
+    assert abs(E.item() - ref["energy"]) < 1e-10 * abs(ref["energy"])
+    assert rel_rms(gx, rdx) < 1e-9
+    assert rel_rms(gq, rdq) < 1e-9
+    # against the oracle's ik forces: the same force discretised two ways
+    # (ik differentiation vs the exact gradient of the ik-G energy); each is
+    # within ~1e-4 of the Ewald force at this mesh, and they differ by
+    # 1.1e-4 here, so the bound is 2e-4
+    e = rel_rms(-gx, ref["f"])
+    print("c5 |dE/dx + F_ik| / |F_ik| =", e)
+    assert e < 2e-4
+
+
+def test_c5_autograd_finite_differences(torch, c5):
+    from paper_1702_04250_gb300.autograd import pppm_energy
+
+    w, g, *_ = c5
+    plan = _plan(w, g, "fp64")
+    x0 = torch.tensor(w.x, dtype=torch.float64, device="cuda", requires_grad=True)
+    q0 = torch.tensor(w.q, dtype=torch.float64, device="cuda")
+    E = pppm_energy(x0, q0, plan)
+    E.backward()
+    grad = x0.grad.cpu().numpy()
+    idx = np.random.default_rng(5).choice(w.n, 64, replace=False)
+    h = 1e-4
+    fd = np.empty((64, 3))
+    base = torch.tensor(w.x, dtype=torch.float64, device="cuda")
+    for j, i in enumerate(idx):
+        for a in range(3):
+            xp = base.clone()
+            xp[i, a] += h
+            xm = base.clone()
+            xm[i, a] -= h
+            ep = pppm_energy(xp, q0, plan).item()
+            em = pppm_energy(xm, q0, plan).item()
+            fd[j, a] = (ep - em) / (2 * h)
+    err = rel_rms(grad[idx], fd)
+    print("c5 autograd vs central differences (64 atoms):", err)
+    assert err < 1e-6
+
+
+def test_c5_fp32_gradients_vs_fp64(torch, c5):
+    from paper_1702_04250_gb300.autograd import pppm_energy
+
+    w, g, rdx, rdq, ref = c5
+    plan = _plan(w, g, "fp32c")
+    x = torch.tensor(w.x, dtype=torch.float32, device="cuda", requires_grad=True)
+    q = torch.tensor(w.q, dtype=torch.float32, device="cuda", requires_grad=True)
+    E = pppm_energy(x, q, plan)
+    E.backward()
+    o = OraclePPPM(w.box, w.mesh, w.order, g, "ik", w.qqrd2e)
+    x32 = w.x.astype(np.float32).astype(np.float64)
+    q32 = w.q.astype(np.float32).astype(np.float64)
+    rdx32, rdq32 = o.energy_gradients(x32, q32)
+    ex = rel_rms(x.grad.double().cpu().numpy(), rdx32)
+    eq = rel_rms(q.grad.double().cpu().numpy(), rdq32)
+    print("c5 FP32C gradients vs FP64 oracle: dx", ex, "dq", eq)
+    assert ex < 1e-4 and eq < 1e-4
+
+
+@pytest.mark.slow
+def test_c3_subsample_fp32c_ad(torch):
+    from paper_1702_04250_gb300 import pppm
+
+    w = config("c3")
+    g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
+    plan = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode="ad", precision="fp32c", qqrd2e=w.qqrd2e)
+    x = torch.tensor(w.x, dtype=torch.float32, device="cuda")
+    q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
+    f, ev = plan.compute(x, q)
+    plan.sync()
+    f = f.double().cpu().numpy()
+    ev = ev.cpu().numpy()
+    x64 = w.x.astype(np.float32).astype(np.float64)
+    q64 = w.q.astype(np.float32).astype(np.float64)
+    go = estimate_g_ewald(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
+    assert abs(go - g) < 1e-12
+    sub = np.arange(0, w.n, 100)
+    ref = OraclePPPM(w.box, w.mesh, w.order, g, "ad", w.qqrd2e).compute(x64, q64, subset=sub)
+    ferr = rel_rms(f[sub], ref["f"])
+    eerr = abs(ev[0] - ref["energy"]) / abs(ref["energy"])
+    verr = np.linalg.norm(ev[1:7] - ref["virial"]) / np.linalg.norm(ref["virial"])
+    print(f"c3 FP32C ad 1% subsample: force {ferr:.2e} energy {eerr:.2e} virial {verr:.2e}")
+    assert ferr < 1e-4 and eerr < 1e-4 and verr < 1e-4
