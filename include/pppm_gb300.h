@@ -163,6 +163,18 @@ int pppm_get_array(pppm_plan *p, int which, void *dst, size_t bytes, int to_host
 int pppm_set_profiling(pppm_plan *p, int stages);
 int pppm_stage_times(pppm_plan *p, float ms[6]);
 
+/* Kernel variants of a plan (Sec. 3.1's mapping functions have one result
+ * and several implementations; the paper picks them by measurement, and so
+ * does this).  Bit 0: fieldforce stages the tile's field brick in shared
+ * memory (1) or reads the field through L1 per particle (0).
+ * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits).
+ * pppm_autotune times every variant on the caller's inputs (one warm-up and
+ * five timed pppm_compute steps each, synchronous, graph mode off while it
+ * runs), keeps the fastest, writes its bitmask to choice_out (nullable), and
+ * leaves f holding a valid result.  Both drop any captured graph. */
+int pppm_set_variant(pppm_plan *p, int variants);
+int pppm_autotune(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, int *choice_out);
+
 /* Plan facts: [0..2] mesh, [3] order, [4] ntiles, [5] tile edge B,
  * [6] diff mode, [7] precision, [8] n_max, [9] last n. */
 int pppm_plan_info(const pppm_plan *p, int64_t info[10]);

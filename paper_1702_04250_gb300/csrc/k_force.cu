@@ -10,10 +10,18 @@
 //      self-force correction (the paper's "split atom" epilogue, fused here).
 //
 // Layout: 8 lanes per particle, lane k owning stencil offset k along z (lanes
-// k >= P idle: the zero-padded "simd8" inner loop), particles in tile-sorted
-// order so a warp's four particles read neighbouring mesh rows; the eight
-// partial sums are combined with warp shuffles and the force is written to the
-// particle's input position.
+// k >= P idle: the zero-padded "simd8" inner loop).  Each lane sums its z
+// column separably -- first over y into per-x partials, then over x -- so the
+// ad gather costs two FMAs per stencil point; the eight lane partials are
+// combined with warp shuffles and the force is written to the particle's
+// input position.
+//
+// Two variants (chosen per plan, see pppm_autotune):
+//  k_fieldforce        particles in tile order, field rows read through L1.
+//  k_fieldforce_tiled  one CTA per mesh tile copies the field over the tile
+//                      plus its P-1 halo (<= 14^3 points) into shared memory
+//                      with asynchronous copies (cp.async, all in flight at
+//                      once), then its particles gather from shared memory.
 //
 // ad self force (paper silent; reading of the Ballenegger-Cerda-Holm form):
 // F_a -= q^2 sum_{n=1,2} c_{a,n} sin(2 pi n u_a), with u_a = n_a - delta_a the
@@ -38,12 +46,195 @@ __device__ __forceinline__ double sin2pi(double x) { return sinpi(2.0 * x); }
 
 __device__ __forceinline__ int wrap1(int i, int M) { return i < 0 ? i + M : (i >= M ? i - M : i); }
 
+// Asynchronous global -> shared copy of `bytes` (4, 8 or 16).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned int s = (unsigned int)__cvta_generic_to_shared(smem);
+    if (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Per-particle weights shared inside an 8-lane group: lane t < P evaluates
+// stencil offset t, every lane receives the x and y sets.
+template <typename R, int P>
+__device__ __forceinline__ R horner_r(const R (&c)[P], R d) {
+    R w = c[P - 1];
+#pragma unroll
+    for (int l = P - 2; l >= 0; --l) w = fma_rn(w, d, c[l]);
+    return w;
+}
+
+// This lane's stencil polynomial (offset k) and its derivative, in registers.
+template <typename R, int P>
+struct LaneCoef {
+    R cw[P], cd[P];
+    __device__ __forceinline__ void load(const Geom<R> &g, int k) {
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            cw[l] = (k < P) ? g.coef[k][l] : R(0);
+            cd[l] = (k < P && l < P - 1) ? g.dcoef[k][l] : R(0);
+        }
+    }
+};
+
+// Per-particle weights shared inside an 8-lane group: lane t < P evaluates
+// stencil offset t, every lane receives the x and y sets.
+template <typename R, int P, int MODE>
+struct GroupWeights {
+    R wx[P], wy[P], wdx[P], wdy[P];
+    R wz, dwz;  // this lane's z offset
+    __device__ __forceinline__ void build(const LaneCoef<R, P> &lc, int gbase, R dx, R dy, R dz) {
+        const R wxl = horner_r<R, P>(lc.cw, dx);
+        const R wyl = horner_r<R, P>(lc.cw, dy);
+        wz = horner_r<R, P>(lc.cw, dz);
+        R dxl = 0, dyl = 0;
+        dwz = 0;
+        if (MODE != 0) {
+            dxl = horner_r<R, P>(lc.cd, dx);
+            dyl = horner_r<R, P>(lc.cd, dy);
+            dwz = horner_r<R, P>(lc.cd, dz);
+        }
+        share(gbase, wxl, wyl, dxl, dyl);
+    }
+    // same, reading this lane's coefficients from the plan's table (fewer
+    // live registers: the better choice when a thread sees one particle)
+    __device__ __forceinline__ void build(const Geom<R> &g, int k, int gbase, R dx, R dy, R dz) {
+        R wxl = 0, wyl = 0, dxl = 0, dyl = 0;
+        wz = 0;
+        dwz = 0;
+        if (k < P) {
+            wxl = weight<R, P>(g.coef, k, dx);
+            wyl = weight<R, P>(g.coef, k, dy);
+            wz = weight<R, P>(g.coef, k, dz);
+            if (MODE != 0) {
+                dxl = dweight<R, P>(g.dcoef, k, dx);
+                dyl = dweight<R, P>(g.dcoef, k, dy);
+                dwz = dweight<R, P>(g.dcoef, k, dz);
+            }
+        }
+        share(gbase, wxl, wyl, dxl, dyl);
+    }
+    __device__ __forceinline__ void share(int gbase, R wxl, R wyl, R dxl, R dyl) {
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            wx[t] = __shfl_sync(0xffffffffu, wxl, gbase + t);
+            wy[t] = __shfl_sync(0xffffffffu, wyl, gbase + t);
+            if (MODE != 0) {
+                wdx[t] = __shfl_sync(0xffffffffu, dxl, gbase + t);
+                wdy[t] = __shfl_sync(0xffffffffu, dyl, gbase + t);
+            }
+        }
+    }
+};
+
+// Separable gather of one lane's z column.  load(a, c) returns the field at
+// stencil offsets (a, c, this lane's k).  Results, before the z weight:
+//  MODE 0: e0..e2 = sum_a wx[a] sum_c wy[c] E_{x,y,z}
+//  MODE 1/2: e0 = sum_a wdx[a] S0[a], e1 = sum_a wx[a] S1[a], e2 = sum_a wx[a] S0[a]
+//            with S0[a] = sum_c wy[c] phi, S1[a] = sum_c wdy[c] phi.
+template <typename R, int P, int MODE, typename Load>
+__device__ __forceinline__ void gather_column(const GroupWeights<R, P, MODE> &w, Load load, R &e0, R &e1, R &e2) {
+    e0 = e1 = e2 = R(0);
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        if (MODE == 0) {
+            R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                const vec4_t<R> v = load(a, c);
+                sx += w.wy[c] * v.x;
+                sy += w.wy[c] * v.y;
+                sz += w.wy[c] * v.z;
+            }
+            e0 += w.wx[a] * sx;
+            e1 += w.wx[a] * sy;
+            e2 += w.wx[a] * sz;
+        } else {
+            R s0 = 0, s1 = 0;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                const R v = load(a, c).x;
+                s0 += w.wy[c] * v;
+                s1 += w.wdy[c] * v;
+            }
+            e0 += w.wdx[a] * s0;
+            e1 += w.wx[a] * s1;
+            e2 += w.wx[a] * s0;
+        }
+    }
+}
+
+// Combine the 8 lanes, finish the per-particle epilogue and store.
+template <typename R, int P, int MODE>
+__device__ __forceinline__ void finish_particle(const Geom<R> &g, const SortBufs &b, bool live, int k, int j,
+                                                const GroupWeights<R, P, MODE> &w, R e0, R e1, R e2, R dx, R dy,
+                                                R dz, R qv, R *__restrict__ f, R *__restrict__ dq, R qC,
+                                                const double *c, R gself, R gbg) {
+    R e3 = R(0);
+    if (MODE == 0) {
+        e0 *= w.wz; e1 *= w.wz; e2 *= w.wz;
+    } else {
+        e0 *= w.wz; e1 *= w.wz;
+        e3 = e2 * w.wz;  // potential at the particle (MODE 2)
+        e2 *= w.dwz;
+    }
+#pragma unroll
+    for (int o = FGROUP / 2; o > 0; o >>= 1) {
+        e0 += __shfl_xor_sync(0xffffffffu, e0, o);
+        e1 += __shfl_xor_sync(0xffffffffu, e1, o);
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        if (MODE == 2) e3 += __shfl_xor_sync(0xffffffffu, e3, o);
+    }
+    if (!live || k != 0) return;
+    const int dst = b.perm[j];
+    R F0, F1, F2;
+    const R s = qC * qv;
+    if (MODE == 0) {
+        F0 = s * e0; F1 = s * e1; F2 = s * e2;
+    } else {
+        // E_a = sum dW/ddelta W W phi / h_a  (dW/dx = -dW/ddelta / h, E = -grad phi)
+        F0 = s * e0 * g.ih[0];
+        F1 = s * e1 * g.ih[1];
+        F2 = s * e2 * g.ih[2];
+        if (MODE == 1) {
+            const R q2 = qv * qv;
+            F0 += q2 * ((R)c[0] * sin2pi(dx) + (R)c[1] * sin2pi(R(2) * dx));
+            F1 += q2 * ((R)c[2] * sin2pi(dy) + (R)c[3] * sin2pi(R(2) * dy));
+            F2 += q2 * ((R)c[4] * sin2pi(dz) + (R)c[5] * sin2pi(R(2) * dz));
+        } else {
+            // gradient of the energy: dE/dx = -(uncorrected ad force)
+            F0 = -F0; F1 = -F1; F2 = -F2;
+            if (dq) dq[dst] = qC * e3 + gself * qv + gbg * (R)b.qsum[0];
+        }
+    }
+    if (f) {
+        f[3 * (int64_t)dst + 0] = F0;
+        f[3 * (int64_t)dst + 1] = F1;
+        f[3 * (int64_t)dst + 2] = F2;
+    }
+}
+
+struct SelfCoef {
+    double c[6];
+};
+
+template <typename R>
+__device__ __forceinline__ vec4_t<R> as_vec(R v) {
+    vec4_t<R> o;
+    o.x = v;
+    o.y = o.z = o.w = R(0);
+    return o;
+}
+
 template <typename R, int P, int MODE>  // MODE 0: ik force, 1: ad force, 2: energy gradient
 __global__ void __launch_bounds__(FF_THREADS) k_fieldforce(Geom<R> g, SortBufs b, int n,
                                                            const R *__restrict__ field, R *__restrict__ f,
-                                                           R *__restrict__ dq, R qC, double c0, double c1,
-                                                           double c2, double c3, double c4, double c5,
-                                                           R gself, R gbg, const double *__restrict__ qsum) {
+                                                           R *__restrict__ dq, R qC, SelfCoef sc, R gself, R gbg) {
     const int lane = threadIdx.x & 31;
     const int k = lane & (FGROUP - 1);
     const int gbase = lane & ~(FGROUP - 1);
@@ -56,110 +247,128 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce(Geom<R> g, SortBufs b
     const vec4_t<R> r = reinterpret_cast<const vec4_t<R> *>(b.rec)[j];
     int ax, ay, az;
     unpack_anchor(b.cell[j], ax, ay, az);
-    const R dx = r.x, dy = r.y, dz = r.z, qv = r.w;
-
-    R wxl = 0, wyl = 0, wzl = 0, dxl = 0, dyl = 0, dzl = 0;
-    if (k < P) {
-        wxl = weight<R, P>(g.coef, k, dx);
-        wyl = weight<R, P>(g.coef, k, dy);
-        wzl = weight<R, P>(g.coef, k, dz);
-        if (MODE != 0) {
-            dxl = dweight<R, P>(g.dcoef, k, dx);
-            dyl = dweight<R, P>(g.dcoef, k, dy);
-            dzl = dweight<R, P>(g.dcoef, k, dz);
-        }
-    }
-    R wx[P], wy[P], wdx[P], wdy[P];
-#pragma unroll
-    for (int t = 0; t < P; ++t) {
-        wx[t] = __shfl_sync(0xffffffffu, wxl, gbase + t);
-        wy[t] = __shfl_sync(0xffffffffu, wyl, gbase + t);
-        if (MODE != 0) {
-            wdx[t] = __shfl_sync(0xffffffffu, dxl, gbase + t);
-            wdy[t] = __shfl_sync(0xffffffffu, dyl, gbase + t);
-        }
-    }
-    const int My = g.M[1], Mz = g.M[2];
-    R e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+    GroupWeights<R, P, MODE> w;
+    w.build(g, k, gbase, r.x, r.y, r.z);
+    R e0 = 0, e1 = 0, e2 = 0;
     if (live && k < P) {
+        const int My = g.M[1], Mz = g.M[2];
         const int iz = wrap1(az - g.rlo + k, Mz);
-        int yoff[P];
+        int yoff[P], xoff[P];
 #pragma unroll
         for (int c = 0; c < P; ++c) yoff[c] = wrap1(ay - g.rlo + c, My) * Mz + iz;
 #pragma unroll
-        for (int a = 0; a < P; ++a) {
-            const int xoff = wrap1(ax - g.rlo + a, g.M[0]) * (My * Mz);
-#pragma unroll
-            for (int c = 0; c < P; ++c) {
-                const int p = xoff + yoff[c];
-                if (MODE == 0) {
-                    const vec4_t<R> v = ld4(field + 4 * (int64_t)p);
-                    const R w = wx[a] * wy[c];
-                    e0 += w * v.x;
-                    e1 += w * v.y;
-                    e2 += w * v.z;
-                } else {
-                    const R v = ldf(field + p);
-                    e0 += wdx[a] * wy[c] * v;
-                    e1 += wx[a] * wdy[c] * v;
-                    e2 += wx[a] * wy[c] * v;
-                    if (MODE == 2) e3 += wx[a] * wy[c] * v;
+        for (int a = 0; a < P; ++a) xoff[a] = wrap1(ax - g.rlo + a, g.M[0]) * (My * Mz);
+        gather_column<R, P, MODE>(w, [&](int a, int c) {
+            const int p = xoff[a] + yoff[c];
+            if (MODE == 0) return ld4(field + 4 * (int64_t)p);
+            return as_vec<R>(ldf(field + p));
+        }, e0, e1, e2);
+    }
+    finish_particle<R, P, MODE>(g, b, live, k, j, w, e0, e1, e2, r.x, r.y, r.z, r.w, f, dq, qC, sc.c, gself, gbg);
+}
+
+template <typename R, int P, int MODE>
+__global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, SortBufs b,
+                                                                 const R *__restrict__ field, R *__restrict__ f,
+                                                                 R *__restrict__ dq, R qC, SelfCoef sc, R gself,
+                                                                 R gbg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *brick = reinterpret_cast<R *>(smem_raw);
+
+    const int tile = blockIdx.x;
+    const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
+    if (start == end) return;
+    const int tz = tile % g.T[2];
+    const int ty = (tile / g.T[2]) % g.T[1];
+    const int tx = tile / (g.T[2] * g.T[1]);
+    const int ox = tile_origin(tx, g.T[0], g.M[0]);
+    const int oy = tile_origin(ty, g.T[1], g.M[1]);
+    const int oz = tile_origin(tz, g.T[2], g.M[2]);
+    const int Ex = tile_origin(tx + 1, g.T[0], g.M[0]) - ox + P - 1;
+    const int Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - oy + P - 1;
+    const int Ez = tile_origin(tz + 1, g.T[2], g.M[2]) - oz + P - 1;
+
+    // stage the brick: 16 lanes along z (Ez <= 14), 16 rows per pass, every
+    // copy issued before any is awaited
+    {
+        const int lz = threadIdx.x & 15, ry = threadIdx.x >> 4;
+        if (lz < Ez) {
+            const int gz = wrap1(oz - g.rlo + lz, g.M[2]);
+            for (int ex = 0; ex < Ex; ++ex) {
+                const int gx = wrap1(ox - g.rlo + ex, g.M[0]);
+                for (int ey = ry; ey < Ey; ey += FF_THREADS / 16) {
+                    const int gy = wrap1(oy - g.rlo + ey, g.M[1]);
+                    const int64_t p = ((int64_t)gx * g.M[1] + gy) * g.M[2] + gz;
+                    const int e = (ex * Ey + ey) * Ez + lz;
+                    if (MODE == 0) {
+                        if (sizeof(R) == 4) {
+                            cp_async<16>(brick + 4 * e, field + 4 * p);
+                        } else {
+                            cp_async<16>(brick + 4 * e, field + 4 * p);
+                            cp_async<16>(brick + 4 * e + 2, field + 4 * p + 2);
+                        }
+                    } else {
+                        cp_async<sizeof(R)>(brick + e, field + p);
+                    }
                 }
             }
         }
-        if (MODE == 0) {
-            e0 *= wzl; e1 *= wzl; e2 *= wzl;
-        } else {
-            e0 *= wzl; e1 *= wzl;
-            e3 = e2 * wzl;               // potential at the particle (MODE 2)
-            e2 *= dzl;
+        cp_async_wait_all();
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int k = lane & (FGROUP - 1);
+    const int gbase = lane & ~(FGROUP - 1);
+    const int grp = threadIdx.x / FGROUP;
+    const int ngrp = FF_THREADS / FGROUP;
+    LaneCoef<R, P> lc;
+    lc.load(g, k);
+    for (int base = start; base < end; base += ngrp) {
+        const int j = base + grp;
+        const bool live = j < end;
+        const int jj = live ? j : start;
+        const vec4_t<R> r = reinterpret_cast<const vec4_t<R> *>(b.rec)[jj];
+        int ax, ay, az;
+        unpack_anchor(b.cell[jj], ax, ay, az);
+        ax -= ox; ay -= oy; az -= oz;  // local anchor; brick index of stencil point = anchor + offset
+        GroupWeights<R, P, MODE> w;
+        w.build(lc, gbase, r.x, r.y, r.z);
+        R e0 = 0, e1 = 0, e2 = 0;
+        if (live && k < P) {
+            const int row0 = (ax * Ey + ay) * Ez + az + k;
+            gather_column<R, P, MODE>(w, [&](int a, int c) {
+                const int e = row0 + (a * Ey + c) * Ez;
+                if (MODE == 0) return reinterpret_cast<const vec4_t<R> *>(brick)[e];
+                return as_vec<R>(brick[e]);
+            }, e0, e1, e2);
         }
+        finish_particle<R, P, MODE>(g, b, live, k, j, w, e0, e1, e2, r.x, r.y, r.z, r.w, f, dq, qC, sc.c, gself,
+                                    gbg);
     }
-#pragma unroll
-    for (int o = FGROUP / 2; o > 0; o >>= 1) {
-        e0 += __shfl_xor_sync(0xffffffffu, e0, o);
-        e1 += __shfl_xor_sync(0xffffffffu, e1, o);
-        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-        if (MODE == 2) e3 += __shfl_xor_sync(0xffffffffu, e3, o);
-    }
-    if (!live || k != 0) return;
-    const int dst = b.perm[j];
-    R F0, F1, F2;
-    if (MODE == 0) {
-        const R s = qC * qv;
-        F0 = s * e0; F1 = s * e1; F2 = s * e2;
-    } else {
-        // E_a = sum dW/ddelta * W W phi / h_a  (dW/dx = -dW/ddelta / h, E = -grad phi)
-        const R s = qC * qv;
-        F0 = s * e0 * g.ih[0];
-        F1 = s * e1 * g.ih[1];
-        F2 = s * e2 * g.ih[2];
-        if (MODE == 1) {
-            const R q2 = qv * qv;
-            F0 += q2 * ((R)c0 * sin2pi(dx) + (R)c1 * sin2pi(R(2) * dx));
-            F1 += q2 * ((R)c2 * sin2pi(dy) + (R)c3 * sin2pi(R(2) * dy));
-            F2 += q2 * ((R)c4 * sin2pi(dz) + (R)c5 * sin2pi(R(2) * dz));
-        } else {
-            // gradient of the energy: dE/dx = -(uncorrected ad force)
-            F0 = -F0; F1 = -F1; F2 = -F2;
-            if (dq) dq[dst] = qC * e3 + gself * qv + gbg * (R)qsum[0];
-        }
-    }
-    if (f) {
-        f[3 * (int64_t)dst + 0] = F0;
-        f[3 * (int64_t)dst + 1] = F1;
-        f[3 * (int64_t)dst + 2] = F2;
-    }
+}
+
+template <typename R, int P, int MODE>
+static size_t ff_brick_bytes() {
+    const int E = TILE_B + P - 1;
+    return (size_t)E * E * E * sizeof(R) * ((MODE == 0) ? 4 : 1);
 }
 
 template <typename R, int P, int MODE>
 static void launch_ff(const Geom<R> &g, int64_t n, const SortBufs &b, const R *field, R *f, R *dq, R qC,
                       const double *c, R gs, R gb, cudaStream_t s) {
     // gb multiplies sum(q), read on the device from the sort buffers
+    SelfCoef sc;
+    for (int i = 0; i < 6; ++i) sc.c[i] = c[i];
+    if (g.ff_tiled) {
+        k_fieldforce_tiled<R, P, MODE><<<g.ntiles, FF_THREADS, ff_brick_bytes<R, P, MODE>(), s>>>(
+            g, b, field, f, dq, qC, sc, gs, gb);
+        return;
+    }
+    // one group of 8 lanes per particle, a full grid
     const int64_t threads = n * FGROUP;
     const int nb = (int)((threads + FF_THREADS - 1) / FF_THREADS);
-    k_fieldforce<R, P, MODE><<<nb, FF_THREADS, 0, s>>>(g, b, (int)n, field, f, dq, qC, c[0], c[1], c[2], c[3],
-                                                       c[4], c[5], gs, gb, b.qsum);
+    k_fieldforce<R, P, MODE><<<nb, FF_THREADS, 0, s>>>(g, b, (int)n, field, f, dq, qC, sc, gs, gb);
 }
 
 template <typename R, int MODE>
@@ -196,6 +405,34 @@ void launch_energy_grad(const Geom<R> &g, int64_t n, const SortBufs &b, const R 
     dispatch<R, 2>(g, n, b, phi, dEdx, dEdq, C, zero, (R)gself, (R)gbg, s);
 }
 
+template <typename R, int P>
+static cudaError_t prepare_ff_p() {
+    cudaError_t e = cudaFuncSetAttribute(k_fieldforce_tiled<R, P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ff_brick_bytes<R, P, 0>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fieldforce_tiled<R, P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ff_brick_bytes<R, P, 1>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fieldforce_tiled<R, P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ff_brick_bytes<R, P, 2>());
+    return e;
+}
+
+template <typename R>
+cudaError_t prepare_fieldforce(int P) {
+    switch (P) {
+        case 2: return prepare_ff_p<R, 2>();
+        case 3: return prepare_ff_p<R, 3>();
+        case 4: return prepare_ff_p<R, 4>();
+        case 5: return prepare_ff_p<R, 5>();
+        case 6: return prepare_ff_p<R, 6>();
+        case 7: return prepare_ff_p<R, 7>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t prepare_fieldforce<float>(int);
+template cudaError_t prepare_fieldforce<double>(int);
 template void launch_fieldforce<float>(const Geom<float> &, bool, int64_t, const SortBufs &, const float *,
                                        float *, float, const double *, cudaStream_t);
 template void launch_fieldforce<double>(const Geom<double> &, bool, int64_t, const SortBufs &, const double *,

@@ -15,13 +15,16 @@
 //              float/double atomic adds are compare-and-swap loops whose
 //              round trip serialises each thread's updates.
 //  ACC_FIXED   FP32C: error-free accumulation in two 32-bit integer words per
-//              brick point, hi = sum floor(v s) and lo = sum of the 16-bit
-//              rounded fractions, with s = 2^(S-16) chosen per tile from the
-//              bound sum|q_j| / vcell on any point's sum.  Integer shared
+//              brick point, hi = sum rint(v s) and lo = sum of the rounded
+//              16-bit fractions, with the power of two s chosen per tile so
+//              that one contribution stays below 2^21 and any point's sum
+//              (bounded by sum|q_j| / vcell) below 2^30.  The split uses only
+//              full-rate float adds (magic-number rounding), integer shared
 //              atomics are native and need no return value, and the sum is
-//              exact (independent of order) to 2^-45 of that bound -- the
-//              hi/lo compensation carried in integers.  lo is folded into hi
-//              every 32768 particles, so neither word can overflow.
+//              exact and independent of order to 2^-37 of the largest
+//              contribution -- the hi/lo compensation carried in integers.
+//              lo is folded into hi every 32768 particles, so neither word
+//              can overflow.
 #include "pppm_common.cuh"
 
 namespace pppm {
@@ -30,6 +33,16 @@ constexpr int RHO_THREADS = 256;
 constexpr int GROUP = 8;
 constexpr int ACC_NATIVE = 0, ACC_FIXED = 1;
 constexpr int LO_CHUNK = 32768;
+constexpr float MAGIC = 12582912.0f;      // 1.5 * 2^23
+constexpr int MAGIC_BITS = 0x4B400000;    // its bit pattern
+
+template <typename R, int P>
+__device__ __forceinline__ R horner(const R (&c)[P], R d) {
+    R w = c[P - 1];
+#pragma unroll
+    for (int l = P - 2; l >= 0; --l) w = fma_rn(w, d, c[l]);
+    return w;
+}
 
 __device__ __forceinline__ float absval(float v) { return fabsf(v); }
 __device__ __forceinline__ double absval(double v) { return fabs(v); }
@@ -38,6 +51,7 @@ template <typename R, int P, int ACC>
 __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b, R *__restrict__ rho) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float sh_red[RHO_THREADS / 32];
+    __shared__ float sh_max[RHO_THREADS / 32];
 
     const int tile = blockIdx.x;
     const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
@@ -60,24 +74,41 @@ __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b,
     unsigned int *accl = reinterpret_cast<unsigned int *>(smem_raw) + vol;
     const R *__restrict__ recp = reinterpret_cast<const R *>(b.rec);
 
-    // fixed-point scale: hi unit = 2^-(S-16), S = 46 - ceil(log2(bound))
+    // fixed-point scale s = 2^e: every contribution |v s| < 2^21 (so it can be
+    // split with the float magic-number trick) and every brick point's sum
+    // |sum v s| < 2^30 (so the hi word cannot overflow)
     float fs = 1.0f, ifs = 1.0f;
     if (ACC == ACC_FIXED) {
-        float part = 0.0f;
-        for (int j = start + threadIdx.x; j < end; j += blockDim.x)
-            part += absval((float)reinterpret_cast<const vec4_t<R> *>(recp)[j].w);
+        float part = 0.0f, pmax = 0.0f;
+        for (int j = start + threadIdx.x; j < end; j += blockDim.x) {
+            const float a = absval((float)reinterpret_cast<const vec4_t<R> *>(recp)[j].w);
+            part += a;
+            pmax = fmaxf(pmax, a);
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if ((threadIdx.x & 31) == 0) sh_red[threadIdx.x >> 5] = part;
+        for (int o = 16; o > 0; o >>= 1) {
+            part += __shfl_xor_sync(0xffffffffu, part, o);
+            pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sh_red[threadIdx.x >> 5] = part;
+            sh_max[threadIdx.x >> 5] = pmax;
+        }
         __syncthreads();
-        float bound = 0.0f;
+        float bound = 0.0f, bmax = 0.0f;
 #pragma unroll
-        for (int w = 0; w < RHO_THREADS / 32; ++w) bound += sh_red[w];
+        for (int w = 0; w < RHO_THREADS / 32; ++w) {
+            bound += sh_red[w];
+            bmax = fmaxf(bmax, sh_max[w]);
+        }
         bound = bound * (float)g.ivcell * 1.0001f + 1e-30f;
-        int e2;
-        frexpf(bound, &e2);            // bound < 2^e2
-        fs = ldexpf(1.0f, 30 - e2);    // |sum v fs| < 2^30
-        ifs = ldexpf(1.0f, e2 - 30);
+        bmax = bmax * (float)g.ivcell * 1.0001f + 1e-30f;
+        int es, em;
+        frexpf(bound, &es);  // bound < 2^es
+        frexpf(bmax, &em);   // largest contribution < 2^em
+        const int e = min(30 - es, 21 - em);
+        fs = ldexpf(1.0f, e);
+        ifs = ldexpf(1.0f, -e);
     }
 
     {
@@ -93,6 +124,10 @@ __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b,
     const int grp = threadIdx.x / GROUP;         // particle slot in the CTA
     const int ngrp = blockDim.x / GROUP;
     const R qscale = (ACC == ACC_FIXED) ? (R)(g.ivcell * (R)fs) : g.ivcell;
+    // this lane's polynomial (stencil offset k), held in registers for the CTA
+    R ck[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) ck[l] = (k < P) ? g.coef[k][l] : R(0);
 
     for (int chunk = start; chunk < end; chunk += LO_CHUNK) {
         const int cend = min(end, chunk + LO_CHUNK);
@@ -109,12 +144,7 @@ __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b,
                 ax -= ox; ay -= oy; az -= oz;        // local anchor in [0, tile size)
             }
             // lane k < P evaluates the three weights of stencil offset k
-            R wx = R(0), wy = R(0), wz = R(0);
-            if (k < P) {
-                wx = weight<R, P>(g.coef, k, dx);
-                wy = weight<R, P>(g.coef, k, dy);
-                wz = weight<R, P>(g.coef, k, dz);
-            }
+            const R wx = horner<R, P>(ck, dx), wy = horner<R, P>(ck, dy), wz = horner<R, P>(ck, dz);
             R wxq[P], wyk[P];
 #pragma unroll
             for (int t = 0; t < P; ++t) {
@@ -131,10 +161,15 @@ __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b,
                         const R v = wa * wyk[c];
                         const int e = row + (a * Ey + c) * Ez;
                         if (ACC == ACC_FIXED) {
+                            // t = v s = hi + lo / 2^16 with full-rate float ops:
+                            // adding 1.5 * 2^23 rounds |t| < 2^22 to an integer
+                            // held in the mantissa bits
                             const float t = (float)v;
-                            const float fl = floorf(t);
-                            atomicAdd(&acch[e], (int)fl);
-                            atomicAdd(&accl[e], __float2uint_rn((t - fl) * 65536.0f));
+                            const float r1 = __fadd_rn(t, MAGIC);
+                            const float fr = __fadd_rn(t, -__fadd_rn(r1, -MAGIC));  // exact
+                            const float r2 = __fmaf_rn(fr, 65536.0f, MAGIC);
+                            atomicAdd(&acch[e], __float_as_int(r1) - MAGIC_BITS);
+                            atomicAdd(&accl[e], (unsigned int)(__float_as_int(r2) - MAGIC_BITS));
                         } else {
                             atomicAdd(&accr[e], v);
                         }
@@ -145,8 +180,9 @@ __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b,
         if (ACC == ACC_FIXED && cend < end) {  // fold lo into hi before it can overflow
             __syncthreads();
             for (int e = threadIdx.x; e < vol; e += blockDim.x) {
-                acch[e] += (int)(accl[e] >> 16);
-                accl[e] &= 0xffffu;
+                const int l = (int)accl[e];  // signed sum of fractions in [-2^15, 2^15] each
+                acch[e] += l >> 16;          // floor division by 2^16
+                accl[e] = (unsigned int)(l & 0xffff);
             }
         }
         __syncthreads();
@@ -172,8 +208,9 @@ __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b,
                 R v;
                 if (ACC == ACC_FIXED) {
                     // normalise in integers (exact), then one FP32 rounding
-                    const int h = acch[e] + (int)(accl[e] >> 16);
-                    v = (R)(fmaf((float)(accl[e] & 0xffffu), 1.0f / 65536.0f, (float)h) * ifs);
+                    const int l = (int)accl[e];
+                    const int h = acch[e] + (l >> 16);
+                    v = (R)(fmaf((float)(l & 0xffff), 1.0f / 65536.0f, (float)h) * ifs);
                 } else {
                     v = accr[e];
                 }

@@ -51,6 +51,7 @@ struct pppm_plan {
     cudaGraphExec_t gexec = nullptr;
     const void *gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int64_t gkey_n = -1;
+    int variants = 0;  // bit 0: tile-staged fieldforce
     std::vector<void *> allocs;
 };
 
@@ -320,6 +321,20 @@ int enqueue(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, void
 
 bool valid_ptr_arg(int64_t n, const void *ptr) { return n == 0 || ptr != nullptr; }
 
+void drop_graph(pppm_plan *p) {
+    if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+        p->gkey_n = -1;
+    }
+}
+
+void set_variants(pppm_plan *p, int v) {
+    p->variants = v;
+    p->gf.ff_tiled = p->gd.ff_tiled = (v & 1) ? 1 : 0;
+    drop_graph(p);
+}
+
 }  // namespace
 
 extern "C" {
@@ -459,7 +474,11 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) != cudaSuccess)
         return fail(PPPM_ECUDA);
     cudaError_t pe = p->fp64 ? prepare_make_rho<double>(order, false) : prepare_make_rho<float>(order, p->comp);
+    if (pe == cudaSuccess) pe = p->fp64 ? prepare_fieldforce<double>(order) : prepare_fieldforce<float>(order);
     if (pe != cudaSuccess) return fail(PPPM_ECUDA);
+    // default kernel variants (pppm_autotune refines them on real inputs):
+    // the tile-staged fieldforce pays off once tiles hold many particles
+    set_variants(p, ((double)n_max >= 16.0 * p->ntiles) ? 1 : 0);
     if ((rc = build_tables_and_green(p))) return fail(rc);
     if ((rc = make_ffts(p))) return fail(rc);
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(PPPM_ECUDA);
@@ -654,6 +673,53 @@ int pppm_stage_times(pppm_plan *p, float ms[6]) {
         }
     }
     return PPPM_OK;
+}
+
+int pppm_set_variant(pppm_plan *p, int variants) {
+    if (!p || (variants & ~1)) return PPPM_EINVAL;
+    set_variants(p, variants);
+    return PPPM_OK;
+}
+
+int pppm_autotune(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, int *choice_out) {
+    if (!p || n < 0 || n > p->n_max) return PPPM_EINVAL;
+    if (!valid_ptr_arg(n, x) || !valid_ptr_arg(n, q) || !valid_ptr_arg(n, f)) return PPPM_EINVAL;
+    const bool graph = p->graph_on;
+    const int pmask = p->prof_mask;
+    p->graph_on = false;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best = 1e30f;
+    int best_v = p->variants;
+    int rc = PPPM_OK;
+    for (int v = 0; v <= 1 && rc == PPPM_OK; ++v) {
+        set_variants(p, v);
+        float tot = 0.0f;
+        for (int it = 0; it < 6 && rc == PPPM_OK; ++it) {  // 1 warm-up + 5 timed
+            if (cudaEventRecord(a, p->stream) != cudaSuccess) rc = PPPM_ECUDA;
+            if (!rc) rc = enqueue(p, n, x, q, f, nullptr, nullptr, 0);
+            if (!rc && cudaEventRecord(b, p->stream) != cudaSuccess) rc = PPPM_ECUDA;
+            if (!rc && cudaEventSynchronize(b) != cudaSuccess) rc = PPPM_ECUDA;
+            float ms = 0.0f;
+            if (!rc && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) rc = PPPM_ECUDA;
+            if (it > 0) tot += ms;
+        }
+        if (!rc && tot < best) {
+            best = tot;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    set_variants(p, best_v);
+    p->graph_on = graph;
+    p->prof_mask = pmask;
+    p->n_last = n;
+    p->field_is_field = true;
+    p->have_rho = true;
+    if (choice_out) *choice_out = best_v;
+    return rc;
 }
 
 int pppm_plan_info(const pppm_plan *p, int64_t info[10]) {

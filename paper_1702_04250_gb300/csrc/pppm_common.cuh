@@ -43,6 +43,7 @@ struct Geom {
     R h[3];
     R coef[MAXP][MAXP];   // coef[k][l]: weight of stencil point k, power l of delta
     R dcoef[MAXP][MAXP];  // d/ddelta of the same polynomials
+    int ff_tiled;         // fieldforce variant: 0 per-particle through L1, 1 tile-staged brick
 };
 
 template <typename R> struct Vec4;
@@ -196,6 +197,8 @@ int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec,
 void launch_energy_final(const GreenBufs &b, const EnergyConsts &ec, int green_nblk, int map_nblk,
                          double *ev_user, cudaStream_t s);
 
+template <typename R>
+cudaError_t prepare_fieldforce(int P);  // shared-memory opt-in of the tile-staged kernels
 template <typename R>
 void launch_fieldforce(const Geom<R> &g, bool ik, int64_t n, const SortBufs &b, const R *field,
                        R *f, R qC, const double *sf_coeff, cudaStream_t s);

@@ -52,9 +52,12 @@ def lib() -> ctypes.CDLL:
         L.pppm_plan_info.argtypes = [vp, ctypes.POINTER(i64)]
         L.pppm_set_profiling.argtypes = [vp, i32]
         L.pppm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        L.pppm_set_variant.argtypes = [vp, i32]
+        L.pppm_autotune.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(i32)]
         for name in ("pppm_estimate_g", "pppm_setup", "pppm_destroy", "pppm_set_stream", "pppm_set_graph",
                      "pppm_compute", "pppm_compute_host", "pppm_sync", "pppm_energy_grad", "pppm_get_array",
-                     "pppm_plan_info", "pppm_set_profiling", "pppm_stage_times"):
+                     "pppm_plan_info", "pppm_set_profiling", "pppm_stage_times", "pppm_set_variant",
+                     "pppm_autotune"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -172,6 +175,18 @@ class PPPM:
         rc = lib().pppm_compute_host(self._h, int(n), ctypes.c_void_p(x_ptr), ctypes.c_void_p(q_ptr),
                                      ctypes.c_void_p(f_ptr), ctypes.c_void_p(ev_ptr))
         _check(rc, "pppm_compute_host")
+
+    def set_variant(self, variants: int):
+        _check(lib().pppm_set_variant(self._h, int(variants)), "pppm_set_variant")
+
+    def autotune(self, x, q):
+        """Time the kernel variants on these inputs, keep the fastest; returns its bitmask."""
+        x, q = self._prep(x, q)
+        f = self.torch.empty((x.shape[0], 3), dtype=self.dtype, device=self.device)
+        choice = ctypes.c_int()
+        _check(lib().pppm_autotune(self._h, x.shape[0], _ptr(x), _ptr(q), _ptr(f), ctypes.byref(choice)),
+               "pppm_autotune")
+        return choice.value
 
     def energy_grad(self, x, q):
         """(dE/dx [n, 3], dE/dq [n], energy/virial) of the PPPM energy."""

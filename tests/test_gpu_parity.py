@@ -292,6 +292,30 @@ def test_graph_mode_and_host_path_match(torch, c2_refs):
     check_all(fh.astype(np.float64), evh, refs[("ik", "fp32")], "fp32c", "c2 host path")
 
 
+@pytest.mark.parametrize("mode", ["ik", "ad"])
+def test_fieldforce_variants_and_autotune(torch, c2_refs, mode):
+    """Both fieldforce variants (per-particle through L1, tile-staged brick)
+    match the oracle, and autotune keeps one of them with a valid result."""
+    w, g, refs = c2_refs
+    from paper_1702_04250_gb300 import pppm
+
+    x = torch.tensor(w.x, dtype=torch.float32, device="cuda")
+    q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
+    plan = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode, "fp32c", w.qqrd2e)
+    for v in (0, 1):
+        plan.set_variant(v)
+        f, ev = plan.compute(x, q)
+        plan.sync()
+        check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"variant {v} {mode}")
+    choice = plan.autotune(x, q)
+    assert choice in (0, 1)
+    f, ev = plan.compute(x, q)
+    plan.sync()
+    check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"autotuned {choice}")
+    with pytest.raises(pppm.PPPMError):
+        plan.set_variant(4)
+
+
 def test_fp64_repeatable(torch, c2_refs):
     w, g, refs = c2_refs
     outs = []
