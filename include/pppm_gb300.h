@@ -203,6 +203,30 @@ int pppm_make_rho_noalloc(const double box[3], const int mesh[3], int order, int
                           int64_t n, const float *x, const float *q, float *rho,
                           void *cuda_stream);
 
+/* ---- Batched path: many independent systems per call -------------------
+ * The same three PPPM steps (Sec. 2.1) for nsys unrelated periodic systems
+ * of uneven size, mesh and order, advanced together: each stage is one launch
+ * over all systems (the paper's mapping functions of Sec. 3.1 run per system
+ * inside it), the 3-D FFTs are one batched transform per mesh size, and with
+ * graph mode on the whole step is one CUDA graph launch.
+ *   box[nsys][3], n[nsys], order[nsys] (2..7), mesh[nsys][3] (>= order,
+ *   at most 4096 tiles of 8^3 points each, e.g. 128^3), g_ewald[nsys]
+ *   diff_mode, precision, qqrd2e, cuda_stream  as for pppm_setup (shared)
+ * pppm_batch_compute takes the systems' particles concatenated in system
+ * order: x [sum n][3], q [sum n], f [sum n][3] (device, step type), and ev
+ * (device, [nsys][7] energy + virial per system, or NULL).  Asynchronous;
+ * pppm_batch_sync reports non-finite inputs like pppm_sync. */
+typedef struct pppm_batch pppm_batch;
+int pppm_batch_setup(pppm_batch **out, int nsys, const double *box, const int64_t *n, const int *order,
+                     const int *mesh, const double *g_ewald, int diff_mode, int precision, double qqrd2e,
+                     void *cuda_stream);
+int pppm_batch_compute(pppm_batch *b, const void *x, const void *q, void *f, double *ev);
+int pppm_batch_set_graph(pppm_batch *b, int enable);
+int pppm_batch_sync(pppm_batch *b);
+/* [0] systems, [1] total particles, [2] mesh-size classes, [3] distinct orders */
+int pppm_batch_info(const pppm_batch *b, int64_t info[4]);
+int pppm_batch_destroy(pppm_batch *b);
+
 /* Static description of a status code (never NULL). */
 const char *pppm_strerror(int status);
 

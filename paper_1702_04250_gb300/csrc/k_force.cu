@@ -231,15 +231,18 @@ __device__ __forceinline__ vec4_t<R> as_vec(R v) {
     return o;
 }
 
-template <typename R, int P, int MODE>  // MODE 0: ik force, 1: ad force, 2: energy gradient
-__global__ void __launch_bounds__(FF_THREADS) k_fieldforce(Geom<R> g, SortBufs b, int n,
-                                                           const R *__restrict__ field, R *__restrict__ f,
-                                                           R *__restrict__ dq, R qC, SelfCoef sc, R gself, R gbg) {
+// MODE 0: ik force, 1: ad force, 2: energy gradient; lb = this CTA's index
+// within its system's launch; c = the six ad self-force coefficients.
+template <typename R, int P, int MODE>
+__device__ __forceinline__ void fieldforce_body(const Geom<R> &g, const SortBufs &b, int n,
+                                                const R *__restrict__ field, R *__restrict__ f,
+                                                R *__restrict__ dq, R qC, const double *c, R gself, R gbg,
+                                                int lb) {
     const int lane = threadIdx.x & 31;
     const int k = lane & (FGROUP - 1);
     const int gbase = lane & ~(FGROUP - 1);
-    const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / FGROUP;
-    const int64_t warp_first = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) / FGROUP;
+    const int64_t gid = (lb * (int64_t)blockDim.x + threadIdx.x) / FGROUP;
+    const int64_t warp_first = (lb * (int64_t)blockDim.x + (threadIdx.x & ~31)) / FGROUP;
     if (warp_first >= n) return;  // whole warp idle
     const bool live = gid < n;
     const int j = live ? (int)gid : 0;
@@ -258,13 +261,38 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce(Geom<R> g, SortBufs b
         for (int c = 0; c < P; ++c) yoff[c] = wrap1(ay - g.rlo + c, My) * Mz + iz;
 #pragma unroll
         for (int a = 0; a < P; ++a) xoff[a] = wrap1(ax - g.rlo + a, g.M[0]) * (My * Mz);
+        const int ps = g.planar_stride;
         gather_column<R, P, MODE>(w, [&](int a, int c) {
             const int p = xoff[a] + yoff[c];
-            if (MODE == 0) return ld4(field + 4 * (int64_t)p);
+            if (MODE == 0) {
+                if (ps == 0) return ld4(field + 4 * (int64_t)p);
+                vec4_t<R> v;  // three planes (batched path)
+                v.x = ldf(field + p);
+                v.y = ldf(field + p + ps);
+                v.z = ldf(field + p + 2 * (int64_t)ps);
+                v.w = R(0);
+                return v;
+            }
             return as_vec<R>(ldf(field + p));
         }, e0, e1, e2);
     }
-    finish_particle<R, P, MODE>(g, b, live, k, j, w, e0, e1, e2, r.x, r.y, r.z, r.w, f, dq, qC, sc.c, gself, gbg);
+    finish_particle<R, P, MODE>(g, b, live, k, j, w, e0, e1, e2, r.x, r.y, r.z, r.w, f, dq, qC, c, gself, gbg);
+}
+
+template <typename R, int P, int MODE>
+__global__ void __launch_bounds__(FF_THREADS) k_fieldforce(Geom<R> g, SortBufs b, int n,
+                                                           const R *__restrict__ field, R *__restrict__ f,
+                                                           R *__restrict__ dq, R qC, SelfCoef sc, R gself, R gbg) {
+    fieldforce_body<R, P, MODE>(g, b, n, field, f, dq, qC, sc.c, gself, gbg, blockIdx.x);
+}
+
+template <typename R, int P, int MODE>
+__global__ void __launch_bounds__(FF_THREADS) k_batch_fieldforce(const BatchSys<R> *__restrict__ sys, BatchList bl,
+                                                                 R *__restrict__ f, R qC) {
+    const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
+    const BatchSys<R> &S = sys[bl.ids[e]];
+    fieldforce_body<R, P, MODE>(S.g, S.sb, S.n, S.field, f + 3 * S.poff, nullptr, qC, S.sf, R(0), R(0),
+                                blockIdx.x - bl.boff[e]);
 }
 
 template <typename R, int P, int MODE>
@@ -430,6 +458,34 @@ cudaError_t prepare_fieldforce(int P) {
         default: return cudaErrorInvalidValue;
     }
 }
+
+template <typename R, int P>
+static void launch_batch_ff(const BatchSys<R> *sys, const BatchList &bl, bool ik, R *f, R qC, cudaStream_t s) {
+    if (ik)
+        k_batch_fieldforce<R, P, 0><<<bl.nblocks, FF_THREADS, 0, s>>>(sys, bl, f, qC);
+    else
+        k_batch_fieldforce<R, P, 1><<<bl.nblocks, FF_THREADS, 0, s>>>(sys, bl, f, qC);
+}
+
+// CTA counts in bl are ceil(8 n / FF_THREADS) per system (one 8-lane group per particle).
+template <typename R>
+void launch_batch_fieldforce(const BatchSys<R> *sys, const BatchList &bl, int P, bool ik, R *f, R qC,
+                             cudaStream_t s) {
+    if (bl.nblocks == 0) return;
+    switch (P) {
+        case 2: launch_batch_ff<R, 2>(sys, bl, ik, f, qC, s); break;
+        case 3: launch_batch_ff<R, 3>(sys, bl, ik, f, qC, s); break;
+        case 4: launch_batch_ff<R, 4>(sys, bl, ik, f, qC, s); break;
+        case 5: launch_batch_ff<R, 5>(sys, bl, ik, f, qC, s); break;
+        case 6: launch_batch_ff<R, 6>(sys, bl, ik, f, qC, s); break;
+        case 7: launch_batch_ff<R, 7>(sys, bl, ik, f, qC, s); break;
+        default: break;
+    }
+}
+template void launch_batch_fieldforce<float>(const BatchSys<float> *, const BatchList &, int, bool, float *, float,
+                                             cudaStream_t);
+template void launch_batch_fieldforce<double>(const BatchSys<double> *, const BatchList &, int, bool, double *,
+                                              double, cudaStream_t);
 
 template cudaError_t prepare_fieldforce<float>(int);
 template cudaError_t prepare_fieldforce<double>(int);

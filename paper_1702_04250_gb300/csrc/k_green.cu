@@ -110,9 +110,9 @@ void launch_green_setup(const GreenSetup &gs, double *G64, double *sf_sums, cuda
 // Per step
 // ---------------------------------------------------------------------------
 template <typename R, bool IK>
-__global__ void __launch_bounds__(GREEN_THREADS) k_green(Geom<R> g, const complex_t<R> *__restrict__ rhat,
-                                                         complex_t<R> *__restrict__ spec, GreenBufs b,
-                                                         EnergyConsts ec) {
+__device__ __forceinline__ void green_body(const Geom<R> &g, const complex_t<R> *__restrict__ rhat,
+                                           complex_t<R> *__restrict__ spec, const GreenBufs &b,
+                                           const EnergyConsts &ec, int lb, int nlb) {
     __shared__ double sh[7][GREEN_THREADS / 32];
     const int Mx = g.M[0], My = g.M[1], Mzh = g.Mzh;
     const int rows = Mx * My;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(GREEN_THREADS) k_green(Geom<R> g, const comple
     // one thread per spectrum element in z-rows: row = (kx, ky), lanes along kz
     const int zlanes = (Mzh >= 32) ? 32 : Mzh;
     const int rows_per_cta = GREEN_THREADS / 32;
-    for (int row = blockIdx.x * rows_per_cta + wrow; row < rows; row += gridDim.x * rows_per_cta) {
+    for (int row = lb * rows_per_cta + wrow; row < rows; row += nlb * rows_per_cta) {
         const int ix = row / My, iy = row - ix * My;
         const R kx = kv[ix], ky = kv[Mx + iy];
         const R dkx = kd[ix], dky = kd[Mx + iy];
@@ -173,9 +173,36 @@ __global__ void __launch_bounds__(GREEN_THREADS) k_green(Geom<R> g, const comple
     if (threadIdx.x < 7) {
         double v = 0.0;
         for (int w = 0; w < GREEN_THREADS / 32; ++w) v += sh[threadIdx.x][w];
-        b.part[7 * blockIdx.x + threadIdx.x] = v;
+        b.part[7 * lb + threadIdx.x] = v;
     }
 }
+
+template <typename R, bool IK>
+__global__ void __launch_bounds__(GREEN_THREADS) k_green(Geom<R> g, const complex_t<R> *__restrict__ rhat,
+                                                         complex_t<R> *__restrict__ spec, GreenBufs b,
+                                                         EnergyConsts ec) {
+    green_body<R, IK>(g, rhat, spec, b, ec, blockIdx.x, gridDim.x);
+}
+
+template <typename R, bool IK>
+__global__ void __launch_bounds__(GREEN_THREADS) k_batch_green(const BatchSys<R> *__restrict__ sys, BatchList bl) {
+    const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
+    const BatchSys<R> &S = sys[bl.ids[e]];
+    green_body<R, IK>(S.g, reinterpret_cast<const complex_t<R> *>(S.rho_hat),
+                      reinterpret_cast<complex_t<R> *>(S.spec), S.gb, S.ec, blockIdx.x - bl.boff[e],
+                      bl.boff[e + 1] - bl.boff[e]);
+}
+
+template <typename R>
+void launch_batch_green(const BatchSys<R> *sys, const BatchList &bl, bool ik, cudaStream_t s) {
+    if (bl.nblocks == 0) return;
+    if (ik)
+        k_batch_green<R, true><<<bl.nblocks, GREEN_THREADS, 0, s>>>(sys, bl);
+    else
+        k_batch_green<R, false><<<bl.nblocks, GREEN_THREADS, 0, s>>>(sys, bl);
+}
+template void launch_batch_green<float>(const BatchSys<float> *, const BatchList &, bool, cudaStream_t);
+template void launch_batch_green<double>(const BatchSys<double> *, const BatchList &, bool, cudaStream_t);
 
 template <typename R>
 int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec, const GreenBufs &b,
@@ -196,8 +223,8 @@ int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec, con
 
 // warp c < 7 sums energy/virial component c over the green partials, warp 7
 // sums q and q^2 over the particle_map partials; fixed order, one CTA.
-__global__ void __launch_bounds__(256) k_energy_final(GreenBufs b, EnergyConsts ec, int gn, int mn,
-                                                      double *ev_user) {
+__device__ __forceinline__ void energy_final_body(const GreenBufs &b, const EnergyConsts &ec, int gn, int mn,
+                                                  double *ev_user) {
     __shared__ double qs[2];
     __shared__ double comp[7];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -229,6 +256,24 @@ __global__ void __launch_bounds__(256) k_energy_final(GreenBufs b, EnergyConsts 
         if (ev_user) ev_user[threadIdx.x] = v;
     }
 }
+
+__global__ void __launch_bounds__(256) k_energy_final(GreenBufs b, EnergyConsts ec, int gn, int mn,
+                                                      double *ev_user) {
+    energy_final_body(b, ec, gn, mn, ev_user);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_batch_energy_final(const BatchSys<R> *__restrict__ sys, double *ev) {
+    const BatchSys<R> &S = sys[blockIdx.x];
+    energy_final_body(S.gb, S.ec, S.green_nb, S.map_nb, ev ? ev + 7 * blockIdx.x : nullptr);
+}
+
+template <typename R>
+void launch_batch_energy_final(const BatchSys<R> *sys, int nsys, double *ev, cudaStream_t s) {
+    if (nsys > 0) k_batch_energy_final<R><<<nsys, 256, 0, s>>>(sys, ev);
+}
+template void launch_batch_energy_final<float>(const BatchSys<float> *, int, double *, cudaStream_t);
+template void launch_batch_energy_final<double>(const BatchSys<double> *, int, double *, cudaStream_t);
 
 void launch_energy_final(const GreenBufs &b, const EnergyConsts &ec, int green_nblk, int map_nblk,
                          double *ev_user, cudaStream_t s) {

@@ -48,12 +48,12 @@ __device__ __forceinline__ float absval(float v) { return fabsf(v); }
 __device__ __forceinline__ double absval(double v) { return fabs(v); }
 
 template <typename R, int P, int ACC>
-__global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b, R *__restrict__ rho) {
+__device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &b, R *__restrict__ rho,
+                                              int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float sh_red[RHO_THREADS / 32];
     __shared__ float sh_max[RHO_THREADS / 32];
 
-    const int tile = blockIdx.x;
     const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
     if (threadIdx.x == 0) b.tile_count[tile] = 0;  // histogram is clean for the next step
     if (start == end) return;
@@ -220,6 +220,18 @@ __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b,
     }
 }
 
+template <typename R, int P, int ACC>
+__global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b, R *__restrict__ rho) {
+    make_rho_body<R, P, ACC>(g, b, rho, blockIdx.x);
+}
+
+template <typename R, int P, int ACC>
+__global__ void __launch_bounds__(RHO_THREADS) k_batch_make_rho(const BatchSys<R> *__restrict__ sys, BatchList bl) {
+    const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
+    const BatchSys<R> &S = sys[bl.ids[e]];
+    make_rho_body<R, P, ACC>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);
+}
+
 template <typename R, int P>
 static size_t brick_bytes(int acc) {
     const int E = TILE_B + P - 1;
@@ -238,10 +250,47 @@ static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, int acc, cudaS
 template <typename R, int P>
 static cudaError_t prepare_p(int acc) {
     const int bytes = (int)brick_bytes<R, P>(acc);
-    if (acc == ACC_FIXED)
-        return cudaFuncSetAttribute(k_make_rho<R, P, ACC_FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return cudaFuncSetAttribute(k_make_rho<R, P, ACC_NATIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e;
+    if (acc == ACC_FIXED) {
+        e = cudaFuncSetAttribute(k_make_rho<R, P, ACC_FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_batch_make_rho<R, P, ACC_FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     bytes);
+        return e;
+    }
+    e = cudaFuncSetAttribute(k_make_rho<R, P, ACC_NATIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_make_rho<R, P, ACC_NATIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
+    return e;
 }
+
+template <typename R, int P>
+static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc, cudaStream_t s) {
+    const size_t bytes = brick_bytes<R, P>(acc);
+    if (acc == ACC_FIXED)
+        k_batch_make_rho<R, P, ACC_FIXED><<<bl.nblocks, RHO_THREADS, bytes, s>>>(sys, bl);
+    else
+        k_batch_make_rho<R, P, ACC_NATIVE><<<bl.nblocks, RHO_THREADS, bytes, s>>>(sys, bl);
+}
+
+// The meshes of the systems in the list must have been cleared.
+template <typename R>
+void launch_batch_make_rho(const BatchSys<R> *sys, const BatchList &bl, int P, bool comp, cudaStream_t s) {
+    if (bl.nblocks == 0) return;
+    const int acc = comp ? ACC_FIXED : ACC_NATIVE;
+    switch (P) {
+        case 2: launch_batch_p<R, 2>(sys, bl, acc, s); break;
+        case 3: launch_batch_p<R, 3>(sys, bl, acc, s); break;
+        case 4: launch_batch_p<R, 4>(sys, bl, acc, s); break;
+        case 5: launch_batch_p<R, 5>(sys, bl, acc, s); break;
+        case 6: launch_batch_p<R, 6>(sys, bl, acc, s); break;
+        case 7: launch_batch_p<R, 7>(sys, bl, acc, s); break;
+        default: break;
+    }
+}
+template void launch_batch_make_rho<float>(const BatchSys<float> *, const BatchList &, int, bool, cudaStream_t);
+template void launch_batch_make_rho<double>(const BatchSys<double> *, const BatchList &, int, bool, cudaStream_t);
 
 template <typename R>
 cudaError_t prepare_make_rho(int P, bool comp) {

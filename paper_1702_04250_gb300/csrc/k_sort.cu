@@ -63,13 +63,15 @@ __device__ double block_sum(R v, double *sh) {
     return r;  // valid in thread 0
 }
 
+// lb / nlb: this CTA's index and the CTA count of its system's launch.
 template <typename R>
-__global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, const R *__restrict__ x,
-                                                              const R *__restrict__ q, SortBufs b, int big) {
+__device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const R *__restrict__ x,
+                                                  const R *__restrict__ q, const SortBufs &b, int big, int lb,
+                                                  int nlb) {
     __shared__ double sh[32];
     __shared__ int sh_scan[MAP_THREADS / 32];
     __shared__ bool last;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = lb * blockDim.x + threadIdx.x;
     R qs = R(0), qq = R(0);
     if (i < n) {
         R xi[3], qi;
@@ -86,8 +88,8 @@ __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, 
     const double s1 = block_sum<R>(qs, sh);
     const double s2 = block_sum<R>(qq, sh);
     if (threadIdx.x == 0) {
-        b.blk[2 * blockIdx.x] = s1;
-        b.blk[2 * blockIdx.x + 1] = s2;
+        b.blk[2 * lb] = s1;
+        b.blk[2 * lb + 1] = s2;
     }
     if (!big) return;  // small tile counts: k_scatter scans the histogram itself
 
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, 
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int ticket = atomicAdd(b.counter, 1u);
-        last = (ticket == gridDim.x - 1);
+        last = (ticket == nlb - 1);
     }
     __syncthreads();
     if (!last) return;
@@ -134,6 +136,12 @@ __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, 
     }
     if (hi == nt && lo < hi) b.tile_start[nt] = run;
     if (threadIdx.x == 0) *b.counter = 0u;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, const R *__restrict__ x,
+                                                              const R *__restrict__ q, SortBufs b, int big) {
+    particle_map_body<R>(g, n, x, q, b, big, blockIdx.x, gridDim.x);
 }
 
 // Block-wide exclusive scan of the tile histogram into shared memory
@@ -174,18 +182,18 @@ __device__ void scan_tiles_smem(const int *__restrict__ count, int nt, int *sh_s
 }
 
 template <typename R>
-__global__ void __launch_bounds__(MAP_THREADS) k_scatter(Geom<R> g, int n, const R *__restrict__ x,
-                                                         const R *__restrict__ q, SortBufs b, int big) {
+__device__ __forceinline__ void scatter_body(const Geom<R> &g, int n, const R *__restrict__ x,
+                                             const R *__restrict__ q, const SortBufs &b, int big, int lb) {
     __shared__ int sh_start[SMALL_TILES + 1];
     __shared__ int sh_warp[MAP_THREADS / 32];
     const int *starts = b.tile_start;
     if (!big) {
         scan_tiles_smem(b.tile_count, g.ntiles, sh_start, sh_warp);
-        if (blockIdx.x == 0)
+        if (lb == 0)
             for (int k = threadIdx.x; k <= g.ntiles; k += blockDim.x) b.tile_start[k] = sh_start[k];
         starts = sh_start;
     }
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = lb * blockDim.x + threadIdx.x;
     if (i >= n) return;
     R xi[3], qi;
     load_particle<R>(x, q, i, xi, qi);
@@ -205,6 +213,40 @@ __global__ void __launch_bounds__(MAP_THREADS) k_scatter(Geom<R> g, int n, const
     b.cell[dest] = packed;
     b.perm[dest] = i;
 }
+
+template <typename R>
+__global__ void __launch_bounds__(MAP_THREADS) k_scatter(Geom<R> g, int n, const R *__restrict__ x,
+                                                         const R *__restrict__ q, SortBufs b, int big) {
+    scatter_body<R>(g, n, x, q, b, big, blockIdx.x);
+}
+
+// Batched: every system of the list in one launch (small tile counts only).
+template <typename R>
+__global__ void __launch_bounds__(MAP_THREADS) k_batch_map(const BatchSys<R> *__restrict__ sys, BatchList bl,
+                                                           const R *__restrict__ x, const R *__restrict__ q) {
+    const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
+    const BatchSys<R> &S = sys[bl.ids[e]];
+    particle_map_body<R>(S.g, S.n, x + 3 * S.poff, q + S.poff, S.sb, 0, blockIdx.x - bl.boff[e],
+                         bl.boff[e + 1] - bl.boff[e]);
+}
+template <typename R>
+__global__ void __launch_bounds__(MAP_THREADS) k_batch_scatter(const BatchSys<R> *__restrict__ sys, BatchList bl,
+                                                               const R *__restrict__ x, const R *__restrict__ q) {
+    const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
+    const BatchSys<R> &S = sys[bl.ids[e]];
+    scatter_body<R>(S.g, S.n, x + 3 * S.poff, q + S.poff, S.sb, 0, blockIdx.x - bl.boff[e]);
+}
+
+template <typename R>
+void launch_batch_sort(const BatchSys<R> *sys, const BatchList &all, const R *x, const R *q, cudaStream_t s) {
+    if (all.nblocks == 0) return;
+    k_batch_map<R><<<all.nblocks, MAP_THREADS, 0, s>>>(sys, all, x, q);
+    k_batch_scatter<R><<<all.nblocks, MAP_THREADS, 0, s>>>(sys, all, x, q);
+}
+template void launch_batch_sort<float>(const BatchSys<float> *, const BatchList &, const float *, const float *,
+                                       cudaStream_t);
+template void launch_batch_sort<double>(const BatchSys<double> *, const BatchList &, const double *,
+                                        const double *, cudaStream_t);
 
 template <typename R>
 void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const SortBufs &b,

@@ -139,62 +139,95 @@ void release(pppm_plan *p) {
     delete p;
 }
 
-int build_tables_and_green(pppm_plan *p) {
-    const int Mx = p->M[0], My = p->M[1], Mz = p->M[2], Mzh = p->Mzh;
+}  // namespace
+
+namespace pppm {
+
+// FP64 influence function and ad self-force coefficients of one system
+// (used by single plans and by batches).  Temporary device tables are
+// allocated and freed here; G64 must hold Mx*My*(Mz/2+1) doubles.
+int green_setup_fp64(const int M[3], const double h[3], double V, int P, bool ik, double g, double C,
+                     double *G64, double sf_out[6], std::vector<double> &ktab, std::vector<double> &kdiff,
+                     cudaStream_t stream) {
+    const int Mx = M[0], My = M[1], Mzh = M[2] / 2 + 1;
     const int len = Mx + My + Mzh;
     const int dimlen[3] = {Mx, My, Mzh};
     const int off[3] = {0, Mx, Mx + My};
-    std::vector<double> ktab(len), kdiff(len), atab(5 * (size_t)len), dtab(len), btab(3 * (size_t)len);
+    ktab.assign(len, 0.0);
+    kdiff.assign(len, 0.0);
+    std::vector<double> atab(5 * (size_t)len), dtab(len), btab(3 * (size_t)len);
     double m2p[MAXP + 1];
-    spline2p_at_integers(p->P, m2p);
+    spline2p_at_integers(P, m2p);
     for (int d = 0; d < 3; ++d) {
         for (int i = 0; i < dimlen[d]; ++i) {
-            const double kappa = grid_kappa(i, p->M[d]);  // k h
-            const double k = kappa / p->h[d];
+            const double kappa = grid_kappa(i, M[d]);  // k h
+            const double k = kappa / h[d];
             ktab[off[d] + i] = k;
-            kdiff[off[d] + i] = (2 * i == p->M[d]) ? 0.0 : k;  // Nyquist derivative dropped
+            kdiff[off[d] + i] = (2 * i == M[d]) ? 0.0 : k;  // Nyquist derivative dropped
             for (int m = -2; m <= 2; ++m) {
-                const double km = k + 2.0 * M_PI * m / p->h[d];
-                const double u = alias_cross(kappa + 2.0 * M_PI * m, 0, p->P, 0);  // U1^2 at this alias
-                atab[(size_t)(m + 2) * len + off[d] + i] = std::exp(-km * km / (4.0 * p->g * p->g)) * u;
+                const double km = k + 2.0 * M_PI * m / h[d];
+                const double u = alias_cross(kappa + 2.0 * M_PI * m, 0, P, 0);  // U1^2 at this alias
+                atab[(size_t)(m + 2) * len + off[d] + i] = std::exp(-km * km / (4.0 * g * g)) * u;
             }
             double D = m2p[0];
-            for (int gg = 1; gg < p->P; ++gg) D += 2.0 * m2p[gg] * std::cos(kappa * gg);
+            for (int gg = 1; gg < P; ++gg) D += 2.0 * m2p[gg] * std::cos(kappa * gg);
             dtab[off[d] + i] = D;
-            for (int n = 0; n <= 2; ++n) btab[(size_t)n * len + off[d] + i] = alias_cross(kappa, n, p->P, 50);
+            for (int n = 0; n <= 2; ++n) btab[(size_t)n * len + off[d] + i] = alias_cross(kappa, n, P, 50);
         }
     }
-    double *d_ktab, *d_atab, *d_dtab, *d_btab;
-    int rc;
-    if ((rc = dmalloc(p, &d_ktab, sizeof(double) * len))) return rc;
-    if ((rc = dmalloc(p, &d_atab, sizeof(double) * 5 * len))) return rc;
-    if ((rc = dmalloc(p, &d_dtab, sizeof(double) * len))) return rc;
-    if ((rc = dmalloc(p, &d_btab, sizeof(double) * 3 * len))) return rc;
-    CK(cudaMemcpy(d_ktab, ktab.data(), sizeof(double) * len, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_atab, atab.data(), sizeof(double) * 5 * len, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_dtab, dtab.data(), sizeof(double) * len, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_btab, btab.data(), sizeof(double) * 3 * len, cudaMemcpyHostToDevice));
-    GreenSetup gs{};
-    for (int d = 0; d < 3; ++d) {
-        gs.M[d] = p->M[d];
-        gs.h[d] = p->h[d];
+    double *tmp = nullptr;  // ktab | atab | dtab | btab | sf sums
+    const size_t words = (size_t)len * 10 + 6;
+    if (cudaMalloc(&tmp, words * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return PPPM_ENOMEM;
     }
-    gs.Mzh = Mzh;
-    gs.P = p->P;
-    gs.ik = p->ik;
-    gs.g = p->g;
-    gs.ktab = d_ktab;
-    gs.atab = d_atab;
-    gs.dtab = d_dtab;
-    gs.btab = d_btab;
-    launch_green_setup(gs, p->G64, p->d_sf, p->stream);
-    CK(cudaGetLastError());
-    double sums[6];
-    CK(cudaMemcpyAsync(sums, p->d_sf, sizeof(sums), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
+    double *d_ktab = tmp, *d_atab = tmp + len, *d_dtab = d_atab + 5 * (size_t)len, *d_btab = d_dtab + len;
+    double *d_sf = d_btab + 3 * (size_t)len;
+    int rc = PPPM_OK;
+    double sums[6] = {0, 0, 0, 0, 0, 0};
+    do {
+        if (cudaMemcpy(d_ktab, ktab.data(), sizeof(double) * len, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d_atab, atab.data(), sizeof(double) * 5 * len, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d_dtab, dtab.data(), sizeof(double) * len, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d_btab, btab.data(), sizeof(double) * 3 * len, cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = PPPM_ECUDA;
+            break;
+        }
+        GreenSetup gs{};
+        for (int d = 0; d < 3; ++d) {
+            gs.M[d] = M[d];
+            gs.h[d] = h[d];
+        }
+        gs.Mzh = Mzh;
+        gs.P = P;
+        gs.ik = ik;
+        gs.g = g;
+        gs.ktab = d_ktab;
+        gs.atab = d_atab;
+        gs.dtab = d_dtab;
+        gs.btab = d_btab;
+        launch_green_setup(gs, G64, d_sf, stream);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(sums, d_sf, sizeof(sums), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess)
+            rc = PPPM_ECUDA;
+    } while (0);
+    cudaFree(tmp);
+    if (rc) return rc;
     for (int a = 0; a < 3; ++a)
-        for (int n = 1; n <= 2; ++n)
-            p->sf[a * 2 + n - 1] = 2.0 * M_PI * n * p->C / (p->h[a] * p->V) * sums[a * 2 + n - 1];
+        for (int n = 1; n <= 2; ++n) sf_out[a * 2 + n - 1] = 2.0 * M_PI * n * C / (h[a] * V) * sums[a * 2 + n - 1];
+    return PPPM_OK;
+}
+
+}  // namespace pppm
+
+namespace {
+
+int build_tables_and_green(pppm_plan *p) {
+    const int len = p->M[0] + p->M[1] + p->Mzh;
+    std::vector<double> ktab, kdiff;
+    int rc = green_setup_fp64(p->M, p->h, p->V, p->P, p->ik, p->g, p->C, p->G64, p->sf, ktab, kdiff, p->stream);
+    if (rc) return rc;
     // step-type copies: G / M, wavenumbers
     const double sc = 1.0 / (double)p->Mtot;
     k_scale_green<<<256, 256, 0, p->stream>>>(p->G64, p->fp64 ? nullptr : (float *)p->Gs,

@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 #include <cufft.h>
 
@@ -44,6 +45,7 @@ struct Geom {
     R coef[MAXP][MAXP];   // coef[k][l]: weight of stencil point k, power l of delta
     R dcoef[MAXP][MAXP];  // d/ddelta of the same polynomials
     int ff_tiled;         // fieldforce variant: 0 per-particle through L1, 1 tile-staged brick
+    int planar_stride;    // ik field layout: 0 interleaved (Ex,Ey,Ez,pad); > 0 three planes this far apart
 };
 
 template <typename R> struct Vec4;
@@ -208,6 +210,59 @@ void launch_energy_grad(const Geom<R> &g, int64_t n, const SortBufs &b, const R 
                         R *dEdq, R C, const double *qsum, double gself, double gbg,
                         cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Batched path: many independent systems in one launch per stage.  Each
+// system has its own geometry, sort buffers and mesh slices; a batched launch
+// covers a list of systems (ids) whose CTAs are laid out back to back
+// (boff = prefix sums of per-system CTA counts, length L + 1), and every CTA
+// finds its system by binary search and runs the single-system body with its
+// local CTA index.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct BatchSys {
+    Geom<R> g;
+    SortBufs sb;
+    GreenBufs gb;
+    EnergyConsts ec;
+    double sf[6];          // ad self-force coefficients c[a][n-1]
+    R *rho;                // [M] mesh slice
+    void *rho_hat;         // [Mhalf] complex
+    void *spec;            // [3 or 1][Mhalf] complex
+    R *field;              // [M][4] (ik) or [M]
+    int64_t poff;          // first particle of this system in the caller's arrays
+    int n;                 // particles
+    int map_nb, green_nb;  // CTAs of its map/scatter and green launches
+};
+struct BatchList {
+    const int *ids;   // [L] system ids
+    const int *boff;  // [L + 1] CTA offsets
+    int L;
+    int nblocks;      // boff[L]
+};
+
+__device__ __forceinline__ int batch_entry(const int *__restrict__ boff, int L, int b) {
+    int lo = 0, hi = L;  // largest e with boff[e] <= b
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&boff[mid]) <= b) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename R>
+void launch_batch_sort(const BatchSys<R> *sys, const BatchList &all, const R *x, const R *q, cudaStream_t s);
+template <typename R>
+void launch_batch_make_rho(const BatchSys<R> *sys, const BatchList &byP, int P, bool compensated,
+                           cudaStream_t s);
+template <typename R>
+void launch_batch_green(const BatchSys<R> *sys, const BatchList &all, bool ik, cudaStream_t s);
+template <typename R>
+void launch_batch_energy_final(const BatchSys<R> *sys, int nsys, double *ev, cudaStream_t s);
+template <typename R>
+void launch_batch_fieldforce(const BatchSys<R> *sys, const BatchList &byP, int P, bool ik, R *f, R qC,
+                             cudaStream_t s);
+
 // Setup: G(k) in FP64 over the half spectrum and the ad self-force sums.
 struct GreenSetup {
     int M[3], Mzh, P;
@@ -219,5 +274,10 @@ struct GreenSetup {
     const double *btab;    // [3 n][Mx + My + Mzh] self-force alias sums, n = 0,1,2
 };
 void launch_green_setup(const GreenSetup &gs, double *G64, double *sf_sums, cudaStream_t s);
+// Host driver of the above for one system (pppm_api.cu): G64 on the device,
+// the ad self-force coefficients c[a][n-1] and the wavenumber tables on the host.
+int green_setup_fp64(const int M[3], const double h[3], double V, int P, bool ik, double g, double C,
+                     double *G64, double sf_out[6], std::vector<double> &ktab, std::vector<double> &kdiff,
+                     cudaStream_t stream);
 
 }  // namespace pppm

@@ -251,3 +251,80 @@ class PPPM:
         _check(lib().pppm_get_array(self._h, ARRAYS[name], out.ctypes.data_as(ctypes.c_void_p), out.nbytes, 1),
                f"pppm_get_array({name})")
         return out
+
+
+class PPPMBatch:
+    """Many independent systems per call (one launch per stage, one graph)."""
+
+    def __init__(self, systems, mode="ik", precision="fp32c", qqrd2e=1.0, stream=None, graph=False, device=None):
+        """systems: list of dicts with keys box, n, order, mesh, g_ewald."""
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        ns = len(systems)
+        self.nsys = ns
+        self.n = [int(s["n"]) for s in systems]
+        self.offsets = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
+        box = (ctypes.c_double * (3 * ns))(*[float(v) for s in systems for v in s["box"]])
+        nn = (ctypes.c_int64 * ns)(*self.n)
+        order = (ctypes.c_int * ns)(*[int(s["order"]) for s in systems])
+        mesh = (ctypes.c_int * (3 * ns))(*[int(v) for s in systems for v in s["mesh"]])
+        gew = (ctypes.c_double * ns)(*[float(s["g_ewald"]) for s in systems])
+        if stream is None:
+            stream = torch.cuda.Stream(device=self.device) if graph else torch.cuda.current_stream(self.device)
+        self.stream = stream
+        L = lib()
+        L.pppm_batch_setup.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]
+        L.pppm_batch_compute.argtypes = [ctypes.c_void_p] * 5
+        L.pppm_batch_set_graph.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.pppm_batch_sync.argtypes = [ctypes.c_void_p]
+        L.pppm_batch_destroy.argtypes = [ctypes.c_void_p]
+        L.pppm_batch_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+        for nm in ("pppm_batch_setup", "pppm_batch_compute", "pppm_batch_set_graph", "pppm_batch_sync",
+                   "pppm_batch_destroy", "pppm_batch_info"):
+            getattr(L, nm).restype = ctypes.c_int
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(L.pppm_batch_setup(ctypes.byref(h), ns, ctypes.cast(box, ctypes.c_void_p),
+                                      ctypes.cast(nn, ctypes.c_void_p), ctypes.cast(order, ctypes.c_void_p),
+                                      ctypes.cast(mesh, ctypes.c_void_p), ctypes.cast(gew, ctypes.c_void_p),
+                                      MODES[mode], PRECISIONS[precision], float(qqrd2e),
+                                      ctypes.c_void_p(stream.cuda_stream)), "pppm_batch_setup")
+        self._h = h
+        self.ev = torch.zeros((ns, 7), dtype=torch.float64, device=self.device)
+        if graph:
+            _check(L.pppm_batch_set_graph(self._h, 1), "pppm_batch_set_graph")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pppm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        a = (ctypes.c_int64 * 4)()
+        _check(lib().pppm_batch_info(self._h, a), "pppm_batch_info")
+        return dict(zip(("systems", "particles", "mesh_classes", "orders"), list(a)))
+
+    def compute(self, x, q, f=None):
+        """x [sum n, 3], q [sum n] concatenated in system order -> (f, ev [nsys, 7])."""
+        torch = self.torch
+        x = torch.as_tensor(x, device=self.device, dtype=self.dtype).contiguous()
+        q = torch.as_tensor(q, device=self.device, dtype=self.dtype).contiguous()
+        if f is None:
+            f = torch.empty((x.shape[0], 3), dtype=self.dtype, device=self.device)
+        _check(lib().pppm_batch_compute(self._h, _ptr(x), _ptr(q), _ptr(f), _ptr(self.ev)), "pppm_batch_compute")
+        return f, self.ev
+
+    def sync(self):
+        _check(lib().pppm_batch_sync(self._h), "pppm_batch_sync")
