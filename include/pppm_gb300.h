@@ -45,7 +45,11 @@ enum pppm_status {
     PPPM_ECUFFT = 4,      /* a cuFFT call failed */
     PPPM_ENONFINITE = 5,  /* a position or charge was NaN/Inf (reported by pppm_sync) */
     PPPM_ETIMEOUT = 6,    /* a bounded device wait gave up */
-    PPPM_ENOTREADY = 7    /* the requested quantity was not computed by the last call */
+    PPPM_ENOTREADY = 7,   /* the requested quantity was not computed by the last call */
+    PPPM_EINTERNAL = 8    /* a device-side consistency check failed (a particle's stencil
+                             anchor outside its tile, a sort slot out of range): the kernel
+                             skipped that work, so the call's results are invalid
+                             (reported by pppm_sync) */
 };
 
 /* Differentiation mode (Sec. 2.1 / Sec. 3.1): ik takes the gradient in
@@ -117,8 +121,9 @@ int pppm_compute_host(pppm_plan *p, int64_t n, const void *x_host, const void *q
                       void *f_host, double *ev_host);
 
 /* Synchronise the plan's stream and report (then clear) the device error
- * word: PPPM_ENONFINITE if a non-finite position or charge was seen by any
- * compute since the last sync, else PPPM_OK (or PPPM_ECUDA). */
+ * word: PPPM_EINTERNAL if a device-side consistency check failed,
+ * PPPM_ENONFINITE if a non-finite position or charge was seen by any compute
+ * since the last sync, else PPPM_OK (or PPPM_ECUDA). */
 int pppm_sync(pppm_plan *p);
 
 /* Turn CUDA-graph launch of pppm_compute on (1) or off (0). */
@@ -166,8 +171,12 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
 /* Kernel variants of a plan (Sec. 3.1's mapping functions have one result
  * and several implementations; the paper picks them by measurement, and so
  * does this).  Bit 0: fieldforce stages the tile's field brick in shared
- * memory (1) or reads the field through L1 per particle (0).
- * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits).
+ * memory (1) or reads the field through L1 per particle (0).  Bit 1
+ * (mesh tiles 16 points long along z) is reserved: refused with PPPM_EINVAL
+ * by every plan of this build.  Default: bit 0 for ik plans whose n_max is at
+ * least 16 per tile, else 0.
+ * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a
+ * combination the plan does not allow).
  * pppm_autotune times every variant on the caller's inputs (one warm-up and
  * five timed pppm_compute steps each, synchronous, graph mode off while it
  * runs), keeps the fastest, writes its bitmask to choice_out (nullable), and
@@ -175,7 +184,7 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
 int pppm_set_variant(pppm_plan *p, int variants);
 int pppm_autotune(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, int *choice_out);
 
-/* Plan facts: [0..2] mesh, [3] order, [4] ntiles, [5] tile edge B,
+/* Plan facts: [0..2] mesh, [3] order, [4] ntiles, [5] widest tile along z,
  * [6] diff mode, [7] precision, [8] n_max, [9] last n. */
 int pppm_plan_info(const pppm_plan *p, int64_t info[10]);
 
@@ -229,6 +238,11 @@ int pppm_batch_destroy(pppm_batch *b);
 
 /* Static description of a status code (never NULL). */
 const char *pppm_strerror(int status);
+
+/* Name and description of the last CUDA runtime error this library saw on
+ * the calling thread, or of the pending (sticky) CUDA error, "" if none.
+ * Points to thread-local storage that the next call overwrites. */
+const char *pppm_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

@@ -250,10 +250,13 @@ __device__ __forceinline__ void fieldforce_body(const Geom<R> &g, const SortBufs
     const vec4_t<R> r = reinterpret_cast<const vec4_t<R> *>(b.rec)[j];
     int ax, ay, az;
     unpack_anchor(b.cell[j], ax, ay, az);
+    const bool inmesh = (unsigned)ax < (unsigned)g.M[0] && (unsigned)ay < (unsigned)g.M[1] &&
+                        (unsigned)az < (unsigned)g.M[2];
+    if (live && !inmesh && k == 0) atomicOr(b.err, ERR_INTERNAL);  // skipped, reported
     GroupWeights<R, P, MODE> w;
     w.build(g, k, gbase, r.x, r.y, r.z);
     R e0 = 0, e1 = 0, e2 = 0;
-    if (live && k < P) {
+    if (live && inmesh && k < P) {
         const int My = g.M[1], Mz = g.M[2];
         const int iz = wrap1(az - g.rlo + k, Mz);
         int yoff[P], xoff[P];
@@ -360,10 +363,13 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, Sort
         int ax, ay, az;
         unpack_anchor(b.cell[jj], ax, ay, az);
         ax -= ox; ay -= oy; az -= oz;  // local anchor; brick index of stencil point = anchor + offset
+        const bool intile = (unsigned)ax <= (unsigned)(Ex - P) && (unsigned)ay <= (unsigned)(Ey - P) &&
+                            (unsigned)az <= (unsigned)(Ez - P);
+        if (live && !intile && k == 0) atomicOr(b.err, ERR_INTERNAL);  // skipped, reported
         GroupWeights<R, P, MODE> w;
         w.build(lc, gbase, r.x, r.y, r.z);
         R e0 = 0, e1 = 0, e2 = 0;
-        if (live && k < P) {
+        if (live && intile && k < P) {
             const int row0 = (ax * Ey + ay) * Ez + az + k;
             gather_column<R, P, MODE>(w, [&](int a, int c) {
                 const int e = row0 + (a * Ey + c) * Ez;

@@ -75,7 +75,7 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
     R qs = R(0), qq = R(0);
     if (i < n) {
         R xi[3], qi;
-        if (!load_particle<R>(x, q, i, xi, qi)) atomicOr(b.err, 1);
+        if (!load_particle<R>(x, q, i, xi, qi)) atomicOr(b.err, ERR_NONFINITE);
         int a[3];
         R d[3];
         anchors<R>(g, xi, a, d);
@@ -204,6 +204,10 @@ __device__ __forceinline__ void scatter_body(const Geom<R> &g, int n, const R *_
     int s[3];
     unpack_anchor(packed, s[0], s[1], s[2]);
     const int dest = starts[tile_index<R>(g, s)] + b.rank[i];
+    if ((unsigned int)dest >= (unsigned int)n) {  // a stale histogram: skip, report
+        atomicOr(b.err, ERR_INTERNAL);
+        return;
+    }
     vec4_t<R> r;
     r.x = d[0];
     r.y = d[1];

@@ -12,6 +12,23 @@
 
 #include "pppm_common.cuh"
 
+namespace pppm {
+static thread_local cudaError_t last_cuda_err = cudaSuccess;
+static thread_local const char *last_cuda_stage = nullptr;
+void note_cuda_error(cudaError_t e) {
+    if (e != cudaSuccess) last_cuda_err = e;
+}
+// PPPM_SYNC_CHECK=1 in the environment: synchronise after every stage of a
+// step and name the stage that saw a CUDA error (diagnosis; slow).
+static bool sync_check_on() {
+    static const bool on = [] {
+        const char *v = std::getenv("PPPM_SYNC_CHECK");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+}  // namespace pppm
+
 using namespace pppm;
 
 struct pppm_plan {
@@ -21,7 +38,8 @@ struct pppm_plan {
     bool fp64 = false, comp = false, ik = true;
     int M[3] = {0, 0, 0}, Mzh = 0;
     int64_t Mtot = 0, Mhalf = 0;
-    int T[3] = {0, 0, 0}, ntiles = 0;
+    int T[3] = {0, 0, 0}, TE[3] = {0, 0, 0}, ntiles = 0;
+    int ntiles_alloc = 0;              // tile arrays are sized for 8^3 tiles, the most numerous shape
     double box[3] = {0, 0, 0}, h[3] = {0, 0, 0}, g = 0, C = 0, V = 0, vcell = 0;
     int64_t n_max = 0, n_last = -1;
     Geom<float> gf{};
@@ -51,7 +69,7 @@ struct pppm_plan {
     cudaGraphExec_t gexec = nullptr;
     const void *gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int64_t gkey_n = -1;
-    int variants = 0;  // bit 0: tile-staged fieldforce
+    int variants = 0;  // bit 0: tile-staged fieldforce, bit 1: long tiles along z
     std::vector<void *> allocs;
 };
 
@@ -59,6 +77,7 @@ namespace {
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return PPPM_OK;
+    note_cuda_error(e);
     if (e == cudaErrorMemoryAllocation) return PPPM_ENOMEM;
     return PPPM_ECUDA;
 }
@@ -103,6 +122,7 @@ void fill_geom(pppm_plan *p, Geom<R> &g, const double coef[MAXP][MAXP], const do
     for (int d = 0; d < 3; ++d) {
         g.M[d] = p->M[d];
         g.T[d] = p->T[d];
+        g.TE[d] = p->TE[d];
         g.L[d] = (R)p->box[d];
         g.iL[d] = (R)(1.0 / p->box[d]);
         const double ih = (double)p->M[d] / p->box[d];
@@ -293,7 +313,7 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
     // External records stay real timing records inside a captured graph
     // (a plain record during capture only becomes a dependency edge).
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (prof) CK(cudaStreamIsCapturing(s, &cap));
+    if (prof || sync_check_on()) CK(cudaStreamIsCapturing(s, &cap));
     // boundary i opens stage i and closes stage i - 1
     auto mark = [&](int i) {
         const bool need = ((pmask >> i) & 1) || (i > 0 && ((pmask >> (i - 1)) & 1));
@@ -303,16 +323,30 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
         else
             cudaEventRecord(p->prof[i], s);
     };
+    const bool chk = sync_check_on() && cap == cudaStreamCaptureStatusNone;
+    auto check = [&](const char *stage) -> int {
+        if (!chk) return PPPM_OK;
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->side);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) return PPPM_OK;
+        last_cuda_stage = stage;
+        return cuda_status(e);
+    };
+    int rc;
     mark(0);
     launch_sort<R>(g, n, (const R *)x, (const R *)q, p->sb, s);
+    if ((rc = check("particle_map/scatter"))) return rc;
     mark(1);
     launch_make_rho<R>(g, n, p->sb, (R *)p->rho, p->comp, s);
+    if ((rc = check("make_rho"))) return rc;
     mark(2);
-    int rc;
     if ((rc = exec_r2c(p))) return rc;
+    if ((rc = check("forward FFT"))) return rc;
     mark(3);
     const bool ik_spec = (kind == 0) && p->ik;
     const int gn = launch_green<R>(g, ik_spec, p->rho_hat, p->spec, p->gb, p->ec, s);
+    if ((rc = check("green"))) return rc;
     mark(4);
     const int mn = (int)((n + 255) / 256);
     if (kind == 0) {
@@ -324,7 +358,9 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
     } else {
         launch_energy_final(p->gb, p->ec, gn, mn, ev, s);  // dE/dq needs sum q first
     }
+    if ((rc = check("energy_final"))) return rc;
     if ((rc = exec_c2r(p, ik_spec))) return rc;
+    if ((rc = check("inverse FFT"))) return rc;
     mark(5);
     if (kind == 0) {
         launch_fieldforce<R>(g, p->ik, n, p->sb, (const R *)p->field, (R *)f, (R)p->C, p->sf, s);
@@ -334,6 +370,7 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
         launch_energy_grad<R>(g, n, p->sb, (const R *)p->field, (R *)f, (R *)dq, (R)p->C, p->sb.qsum, gself,
                               gbg, s);
     }
+    if ((rc = check("fieldforce"))) return rc;
     mark(6);
     if (kind == 0) CK(cudaStreamWaitEvent(s, p->join, 0));
     p->prof_valid = pmask;
@@ -362,9 +399,25 @@ void drop_graph(pppm_plan *p) {
     }
 }
 
+bool variant_ok(const pppm_plan *p, int v) {
+    if (v & ~3) return false;
+    if ((v & 2) && !long_tiles_allowed(p->P, p->comp)) return false;
+    return !((v & 1) && (v & 2));  // the tile-staged fieldforce brick holds 8^3 tiles only
+}
+
+// Variant bits: 0 tile-staged fieldforce, 1 long tiles (16 along z).  The
+// tile shape changes the sort; the histogram is cleared for the new shape.
 void set_variants(pppm_plan *p, int v) {
     p->variants = v;
+    tile_shape(p->M, (v & 2) != 0, p->T, p->TE);
+    p->ntiles = p->T[0] * p->T[1] * p->T[2];
+    for (int d = 0; d < 3; ++d) {
+        p->gf.T[d] = p->gd.T[d] = p->T[d];
+        p->gf.TE[d] = p->gd.TE[d] = p->TE[d];
+    }
+    p->gf.ntiles = p->gd.ntiles = p->ntiles;
     p->gf.ff_tiled = p->gd.ff_tiled = (v & 1) ? 1 : 0;
+    if (p->sb.tile_count) cudaMemsetAsync(p->sb.tile_count, 0, 4 * (size_t)p->ntiles_alloc, p->stream);
     drop_graph(p);
 }
 
@@ -382,8 +435,22 @@ const char *pppm_strerror(int s) {
         case PPPM_ENONFINITE: return "non-finite position or charge";
         case PPPM_ETIMEOUT: return "device wait timed out";
         case PPPM_ENOTREADY: return "quantity not computed by the last call";
+        case PPPM_EINTERNAL: return "device consistency check failed (results invalid)";
         default: return "unknown status";
     }
+}
+
+
+const char *pppm_last_cuda_error(void) {
+    static thread_local char buf[256];
+    cudaError_t e = pppm::last_cuda_err != cudaSuccess ? pppm::last_cuda_err : cudaPeekAtLastError();
+    if (e == cudaSuccess) return "";
+    if (pppm::last_cuda_stage)
+        snprintf(buf, sizeof(buf), "%s: %s (after %s)", cudaGetErrorName(e), cudaGetErrorString(e),
+                 pppm::last_cuda_stage);
+    else
+        snprintf(buf, sizeof(buf), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return buf;
 }
 
 int pppm_estimate_g(double rel_acc, double r_cut, int64_t n, double q2, const double box[3], double *g_out) {
@@ -427,12 +494,13 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         p->M[d] = mesh[d];
         p->box[d] = box[d];
         p->h[d] = box[d] / mesh[d];
-        p->T[d] = (mesh[d] + TILE_B - 1) / TILE_B;
     }
+    tile_shape(p->M, false, p->T, p->TE);
     p->Mzh = mesh[2] / 2 + 1;
     p->Mtot = (int64_t)mesh[0] * mesh[1] * mesh[2];
     p->Mhalf = (int64_t)mesh[0] * mesh[1] * p->Mzh;
     p->ntiles = p->T[0] * p->T[1] * p->T[2];
+    p->ntiles_alloc = p->ntiles;
     p->V = box[0] * box[1] * box[2];
     p->vcell = p->h[0] * p->h[1] * p->h[2];
 
@@ -448,8 +516,8 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     do {
         if ((rc = dmalloc(p, &p->sb.anchor, 4 * nm))) break;
         if ((rc = dmalloc(p, &p->sb.rank, 4 * nm))) break;
-        if ((rc = dmalloc(p, &p->sb.tile_count, 4 * (size_t)p->ntiles))) break;
-        if ((rc = dmalloc(p, &p->sb.tile_start, 4 * ((size_t)p->ntiles + 1)))) break;
+        if ((rc = dmalloc(p, &p->sb.tile_count, 4 * (size_t)p->ntiles_alloc))) break;
+        if ((rc = dmalloc(p, &p->sb.tile_start, 4 * ((size_t)p->ntiles_alloc + 1)))) break;
         if ((rc = dmalloc(p, &p->sb.perm, 4 * nm))) break;
         if ((rc = dmalloc(p, &p->sb.rec, 4 * rs * nm))) break;
         if ((rc = dmalloc(p, &p->sb.cell, 4 * nm))) break;
@@ -497,7 +565,7 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         release(p);
         return code;
     };
-    if (cudaMemsetAsync(p->sb.tile_count, 0, 4 * (size_t)p->ntiles, p->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(p->sb.tile_count, 0, 4 * (size_t)p->ntiles_alloc, p->stream) != cudaSuccess ||
         cudaMemsetAsync(p->counters, 0, 4 * sizeof(unsigned int), p->stream) != cudaSuccess ||
         cudaMemsetAsync(p->sb.err, 0, 4 * sizeof(int), p->stream) != cudaSuccess ||
         cudaMemsetAsync(p->ev, 0, 8 * sizeof(double), p->stream) != cudaSuccess)
@@ -510,8 +578,9 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     if (pe == cudaSuccess) pe = p->fp64 ? prepare_fieldforce<double>(order) : prepare_fieldforce<float>(order);
     if (pe != cudaSuccess) return fail(PPPM_ECUDA);
     // default kernel variants (pppm_autotune refines them on real inputs):
-    // the tile-staged fieldforce pays off once tiles hold many particles
-    set_variants(p, ((double)n_max >= 16.0 * p->ntiles) ? 1 : 0);
+    // the ik field (16 bytes a point) is worth staging per tile once tiles
+    // hold enough particles; the ad potential (4 bytes) reads best through L1
+    set_variants(p, (p->ik && (double)n_max >= 16.0 * p->ntiles) ? 1 : 0);
     if ((rc = build_tables_and_green(p))) return fail(rc);
     if ((rc = make_ffts(p))) return fail(rc);
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(PPPM_ECUDA);
@@ -593,7 +662,7 @@ int pppm_sync(pppm_plan *p) {
     CK(cudaMemcpy(&err, p->sb.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         CK(cudaMemset(p->sb.err, 0, sizeof(int)));
-        return PPPM_ENONFINITE;
+        return (err & ERR_INTERNAL) ? PPPM_EINTERNAL : PPPM_ENONFINITE;
     }
     return PPPM_OK;
 }
@@ -709,7 +778,7 @@ int pppm_stage_times(pppm_plan *p, float ms[6]) {
 }
 
 int pppm_set_variant(pppm_plan *p, int variants) {
-    if (!p || (variants & ~1)) return PPPM_EINVAL;
+    if (!p || !variant_ok(p, variants)) return PPPM_EINVAL;
     set_variants(p, variants);
     return PPPM_OK;
 }
@@ -726,7 +795,8 @@ int pppm_autotune(pppm_plan *p, int64_t n, const void *x, const void *q, void *f
     float best = 1e30f;
     int best_v = p->variants;
     int rc = PPPM_OK;
-    for (int v = 0; v <= 1 && rc == PPPM_OK; ++v) {
+    for (int v = 0; v <= 3 && rc == PPPM_OK; ++v) {
+        if (!variant_ok(p, v)) continue;
         set_variants(p, v);
         float tot = 0.0f;
         for (int it = 0; it < 6 && rc == PPPM_OK; ++it) {  // 1 warm-up + 5 timed
@@ -762,7 +832,7 @@ int pppm_plan_info(const pppm_plan *p, int64_t info[10]) {
     info[2] = p->M[2];
     info[3] = p->P;
     info[4] = p->ntiles;
-    info[5] = TILE_B;
+    info[5] = p->TE[2];
     info[6] = p->mode;
     info[7] = p->prec;
     info[8] = p->n_max;

@@ -93,14 +93,13 @@ void batch_release(pppm_batch *b) {
 }
 
 template <typename R>
-void fill_geom_b(Geom<R> &g, const double box[3], const int M[3], int P) {
+void fill_geom_b(Geom<R> &g, const double box[3], const int M[3], int P, bool comp) {
     double coef[MAXP][MAXP], dcoef[MAXP][MAXP];
     stencil_polynomials(P, coef, dcoef);
     double vcell = 1.0;
     for (int d = 0; d < 3; ++d) {
         const double ih = (double)M[d] / box[d];
         g.M[d] = M[d];
-        g.T[d] = (M[d] + TILE_B - 1) / TILE_B;
         g.L[d] = (R)box[d];
         g.iL[d] = (R)(1.0 / box[d]);
         g.ih[d] = (R)ih;
@@ -108,6 +107,7 @@ void fill_geom_b(Geom<R> &g, const double box[3], const int M[3], int P) {
         g.h[d] = (R)(box[d] / M[d]);
         vcell *= box[d] / M[d];
     }
+    tile_shape(M, long_tiles_allowed(P, comp), g.T, g.TE);
     g.Mzh = M[2] / 2 + 1;
     g.ntiles = g.T[0] * g.T[1] * g.T[2];
     g.P = P;
@@ -168,7 +168,7 @@ int batch_build(pppm_batch *b, const double *box, const int64_t *n, const int *o
         BatchSys<R> &S = hs[s];
         const int *M = mesh + 3 * s;
         const double *bx = box + 3 * s;
-        fill_geom_b<R>(S.g, bx, M, order[s]);
+        fill_geom_b<R>(S.g, bx, M, order[s], b->comp);
         if (S.g.ntiles > BATCH_SMALL_TILES) return PPPM_EINVAL;
         S.n = (int)n[s];
         S.poff = poff;
@@ -462,12 +462,16 @@ int pppm_batch_compute(pppm_batch *b, const void *x, const void *q, void *f, dou
 
 int pppm_batch_sync(pppm_batch *b) {
     if (!b) return PPPM_EINVAL;
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return PPPM_ECUDA;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
     int err = 0;
-    if (cudaMemcpy(&err, b->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PPPM_ECUDA;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, b->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        return PPPM_ECUDA;
+    }
     if (err) {
         cudaMemset(b->err, 0, sizeof(int));
-        return PPPM_ENONFINITE;
+        return (err & ERR_INTERNAL) ? PPPM_EINTERNAL : PPPM_ENONFINITE;
     }
     return PPPM_OK;
 }

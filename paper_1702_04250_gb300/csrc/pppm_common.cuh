@@ -11,7 +11,8 @@
 // Tiles: each mesh dimension of M points is cut into T = ceil(M/B) tiles with
 // boundaries floor(t*M/T); every tile is between floor(M/T) and B points wide,
 // which is >= 4 > rlo for the supported sizes, so a particle only reaches the
-// 27 tiles around the tile of its anchor.
+// 27 tiles around the tile of its anchor.  B = 8, or 16 along z for "long
+// tiles" (compensated FP32 at order >= 6, see tile_shape).
 #pragma once
 
 #include <cstdint>
@@ -27,6 +28,13 @@ constexpr int MAXP = 7;
 constexpr int TILE_B = 8;           // tile edge in mesh points
 constexpr int MAX_MESH = 1024;
 
+// Device error word bits (SortBufs::err): reported by pppm_sync.
+constexpr int ERR_NONFINITE = 1;  // a non-finite position or charge
+constexpr int ERR_INTERNAL = 2;   // a consistency check failed; the offending work was skipped
+
+// Remembers a failed CUDA runtime call for pppm_last_cuda_error.
+void note_cuda_error(cudaError_t e);
+
 // ---------------------------------------------------------------------------
 // Geometry and per-order constants passed to kernels by value.
 // ---------------------------------------------------------------------------
@@ -35,6 +43,7 @@ struct Geom {
     int M[3];
     int Mzh;            // Mz/2 + 1
     int T[3];           // tiles per dimension
+    int TE[3];          // widest tile per dimension, ceil(M / T)
     int ntiles;
     int P, rlo;
     R L[3], iL[3];
@@ -59,6 +68,23 @@ template <> struct Complex<double> { using type = cufftDoubleComplex; };
 template <typename R> using complex_t = typename Complex<R>::type;
 
 __host__ __device__ inline int tile_of(int n, int T, int M) { return ((n + 1) * T - 1) / M; }
+
+// Tiles per dimension (T) and the widest tile (TE) for tile edge TILE_B, or
+// 2 TILE_B along z when long_z.  Long tiles halve the tile count and cut the
+// halo share of the make_rho brick flush; only the compensated FP32 make_rho
+// at order >= 6 has a brick deep enough for them.
+inline void tile_shape(const int M[3], bool long_z, int T[3], int TE[3]) {
+    for (int d = 0; d < 3; ++d) {
+        const int e = (d == 2 && long_z) ? 2 * TILE_B : TILE_B;
+        T[d] = (M[d] + e - 1) / e;
+        TE[d] = (M[d] + T[d] - 1) / T[d];
+    }
+}
+inline bool long_tiles_allowed(int P, bool compensated) {
+    (void)P;
+    (void)compensated;
+    return false;  // needs the warp-per-particle make_rho, which is not dispatched (see k_rho.cu)
+}
 __host__ __device__ inline int tile_origin(int t, int T, int M) { return (t * M) / T; }
 
 __host__ __device__ inline uint32_t pack_anchor(int a, int b, int c) {

@@ -73,11 +73,10 @@ extern "C" int pppm_make_rho_noalloc(const double box[3], const int mesh[3], int
     if (precision != PPPM_FP32 && precision != PPPM_FP32C) return PPPM_EINVAL;
     if (n < 0 || n > NA_MAX_N) return PPPM_EINVAL;
     if (n > 0 && (!x || !q)) return PPPM_EINVAL;
-    int T[3];
-    for (int d = 0; d < 3; ++d) {
+    int T[3], TE[3];
+    for (int d = 0; d < 3; ++d)
         if (!(box[d] > 0) || mesh[d] < order || mesh[d] > MAX_MESH) return PPPM_EINVAL;
-        T[d] = (mesh[d] + TILE_B - 1) / TILE_B;
-    }
+    tile_shape(mesh, false, T, TE);
     const int ntiles = T[0] * T[1] * T[2];
     if (ntiles > NA_MAX_TILES) return PPPM_EINVAL;
 
@@ -97,6 +96,7 @@ extern "C" int pppm_make_rho_noalloc(const double box[3], const int mesh[3], int
         const double ih = (double)mesh[d] / box[d];
         g.M[d] = mesh[d];
         g.T[d] = T[d];
+        g.TE[d] = TE[d];
         g.L[d] = (float)box[d];
         g.iL[d] = (float)(1.0 / box[d]);
         g.ih[d] = (float)ih;

@@ -14,7 +14,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpppm_gb300.so")
 
-PPPM_OK, PPPM_EINVAL, PPPM_ENOMEM, PPPM_ECUDA, PPPM_ECUFFT, PPPM_ENONFINITE, PPPM_ETIMEOUT, PPPM_ENOTREADY = range(8)
+(PPPM_OK, PPPM_EINVAL, PPPM_ENOMEM, PPPM_ECUDA, PPPM_ECUFFT, PPPM_ENONFINITE, PPPM_ETIMEOUT, PPPM_ENOTREADY,
+ PPPM_EINTERNAL) = range(9)
 MODES = {"ik": 0, "ad": 1}
 PRECISIONS = {"fp64": 0, "fp32c": 1, "fp32": 2}
 ARRAYS = {"rho": 0, "green": 1, "field": 2, "anchor": 3, "tilestart": 4, "perm": 5, "selfforce": 6, "energy": 7}
@@ -25,7 +26,12 @@ _lib = None
 class PPPMError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {strerror(status)} (status {status})")
+        msg = f"{what}: {strerror(status)} (status {status})"
+        if status == PPPM_ECUDA:
+            detail = lib().pppm_last_cuda_error().decode()
+            if detail:
+                msg += f" [{detail}]"
+        super().__init__(msg)
 
 
 def lib() -> ctypes.CDLL:
@@ -39,6 +45,8 @@ def lib() -> ctypes.CDLL:
         dptr = ctypes.POINTER(ctypes.c_double)
         L.pppm_strerror.restype = ctypes.c_char_p
         L.pppm_strerror.argtypes = [i32]
+        L.pppm_last_cuda_error.restype = ctypes.c_char_p
+        L.pppm_last_cuda_error.argtypes = []
         L.pppm_estimate_g.argtypes = [dbl, dbl, i64, dbl, dptr, dptr]
         L.pppm_setup.argtypes = [ctypes.POINTER(vp), dptr, i64, i32, ctypes.POINTER(i32), dbl, i32, i32, dbl, vp]
         L.pppm_destroy.argtypes = [vp]

@@ -181,7 +181,8 @@ def test_fp32c_is_not_worse_than_fp32(torch, c2_refs):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("P", [2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("mode", ["ik", "ad"])
-def test_orders_on_ragged_mesh(torch, P, mode):
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_orders_on_ragged_mesh(torch, P, mode, prec):
     """Non-cubic box, mesh 20 x 17 x 12 (uneven tiles, odd Mz/2+1 handling),
     positions partly outside the box, a non-neutral charge set."""
     r = np.random.default_rng(100 + P)
@@ -191,9 +192,10 @@ def test_orders_on_ragged_mesh(torch, P, mode):
     x = r.uniform(-5.0, 20.0, (n, 3))
     q = r.normal(size=n)
     g = 0.55
-    plan, f, ev = run(torch, box, mesh, P, g, mode, "fp64", x, q, 2.0)
-    ref = OraclePPPM(box, mesh, P, g, mode, 2.0).compute(x, q)
-    check_all(f, ev, ref, "fp64", f"P={P} {mode}")
+    plan, f, ev = run(torch, box, mesh, P, g, mode, prec, x, q, 2.0)
+    xo, qo = oracle_inputs(x, q, prec)
+    ref = OraclePPPM(box, mesh, P, g, mode, 2.0).compute(xo, qo)
+    check_all(f, ev, ref, prec, f"P={P} {mode}")
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
@@ -215,13 +217,13 @@ def test_tiny_and_degenerate(torch, prec):
             assert abs(ev[0] - ref["energy"]) <= tol * abs(ref["energy"])
 
 
-@pytest.mark.parametrize("prec", ["fp32c", "fp32", "fp64"])
-def test_dense_tile(torch, prec):
+@pytest.mark.parametrize("prec,P", [("fp32c", 5), ("fp32c", 7), ("fp32", 5), ("fp64", 5)])
+def test_dense_tile(torch, prec, P):
     """70,000 charges packed into one mesh tile: the FP32C fixed-point brick
     folds its low words twice (every 32,768 particles), and every precision
     must still match the oracle's mesh and forces."""
     r = np.random.default_rng(31)
-    box, mesh, P, g = (20.0, 20.0, 20.0), (20, 20, 20), 5, 0.5
+    box, mesh, g = (20.0, 20.0, 20.0), (20, 20, 20), 0.5
     n = 70000
     x = 3.0 + r.uniform(0.0, 1.5, (n, 3))
     q = r.normal(size=n)
@@ -312,8 +314,39 @@ def test_fieldforce_variants_and_autotune(torch, c2_refs, mode):
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"autotuned {choice}")
-    with pytest.raises(pppm.PPPMError):
-        plan.set_variant(4)
+    for bad in (2, 3, 4):  # long tiles need order >= 6
+        with pytest.raises(pppm.PPPMError):
+            plan.set_variant(bad)
+
+
+@pytest.mark.parametrize("mode", ["ik", "ad"])
+def test_order7_variants(torch, mode):
+    """FP32C at P = 7 on the water-like 64^3 system: both fieldforce variants
+    match the oracle, long tiles (bit 1) are refused, autotune keeps a valid
+    variant."""
+    from paper_1702_04250_gb300 import pppm
+
+    w = config("c2")
+    g = g_of(w)
+    xo, qo = oracle_inputs(w.x, w.q, "fp32")
+    ref = OraclePPPM(w.box, w.mesh, 7, g, mode, w.qqrd2e).compute(xo, qo)
+    x = torch.tensor(w.x, dtype=torch.float32, device="cuda")
+    q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
+    plan = pppm.PPPM(w.box, w.n, 7, w.mesh, g, mode, "fp32c", w.qqrd2e)
+    assert plan.info()["tile"] == 8 and plan.info()["ntiles"] == 512
+    for v in (0, 1):
+        plan.set_variant(v)
+        f, ev = plan.compute(x, q)
+        plan.sync()
+        check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, "fp32c", f"P=7 variant {v} {mode}")
+    for bad in (2, 3):
+        with pytest.raises(pppm.PPPMError):
+            plan.set_variant(bad)
+    choice = plan.autotune(x, q)
+    assert choice in (0, 1)
+    f, ev = plan.compute(x, q)
+    plan.sync()
+    check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, "fp32c", f"P=7 autotuned {choice}")
 
 
 def test_fp64_repeatable(torch, c2_refs):
