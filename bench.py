@@ -13,6 +13,11 @@ Also reported on the same line: Mparticles/s, the force error of this FP32C
 form against the FP64 form (same GPU, same inputs), the dominant kernel's
 roofline fraction, the end-to-end rate through the host-buffer C-ABI call,
 the FP64 oracle timed on the host cores, and the same metric for ad / FP64.
+Two more workloads are measured on rank 0 (key "extra", skipped with
+--no-extra): the 2,048,001-charge water-like system (256^3, P=7, ad, FP32C;
+the HBM-sized case: per-stage times and the make_rho / fieldforce roofline
+fractions) and the batch of 256 independent systems (one call, one graph;
+against the FP64 batch and against 256 single-system plans).
 
 --impl reference times the FP64 CPU oracle on the same workload instead.
 Multi-GPU: the path does not shard (one system); N ranks run N independent
@@ -140,14 +145,51 @@ def known_traffic(stage, workload_name):
     return None
 
 
+def aggregate_ms(t_ms, world):
+    """Max over ranks of a per-rank time (ms); a no-op for one rank."""
+    import torch
+
+    if world <= 1 or not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(t_ms)
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def throughput(units_per_rank, t_ms, steps, world):
+    """Whole-job units/s: every rank processed units_per_rank per step; the
+    slowest rank's time bounds the job."""
+    return world * units_per_rank * steps / (t_ms * 1e-3)
+
+
+# shared-memory int32 atomic adds per SM per clock on GB300, conflict-free
+# warps (microbenchmark of ATOMS.ADD without return)
+SHARED_ATOMIC_OPS_PER_CLK_SM = 25.9
+N_SM = 152
+
+
+def onchip_make_rho(n, P, ms, sm_mhz):
+    """make_rho against its on-chip bound: FP32C adds two int32 words per
+    stencil point in shared memory (2 N P^3 atomics per launch)."""
+    ops = 2.0 * n * P ** 3
+    mhz = sm_mhz or 2070.0
+    peak = SHARED_ATOMIC_OPS_PER_CLK_SM * N_SM * mhz * 1e6 / 1e9
+    ach = ops / (ms * 1e-3) / 1e9
+    return {"resource": "shared-memory int32 atomics", "ops_per_launch": int(ops),
+            "achieved_gops": round(ach, 1), "peak_gops": round(peak, 1), "frac": round(ach / peak, 4),
+            "peak_source": f"microbenchmark, {SHARED_ATOMIC_OPS_PER_CLK_SM} ops/clk/SM x {N_SM} SMs at {mhz:.0f} MHz"}
+
+
 def make_plan(w, g, mode, prec, graph=True):
     from paper_1702_04250_gb300 import pppm
 
     return pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode=mode, precision=prec, qqrd2e=w.qqrd2e, graph=graph)
 
 
-def time_steps(torch, plan, x, q, f, ev, steps, warmup, flush, profile=False):
-    """Returns (total device ms over the timed steps, per-stage ms sums)."""
+def time_steps(torch, plan, x, q, f, ev, steps, warmup, flush, profile=False, sync_ranks=True):
+    """Returns (total device ms over the timed steps, per-stage ms sums).
+    sync_ranks: barrier with the other ranks around the timed region."""
     s = plan.stream
     stage_sum = {k: 0.0 for k in plan.STAGES}
     plan.set_profiling(profile)
@@ -155,7 +197,7 @@ def time_steps(torch, plan, x, q, f, ev, steps, warmup, flush, profile=False):
         flush.zero_()
         plan.compute(x, q, f, ev)
     torch.cuda.synchronize()
-    if torch.distributed.is_available() and torch.distributed.is_initialized():
+    if sync_ranks and torch.distributed.is_available() and torch.distributed.is_initialized():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     total = 0.0
@@ -174,7 +216,7 @@ def time_steps(torch, plan, x, q, f, ev, steps, warmup, flush, profile=False):
                 if v >= 0:
                     stage_sum[k] += v
     torch.cuda.synchronize()
-    if torch.distributed.is_available() and torch.distributed.is_initialized():
+    if sync_ranks and torch.distributed.is_available() and torch.distributed.is_initialized():
         torch.distributed.barrier()
     plan.set_profiling(False)
     return total, stage_sum
@@ -200,6 +242,7 @@ def gpu_arm(args, rank, world):
     plan = make_plan(w, g, "ik", "fp32c")
     f = torch.empty((w.n, 3), dtype=torch.float32, device="cuda")
     ev = torch.zeros(8, dtype=torch.float64, device="cuda")
+    variant = plan.autotune(x32, q32)  # what a user of the plan does once
     plan.compute(x32, q32, f, ev)
     plan.sync()
 
@@ -227,11 +270,9 @@ def gpu_arm(args, rank, world):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = tt.item()
+    t_ms = aggregate_ms(t_ms, world)
     ms_per_step = t_ms / args.steps
-    steps_per_s = world * 1000.0 / ms_per_step
+    steps_per_s = throughput(1, t_ms, args.steps, world)
 
     # the same steps without any stage event (graph of kernels only)
     t_plain, _ = time_steps(torch, plan, x32, q32, f, ev, max(20, args.steps // 2), 3, flush, profile=False)
@@ -276,17 +317,20 @@ def gpu_arm(args, rank, world):
         variants[f"{mode}_{prec}"] = {"steps_per_s": round(1000.0 / (tv / max(20, args.steps // 4)), 1)}
         pv.close()
 
-    launches_per_step = 5  # particle_map, scatter, make_rho, green, fieldforce (cuFFT and the memset are not ours)
+    # particle_map, scatter, make_rho, green, energy_final, fieldforce (cuFFT and the memset are not ours)
+    launches_per_step = 6
     line = {
         "metric": metric_name(), "value": round(steps_per_s, 2), "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32c", "data": "synthetic",
-        "config": config_dict(w, {"parallelism": "replicas" if world > 1 else "single"}),
+        "config": config_dict(w, {"parallelism": "replicas" if world > 1 else "single",
+                                  "fieldforce_variant": "tile-staged" if variant & 1 else "per-particle L1"}),
         "mparticles_per_s": round(world * N / (ms_per_step * 1e-3) / 1e6, 2),
         "rel_force_err_vs_fp64": rel_err, "rel_energy_err_vs_fp64": e_err,
         "ms_per_step_without_kernel_events": round(ms_plain, 5),
         "steps_per_s_without_kernel_events": round(world * 1000.0 / ms_plain, 2),
         "roofline": roof,
+        "onchip": onchip_make_rho(N, w.order, stage_ms["make_rho"], clocks_rep.get("sm_mhz")),
         "e2e": {"value": round(world / e2e_s, 2), "unit": "steps/s", "h2d_bytes_per_step": int(16 * N),
                 "d2h_bytes_per_step": int(12 * N + 56)},
         "gpu_launches": launches_per_step * args.steps,
@@ -294,6 +338,145 @@ def gpu_arm(args, rank, world):
         "variants": variants,
     }
     return line
+
+
+# ---------------------------------------------------------------------------
+# extra workloads (rank 0)
+# ---------------------------------------------------------------------------
+def large_leg(torch, flush, steps=30):
+    """2,048,001 water-like charges, 256^3, P=7, ad, FP32C, one graph per step."""
+    from paper_1702_04250_gb300 import pppm
+    from paper_1702_04250_gb300.workloads import config
+
+    w = config("c3")
+    g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
+    x = torch.tensor(w.x, dtype=torch.float32, device="cuda")
+    q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
+    plan = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode="ad", precision="fp32c", qqrd2e=w.qqrd2e, graph=True)
+    variant = plan.autotune(x, q)
+    f = torch.empty((w.n, 3), dtype=torch.float32, device="cuda")
+    ev = torch.zeros(8, dtype=torch.float64, device="cuda")
+    t_plain, _ = time_steps(torch, plan, x, q, f, ev, steps, 3, flush, profile=False, sync_ranks=False)
+    _, st = time_steps(torch, plan, x, q, f, ev, steps, 3, flush, profile=True, sync_ranks=False)
+    stage = {k: v / steps for k, v in st.items()}
+    ms = t_plain / steps
+    # error of this form against the FP64 form on a 1 % subsample (every 100th charge)
+    p64 = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode="ad", precision="fp64", qqrd2e=w.qqrd2e)
+    f64, ev64 = p64.compute(x.double(), q.double())
+    p64.sync()
+    sub = slice(0, w.n, 100)
+    a = f[sub].double().cpu().numpy()
+    b = f64[sub].cpu().numpy()
+    err = math.sqrt(float(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+    e_err = abs(ev[0].item() - ev64[0].item()) / abs(ev64[0].item())
+    p64.close()
+    N, M = w.n, int(np.prod(w.mesh))
+    peak, kind = measured_peak()
+    alg = {"make_rho": 20 * N + 4 * M, "fieldforce": 4 * M + 36 * N}
+    roof = {}
+    for k, nbytes in alg.items():
+        achieved = nbytes / (stage[k] * 1e-3) / 1e9
+        roof[k] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                   "frac": round(achieved / peak, 4), "alg_bytes_per_launch": int(nbytes),
+                   "avg_launch_ms": round(stage[k], 4), "peak_source": kind}
+    plan.close()
+    return {"workload": "water-like 682,667 molecules (2,048,001 charges), 272 A cube, mesh 256^3, order 7, ad, FP32C",
+            "steps_per_s": round(1000.0 / ms, 2), "ms_per_step": round(ms, 4),
+            "mparticles_per_s": round(N / (ms * 1e-3) / 1e6, 1),
+            "rel_force_err_vs_fp64_1pct_subsample": err, "rel_energy_err_vs_fp64": e_err,
+            "fieldforce_variant": "tile-staged" if variant & 1 else "per-particle L1",
+            "stage_ms": {k: round(v, 4) for k, v in stage.items()},
+            "roofline": roof,
+            "onchip_make_rho": onchip_make_rho(N, w.order, stage["make_rho"], None),
+            "timing": f"{steps} graph steps, L2 flushed before each; stage times from a second pass with stage events"}
+
+
+def batch_leg(torch, flush, steps=20):
+    """256 independent systems in one call and one graph, FP32C ik, against
+    the FP64 batch and against one single-system plan per system."""
+    from paper_1702_04250_gb300 import pppm
+    from paper_1702_04250_gb300.workloads import batch_systems
+
+    ws = batch_systems()
+    systems = []
+    for w in ws:
+        g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
+        systems.append(dict(box=w.box, n=w.n, order=w.order, mesh=w.mesh, g_ewald=g, x=w.x, q=w.q))
+    C = ws[0].qqrd2e
+    xs = np.concatenate([s["x"] for s in systems])
+    qs = np.concatenate([s["q"] for s in systems])
+    ntot = len(qs)
+
+    def time_batch(prec):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        b = pppm.PPPMBatch(systems, mode="ik", precision=prec, qqrd2e=C, graph=True)
+        x = torch.tensor(xs, dtype=dt, device="cuda")
+        q = torch.tensor(qs, dtype=dt, device="cuda")
+        f = torch.empty((ntot, 3), dtype=dt, device="cuda")
+        for _ in range(3):
+            b.compute(x, q, f)
+        b.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(steps):
+            with torch.cuda.stream(b.stream):
+                flush.zero_()
+            e0.record(b.stream)
+            b.compute(x, q, f)
+            e1.record(b.stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        b.sync()
+        out = f.double().cpu().numpy()
+        info = b.info()
+        b.close()
+        return tot / steps, out, info
+
+    ms32, f32, info = time_batch("fp32c")
+    ms64, f64, _ = time_batch("fp64")
+    err = math.sqrt(float(np.sum((f32 - f64) ** 2) / np.sum(f64 ** 2)))
+
+    # the same 256 systems as 256 single-system plans, one graph each, back to back
+    plans, xt, qt, ft = [], [], [], []
+    stream = torch.cuda.Stream()
+    for sd in systems:
+        p = pppm.PPPM(sd["box"], sd["n"], sd["order"], sd["mesh"], sd["g_ewald"], "ik", "fp32c", C,
+                      stream=stream, graph=True)
+        plans.append(p)
+        xt.append(torch.tensor(sd["x"], dtype=torch.float32, device="cuda"))
+        qt.append(torch.tensor(sd["q"], dtype=torch.float32, device="cuda"))
+        ft.append(torch.empty((sd["n"], 3), dtype=torch.float32, device="cuda"))
+    for _ in range(2):
+        for p, x, q, f in zip(plans, xt, qt, ft):
+            p.compute(x, q, f)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(max(3, steps // 4)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0.record(stream)
+        for p, x, q, f in zip(plans, xt, qt, ft):
+            p.compute(x, q, f)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms_single = tot / max(3, steps // 4)
+    for p in plans:
+        p.close()
+    return {"workload": f"{len(systems)} independent neutral +-1 systems, N 500-20,000 (total {ntot:,}), "
+                        f"meshes 16^3-64^3 ({info['mesh_classes']} mesh classes), orders 3/5/7, ik",
+            "fp32c": {"calls_per_s": round(1000.0 / ms32, 2), "ms_per_call": round(ms32, 4),
+                      "systems_per_s": round(len(systems) * 1000.0 / ms32, 1),
+                      "mparticles_per_s": round(ntot / (ms32 * 1e-3) / 1e6, 1)},
+            "fp64": {"calls_per_s": round(1000.0 / ms64, 2), "ms_per_call": round(ms64, 4)},
+            "fp32c_over_fp64": round(ms64 / ms32, 3),
+            "rel_force_err_fp32c_vs_fp64": err,
+            "single_plans_fp32c": {"ms_for_all_systems": round(ms_single, 4),
+                                   "batch_speedup": round(ms_single / ms32, 2)},
+            "timing": f"{steps} graph calls, L2 flushed before each"}
 
 
 # ---------------------------------------------------------------------------
@@ -344,6 +527,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 2M-charge and batched workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -360,6 +544,11 @@ def main():
             print(json.dumps(line))
         return
     line = gpu_arm(args, rank, world)
+    if rank == 0 and not args.no_extra:
+        import torch
+
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        line["extra"] = {"large": large_leg(torch, flush), "batch": batch_leg(torch, flush)}
     if rank == 0:
         if not args.no_cpu_baseline:
             rate, n, dt = oracle_rate(workload())

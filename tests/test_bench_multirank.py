@@ -1,0 +1,63 @@
+"""The multi-rank bookkeeping of bench.py on CPU: two gloo ranks, the job
+time is the slowest rank's, throughput counts every rank's units, and the
+reference arm runs on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, times, out):
+    import torch.distributed as dist
+
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t = bench.aggregate_ms(times[rank], world)
+    out[rank] = (t, bench.throughput(1000, t, 10, world))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_time():
+    import torch.multiprocessing as mp
+
+    port = _free_port()
+    times = [12.5, 20.0]
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_rank, args=(2, port, times, out), nprocs=2, start_method="spawn", join=True)
+        res = dict(out)
+    for r in (0, 1):
+        t, thr = res[r]
+        assert t == 20.0
+        # 2 ranks x 1000 units x 10 steps in 20 ms
+        assert thr == pytest.approx(2 * 1000 * 10 / 0.020)
+
+
+def test_single_rank_is_identity():
+    import bench
+
+    assert bench.aggregate_ms(7.25, 1) == 7.25
+    assert bench.throughput(5, 10.0, 4, 1) == pytest.approx(5 * 4 / 0.010)
+
+
+def test_reference_arm_other_ranks_do_no_work():
+    import argparse
+
+    import bench
+
+    args = argparse.Namespace(steps=1, warmup=3)
+    assert bench.reference_arm(args, rank=1, world=2) is None
