@@ -111,7 +111,9 @@ int pppm_set_stream(pppm_plan *p, void *cuda_stream);
  *            neutralising-background terms) then virial xx yy zz xy xz yz
  * Asynchronous; inputs must stay valid until the stream reaches the end of
  * the call.  With graph mode on (pppm_set_graph) the whole step is launched
- * as one CUDA graph, re-captured whenever n or a pointer changes. */
+ * as one CUDA graph; the plan keeps up to four instantiated graphs keyed by
+ * n, the four pointers and the profiled stages (least recently used one
+ * replaced), so alternating profiled and plain steps captures nothing new. */
 int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, double *ev);
 
 /* pppm_compute on HOST buffers: copies x and q to the device, computes, copies

@@ -94,10 +94,6 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
                                               int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
-    const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
-    if (threadIdx.x == 0) b.tile_count[tile] = 0;  // histogram is clean for the next step
-    if (start == end) return;
-
     const int tz = tile % g.T[2];
     const int ty = (tile / g.T[2]) % g.T[1];
     const int tx = tile / (g.T[2] * g.T[1]);
@@ -108,6 +104,11 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     const int Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - oy + P - 1;
     const int Ez = tile_origin(tz + 1, g.T[2], g.M[2]) - oz + P - 1;
     const int vol = Ex * Ey * Ez;
+
+    pdl_wait();  // the sort's outputs (and its reads of the histogram) are complete
+    const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
+    if (threadIdx.x == 0) b.tile_count[tile] = 0;  // histogram is clean for the next step
+    if (start == end) return;
 
     R *accr = reinterpret_cast<R *>(smem_raw);
     int *acch = reinterpret_cast<int *>(smem_raw);
@@ -329,6 +330,7 @@ __device__ __forceinline__ void make_rho_w_body(const Geom<float> &g, const Sort
     unsigned int *acch = reinterpret_cast<unsigned int *>(smem_raw);
     unsigned int *accl = acch + BR::VOLW;
 
+    pdl_wait();  // the sort's outputs (and its reads of the histogram) are complete
     const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
     if (threadIdx.x == 0) b.tile_count[tile] = 0;  // histogram is clean for the next step
     if (start == end) return;
@@ -505,19 +507,28 @@ static size_t brick_bytes(int acc) {
     return (size_t)E * E * E * (acc == ACC_FIXED ? 8 : sizeof(R));
 }
 
+template <typename K, typename R>
+static void launch_one(K kernel, bool pdl, dim3 grid, size_t bytes, cudaStream_t s, const Geom<R> &g,
+                       const SortBufs &b, R *rho) {
+    if (pdl)
+        launch_pdl(kernel, grid, dim3(RHO_THREADS), bytes, s, g, b, rho);
+    else
+        kernel<<<grid, RHO_THREADS, bytes, s>>>(g, b, rho);
+}
+
 template <typename R, int P>
-static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, int acc, cudaStream_t s) {
+static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, int acc, cudaStream_t s, bool pdl) {
     const size_t bytes = brick_bytes<R, P>(acc);
     if constexpr (std::is_same<R, float>::value && P >= 5) {
         if (acc == ACC_FIXED && kMakeRhoW) {
-            k_make_rho_w<P><<<g.ntiles, RHO_THREADS, 8 * WBrick<P>::VOLW, s>>>(g, b, rho);
+            launch_one(k_make_rho_w<P>, pdl, dim3(g.ntiles), 8 * WBrick<P>::VOLW, s, g, b, rho);
             return;
         }
     }
     if (acc == ACC_FIXED)
-        k_make_rho<R, P, ACC_FIXED><<<g.ntiles, RHO_THREADS, bytes, s>>>(g, b, rho);
+        launch_one(k_make_rho<R, P, ACC_FIXED>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
     else
-        k_make_rho<R, P, ACC_NATIVE><<<g.ntiles, RHO_THREADS, bytes, s>>>(g, b, rho);
+        launch_one(k_make_rho<R, P, ACC_NATIVE>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
 }
 
 template <typename R, int P>
@@ -586,24 +597,30 @@ cudaError_t prepare_make_rho(int P, bool comp) {
 }
 
 template <typename R>
-void launch_make_rho(const Geom<R> &g, int64_t n, const SortBufs &b, R *rho, bool comp, cudaStream_t s) {
-    cudaMemsetAsync(rho, 0, sizeof(R) * (size_t)g.M[0] * g.M[1] * g.M[2], s);
+void launch_make_rho(const Geom<R> &g, int64_t n, const SortBufs &b, R *rho, bool comp, cudaStream_t s,
+                     bool mesh_zeroed, bool pdl) {
+    if (!mesh_zeroed) {
+        cudaMemsetAsync(rho, 0, sizeof(R) * (size_t)g.M[0] * g.M[1] * g.M[2], s);
+        pdl = false;  // the memset now sits between the sort and this launch
+    }
     if (n == 0) return;
     const int acc = comp ? ACC_FIXED : ACC_NATIVE;
     switch (g.P) {
-        case 2: launch_p<R, 2>(g, b, rho, acc, s); break;
-        case 3: launch_p<R, 3>(g, b, rho, acc, s); break;
-        case 4: launch_p<R, 4>(g, b, rho, acc, s); break;
-        case 5: launch_p<R, 5>(g, b, rho, acc, s); break;
-        case 6: launch_p<R, 6>(g, b, rho, acc, s); break;
-        case 7: launch_p<R, 7>(g, b, rho, acc, s); break;
+        case 2: launch_p<R, 2>(g, b, rho, acc, s, pdl); break;
+        case 3: launch_p<R, 3>(g, b, rho, acc, s, pdl); break;
+        case 4: launch_p<R, 4>(g, b, rho, acc, s, pdl); break;
+        case 5: launch_p<R, 5>(g, b, rho, acc, s, pdl); break;
+        case 6: launch_p<R, 6>(g, b, rho, acc, s, pdl); break;
+        case 7: launch_p<R, 7>(g, b, rho, acc, s, pdl); break;
         default: break;
     }
 }
 
 template cudaError_t prepare_make_rho<float>(int, bool);
 template cudaError_t prepare_make_rho<double>(int, bool);
-template void launch_make_rho<float>(const Geom<float> &, int64_t, const SortBufs &, float *, bool, cudaStream_t);
-template void launch_make_rho<double>(const Geom<double> &, int64_t, const SortBufs &, double *, bool, cudaStream_t);
+template void launch_make_rho<float>(const Geom<float> &, int64_t, const SortBufs &, float *, bool, cudaStream_t,
+                                     bool, bool);
+template void launch_make_rho<double>(const Geom<double> &, int64_t, const SortBufs &, double *, bool,
+                                      cudaStream_t, bool, bool);
 
 }  // namespace pppm

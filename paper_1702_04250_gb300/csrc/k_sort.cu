@@ -64,13 +64,24 @@ __device__ double block_sum(R v, double *sh) {
 }
 
 // lb / nlb: this CTA's index and the CTA count of its system's launch.
+// Grid-stride clear of the mesh (mtot values, 16-byte stores for the bulk).
+template <typename R>
+__device__ __forceinline__ void clear_mesh(R *__restrict__ rho, int64_t mtot, int lb, int nlb) {
+    constexpr int V = 16 / sizeof(R);
+    const int64_t nv = mtot / V;
+    const int64_t t0 = (int64_t)lb * blockDim.x + threadIdx.x, stride = (int64_t)nlb * blockDim.x;
+    for (int64_t k = t0; k < nv; k += stride) reinterpret_cast<uint4 *>(rho)[k] = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t k = nv * V + t0; k < mtot; k += stride) rho[k] = R(0);
+}
+
 template <typename R>
 __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const R *__restrict__ x,
                                                   const R *__restrict__ q, const SortBufs &b, int big, int lb,
-                                                  int nlb) {
+                                                  int nlb, R *__restrict__ rho_zero = nullptr, int64_t mtot = 0) {
     __shared__ double sh[32];
     __shared__ int sh_scan[MAP_THREADS / 32];
     __shared__ bool last;
+    if (rho_zero) clear_mesh<R>(rho_zero, mtot, lb, nlb);
     const int i = lb * blockDim.x + threadIdx.x;
     R qs = R(0), qq = R(0);
     if (i < n) {
@@ -91,6 +102,7 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
         b.blk[2 * lb] = s1;
         b.blk[2 * lb + 1] = s2;
     }
+    pdl_trigger();
     if (!big) return;  // small tile counts: k_scatter scans the histogram itself
 
     // the histogram atomics returned their ranks, so they are complete at L2
@@ -140,8 +152,9 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
 
 template <typename R>
 __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, const R *__restrict__ x,
-                                                              const R *__restrict__ q, SortBufs b, int big) {
-    particle_map_body<R>(g, n, x, q, b, big, blockIdx.x, gridDim.x);
+                                                              const R *__restrict__ q, SortBufs b, int big,
+                                                              R *__restrict__ rho_zero, int64_t mtot) {
+    particle_map_body<R>(g, n, x, q, b, big, blockIdx.x, gridDim.x, rho_zero, mtot);
 }
 
 // Block-wide exclusive scan of the tile histogram into shared memory
@@ -186,6 +199,16 @@ __device__ __forceinline__ void scatter_body(const Geom<R> &g, int n, const R *_
                                              const R *__restrict__ q, const SortBufs &b, int big, int lb) {
     __shared__ int sh_start[SMALL_TILES + 1];
     __shared__ int sh_warp[MAP_THREADS / 32];
+    // the record comes from the inputs alone: computed before the histogram is final
+    const int i = lb * blockDim.x + threadIdx.x;
+    R xi[3], qi = R(0);
+    int a[3];
+    R d[3] = {R(0), R(0), R(0)};
+    if (i < n) {
+        load_particle<R>(x, q, i, xi, qi);
+        anchors<R>(g, xi, a, d);
+    }
+    pdl_wait();
     const int *starts = b.tile_start;
     if (!big) {
         scan_tiles_smem(b.tile_count, g.ntiles, sh_start, sh_warp);
@@ -193,13 +216,8 @@ __device__ __forceinline__ void scatter_body(const Geom<R> &g, int n, const R *_
             for (int k = threadIdx.x; k <= g.ntiles; k += blockDim.x) b.tile_start[k] = sh_start[k];
         starts = sh_start;
     }
-    const int i = lb * blockDim.x + threadIdx.x;
+    pdl_trigger();
     if (i >= n) return;
-    R xi[3], qi;
-    load_particle<R>(x, q, i, xi, qi);
-    int a[3];
-    R d[3];
-    anchors<R>(g, xi, a, d);
     const uint32_t packed = b.anchor[i];  // same computation as k_particle_map
     int s[3];
     unpack_anchor(packed, s[0], s[1], s[2]);
@@ -254,16 +272,16 @@ template void launch_batch_sort<double>(const BatchSys<double> *, const BatchLis
 
 template <typename R>
 void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const SortBufs &b,
-                 cudaStream_t s) {
+                 cudaStream_t s, R *rho_zero, int64_t mtot) {
     const int nb = (int)((n + MAP_THREADS - 1) / MAP_THREADS);
     const int big = g.ntiles > SMALL_TILES;
-    k_particle_map<R><<<nb, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, big);
-    k_scatter<R><<<nb, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, big);
+    k_particle_map<R><<<nb, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, big, rho_zero, mtot);
+    launch_pdl(k_scatter<R>, dim3(nb), dim3(MAP_THREADS), 0, s, g, (int)n, x, q, b, big);
 }
 
 template void launch_sort<float>(const Geom<float> &, int64_t, const float *, const float *,
-                                 const SortBufs &, cudaStream_t);
+                                 const SortBufs &, cudaStream_t, float *, int64_t);
 template void launch_sort<double>(const Geom<double> &, int64_t, const double *, const double *,
-                                  const SortBufs &, cudaStream_t);
+                                  const SortBufs &, cudaStream_t, double *, int64_t);
 
 }  // namespace pppm

@@ -65,10 +65,18 @@ struct pppm_plan {
     int prof_mask = 0, prof_valid = 0;  // stages timed; stages timed by the last call
     cudaEvent_t prof[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool graph_on = false;
-    int gkey_prof = 0;
-    cudaGraphExec_t gexec = nullptr;
-    const void *gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    int64_t gkey_n = -1;
+    // instantiated step graphs, one per (n, pointers, profiled stages): a
+    // caller that profiles every k-th step alternates between two of them
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        const void *key[4] = {nullptr, nullptr, nullptr, nullptr};
+        int64_t n = -1;
+        int prof = 0;
+        uint64_t used = 0;
+    };
+    static constexpr int kGraphSlots = 4;
+    GraphSlot graphs[kGraphSlots];
+    uint64_t graph_clock = 0;
     int variants = 0;  // bit 0: tile-staged fieldforce, bit 1: long tiles along z
     std::vector<void *> allocs;
 };
@@ -146,7 +154,8 @@ void release(pppm_plan *p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
-    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (auto &g : p->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto &e : p->prof)
         if (e) cudaEventDestroy(e);
     if (p->fork) cudaEventDestroy(p->fork);
@@ -315,9 +324,9 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (prof || sync_check_on()) CK(cudaStreamIsCapturing(s, &cap));
     // boundary i opens stage i and closes stage i - 1
+    auto need_mark = [&](int i) { return ((pmask >> i) & 1) || (i > 0 && ((pmask >> (i - 1)) & 1)); };
     auto mark = [&](int i) {
-        const bool need = ((pmask >> i) & 1) || (i > 0 && ((pmask >> (i - 1)) & 1));
-        if (!need) return;
+        if (!need_mark(i)) return;
         if (cap == cudaStreamCaptureStatusActive)
             cudaEventRecordWithFlags(p->prof[i], s, cudaEventRecordExternal);
         else
@@ -335,10 +344,11 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
     };
     int rc;
     mark(0);
-    launch_sort<R>(g, n, (const R *)x, (const R *)q, p->sb, s);
+    launch_sort<R>(g, n, (const R *)x, (const R *)q, p->sb, s, (R *)p->rho, p->Mtot);  // also clears rho
     if ((rc = check("particle_map/scatter"))) return rc;
     mark(1);
-    launch_make_rho<R>(g, n, p->sb, (R *)p->rho, p->comp, s);
+    // programmatic launch straight after the scatter unless a stage event sits between them
+    launch_make_rho<R>(g, n, p->sb, (R *)p->rho, p->comp, s, true, !need_mark(1) && !chk);
     if ((rc = check("make_rho"))) return rc;
     mark(2);
     if ((rc = exec_r2c(p))) return rc;
@@ -392,10 +402,9 @@ int enqueue(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, void
 bool valid_ptr_arg(int64_t n, const void *ptr) { return n == 0 || ptr != nullptr; }
 
 void drop_graph(pppm_plan *p) {
-    if (p->gexec) {
-        cudaGraphExecDestroy(p->gexec);
-        p->gexec = nullptr;
-        p->gkey_n = -1;
+    for (auto &g : p->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = pppm_plan::GraphSlot{};
     }
 }
 
@@ -597,11 +606,7 @@ int pppm_destroy(pppm_plan *p) {
 int pppm_set_stream(pppm_plan *p, void *cuda_stream) {
     if (!p) return PPPM_EINVAL;
     p->stream = (cudaStream_t)cuda_stream;
-    if (p->gexec) {
-        cudaGraphExecDestroy(p->gexec);
-        p->gexec = nullptr;
-        p->gkey_n = -1;
-    }
+    drop_graph(p);
     if (p->have_r2c) CKF(cufftSetStream(p->r2c, p->stream));
     if (p->have_c2r) CKF(cufftSetStream(p->c2r, p->stream));
     if (p->have_c2r1) CKF(cufftSetStream(p->c2r1, p->stream));
@@ -611,11 +616,7 @@ int pppm_set_stream(pppm_plan *p, void *cuda_stream) {
 int pppm_set_graph(pppm_plan *p, int enable) {
     if (!p) return PPPM_EINVAL;
     p->graph_on = enable != 0;
-    if (!p->graph_on && p->gexec) {
-        cudaGraphExecDestroy(p->gexec);
-        p->gexec = nullptr;
-        p->gkey_n = -1;
-    }
+    if (!p->graph_on) drop_graph(p);
     return PPPM_OK;
 }
 
@@ -626,14 +627,18 @@ int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f,
     p->field_is_field = true;
     p->have_rho = true;
     if (!p->graph_on) return enqueue(p, n, x, q, f, nullptr, ev, 0);
-    const void *key[5] = {x, q, f, ev, nullptr};
-    bool same = p->gexec && p->gkey_n == n && p->gkey_prof == p->prof_mask;
-    for (int i = 0; i < 5 && same; ++i) same = key[i] == p->gkey[i];
-    if (!same) {
-        if (p->gexec) {
-            cudaGraphExecDestroy(p->gexec);
-            p->gexec = nullptr;
-        }
+    const void *key[4] = {x, q, f, ev};
+    pppm_plan::GraphSlot *hit = nullptr, *lru = &p->graphs[0];
+    for (auto &g : p->graphs) {
+        if (g.exec && g.n == n && g.prof == p->prof_mask && g.key[0] == key[0] && g.key[1] == key[1] &&
+            g.key[2] == key[2] && g.key[3] == key[3])
+            hit = &g;
+        if (!g.exec || (lru->exec && g.used < lru->used)) lru = &g;
+    }
+    if (!hit) {
+        hit = lru;
+        if (hit->exec) cudaGraphExecDestroy(hit->exec);
+        *hit = pppm_plan::GraphSlot{};
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
         int rc = enqueue(p, n, x, q, f, nullptr, ev, 0);
@@ -643,14 +648,16 @@ int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f,
             return rc;
         }
         CK(ee);
-        cudaError_t ie = cudaGraphInstantiate(&p->gexec, graph, 0);
+        cudaError_t ie = cudaGraphInstantiate(&hit->exec, graph, 0);
         cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) hit->exec = nullptr;
         CK(ie);
-        for (int i = 0; i < 5; ++i) p->gkey[i] = key[i];
-        p->gkey_n = n;
-        p->gkey_prof = p->prof_mask;
+        for (int i = 0; i < 4; ++i) hit->key[i] = key[i];
+        hit->n = n;
+        hit->prof = p->prof_mask;
     }
-    CK(cudaGraphLaunch(p->gexec, p->stream));
+    hit->used = ++p->graph_clock;
+    CK(cudaGraphLaunch(hit->exec, p->stream));
     p->prof_valid = p->prof_mask;
     return PPPM_OK;
 }

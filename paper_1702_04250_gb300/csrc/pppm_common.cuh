@@ -142,6 +142,31 @@ __device__ __forceinline__ R dweight(const R (&c)[MAXP][MAXP], int k, R d) {
     return w;
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while its stream predecessor (a kernel) is still running; it must call
+// pdl_wait() before it reads anything the predecessor writes or writes
+// anything the predecessor reads.  pdl_trigger() lets the successor start
+// early; it changes scheduling only (the successor's pdl_wait still waits for
+// the whole predecessor grid).  Both are no-ops for ordinary launches.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Warp reduction of a double (full warp).
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -188,15 +213,20 @@ struct SortBufs {
     int *err;              // [1] device error word
 };
 
+// rho_zero (nullable, mtot values) is cleared by the same launch, so that
+// make_rho can follow with mesh_zeroed = true.
 template <typename R>
 void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const SortBufs &b,
-                 cudaStream_t s);
+                 cudaStream_t s, R *rho_zero = nullptr, int64_t mtot = 0);
 
 template <typename R>
 cudaError_t prepare_make_rho(int P, bool compensated);  // once per process/device, before capture
+// mesh_zeroed: rho was cleared by launch_sort (no memset here); pdl: the
+// launch directly follows launch_sort's kernels in the stream and may use a
+// programmatic dependent launch.
 template <typename R>
 void launch_make_rho(const Geom<R> &g, int64_t n, const SortBufs &b, R *rho, bool compensated,
-                     cudaStream_t s);
+                     cudaStream_t s, bool mesh_zeroed = false, bool pdl = false);
 
 struct GreenBufs {
     const double *G64;     // [Mx*My*Mzh] unscaled G
