@@ -255,6 +255,7 @@ __device__ __forceinline__ void fieldforce_body(const Geom<R> &g, const SortBufs
     if (live && !inmesh && k == 0) atomicOr(b.err, ERR_INTERNAL);  // skipped, reported
     GroupWeights<R, P, MODE> w;
     w.build(g, k, gbase, r.x, r.y, r.z);
+    pdl_wait();  // weights come from the sort's records; the field from the inverse transform
     R e0 = 0, e1 = 0, e2 = 0;
     if (live && inmesh && k < P) {
         const int My = g.M[1], Mz = g.M[2];
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, Sort
     const int Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - oy + P - 1;
     const int Ez = tile_origin(tz + 1, g.T[2], g.M[2]) - oz + P - 1;
 
+    pdl_wait();  // the field of the inverse transform is complete
     // stage the brick: 16 lanes along z (Ez <= 14), 16 rows per pass, every
     // copy issued before any is awaited
     {
@@ -394,15 +396,24 @@ static void launch_ff(const Geom<R> &g, int64_t n, const SortBufs &b, const R *f
     // gb multiplies sum(q), read on the device from the sort buffers
     SelfCoef sc;
     for (int i = 0; i < 6; ++i) sc.c[i] = c[i];
+    const bool pdl = (g.launch_flags & LF_PDL_FF) != 0;
     if (g.ff_tiled) {
-        k_fieldforce_tiled<R, P, MODE><<<g.ntiles, FF_THREADS, ff_brick_bytes<R, P, MODE>(), s>>>(
-            g, b, field, f, dq, qC, sc, gs, gb);
+        if (pdl)
+            launch_pdl(k_fieldforce_tiled<R, P, MODE>, dim3(g.ntiles), dim3(FF_THREADS), ff_brick_bytes<R, P, MODE>(),
+                       s, g, b, field, f, dq, qC, sc, gs, gb);
+        else
+            k_fieldforce_tiled<R, P, MODE><<<g.ntiles, FF_THREADS, ff_brick_bytes<R, P, MODE>(), s>>>(
+                g, b, field, f, dq, qC, sc, gs, gb);
         return;
     }
     // one group of 8 lanes per particle, a full grid
     const int64_t threads = n * FGROUP;
     const int nb = (int)((threads + FF_THREADS - 1) / FF_THREADS);
-    k_fieldforce<R, P, MODE><<<nb, FF_THREADS, 0, s>>>(g, b, (int)n, field, f, dq, qC, sc, gs, gb);
+    if (pdl)
+        launch_pdl(k_fieldforce<R, P, MODE>, dim3(nb), dim3(FF_THREADS), 0, s, g, b, (int)n, field, f, dq, qC, sc,
+                   gs, gb);
+    else
+        k_fieldforce<R, P, MODE><<<nb, FF_THREADS, 0, s>>>(g, b, (int)n, field, f, dq, qC, sc, gs, gb);
 }
 
 template <typename R, int MODE>

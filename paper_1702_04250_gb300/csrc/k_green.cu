@@ -114,6 +114,7 @@ __device__ __forceinline__ void green_body(const Geom<R> &g, const complex_t<R> 
                                            complex_t<R> *__restrict__ spec, const GreenBufs &b,
                                            const EnergyConsts &ec, int lb, int nlb) {
     __shared__ double sh[7][GREEN_THREADS / 32];
+    pdl_wait();  // the forward transform is complete
     const int Mx = g.M[0], My = g.M[1], Mzh = g.Mzh;
     const int rows = Mx * My;
     const int total = rows * Mzh;
@@ -214,10 +215,14 @@ int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec, con
     nb = std::min(std::max(nb, 1), 152 * 8);
     const auto *rh = reinterpret_cast<const complex_t<R> *>(rho_hat);
     auto *sp = reinterpret_cast<complex_t<R> *>(spec);
-    if (ik)
-        k_green<R, true><<<nb, GREEN_THREADS, 0, s>>>(g, rh, sp, b, ec);
-    else
-        k_green<R, false><<<nb, GREEN_THREADS, 0, s>>>(g, rh, sp, b, ec);
+    const bool pdl = (g.launch_flags & LF_PDL_GREEN) != 0;
+    if (ik) {
+        if (pdl) launch_pdl(k_green<R, true>, dim3(nb), dim3(GREEN_THREADS), 0, s, g, rh, sp, b, ec);
+        else k_green<R, true><<<nb, GREEN_THREADS, 0, s>>>(g, rh, sp, b, ec);
+    } else {
+        if (pdl) launch_pdl(k_green<R, false>, dim3(nb), dim3(GREEN_THREADS), 0, s, g, rh, sp, b, ec);
+        else k_green<R, false><<<nb, GREEN_THREADS, 0, s>>>(g, rh, sp, b, ec);
+    }
     return nb;
 }
 

@@ -60,6 +60,7 @@ struct pppm_plan {
     bool field_is_field = false, have_rho = false;
     void *hx = nullptr, *hq = nullptr, *hf = nullptr;  // device staging for the host path
     double *hev = nullptr;
+    int *h_err = nullptr;              // pinned host copy of the device error word (host path)
     cudaStream_t side = nullptr;       // energy/virial reduction branch
     cudaEvent_t fork = nullptr, join = nullptr;
     int prof_mask = 0, prof_valid = 0;  // stages timed; stages timed by the last call
@@ -156,6 +157,7 @@ void release(pppm_plan *p) {
     else cudaDeviceSynchronize();
     for (auto &g : p->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (p->h_err) cudaFreeHost(p->h_err);
     for (auto &e : p->prof)
         if (e) cudaEventDestroy(e);
     if (p->fork) cudaEventDestroy(p->fork);
@@ -314,8 +316,9 @@ int exec_c2r(pppm_plan *p, bool all3) {
 
 // kind 0: forces, 1: energy gradient
 template <typename R>
-int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const void *q, void *f, void *dq,
+int enqueue_t(pppm_plan *p, const Geom<R> &gp, int64_t n, const void *x, const void *q, void *f, void *dq,
               double *ev, int kind) {
+    Geom<R> g = gp;  // this step's copy: launch flags below
     cudaStream_t s = p->stream;
     const int pmask = (kind == 0) ? p->prof_mask : 0;
     const bool prof = pmask != 0;
@@ -342,6 +345,11 @@ int enqueue_t(pppm_plan *p, const Geom<R> &g, int64_t n, const void *x, const vo
         last_cuda_stage = stage;
         return cuda_status(e);
     };
+    // green follows the forward transform's last kernel and fieldforce the
+    // inverse transform's, unless a stage event node sits in between
+    g.launch_flags = 0;
+    if (!chk && !need_mark(3)) g.launch_flags |= LF_PDL_GREEN;
+    if (!chk && !need_mark(5)) g.launch_flags |= LF_PDL_FF;
     int rc;
     mark(0);
     launch_sort<R>(g, n, (const R *)x, (const R *)q, p->sb, s, (R *)p->rho, p->Mtot);  // also clears rho
@@ -550,6 +558,12 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         if ((rc = dmalloc(p, &p->hq, rs * nm))) break;
         if ((rc = dmalloc(p, &p->hf, 3 * rs * nm))) break;
         if ((rc = dmalloc(p, &p->hev, 8 * sizeof(double)))) break;
+        if (cudaHostAlloc((void **)&p->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            p->h_err = nullptr;
+            rc = PPPM_ENOMEM;
+            break;
+        }
     } while (0);
     if (rc) {
         release(p);
@@ -687,7 +701,16 @@ int pppm_compute_host(pppm_plan *p, int64_t n, const void *x_host, const void *q
     if (rc) return rc;
     if (n > 0) CK(cudaMemcpyAsync(f_host, p->hf, 3 * rs * n, cudaMemcpyDeviceToHost, p->stream));
     if (ev_host) CK(cudaMemcpyAsync(ev_host, p->hev, 7 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
-    return pppm_sync(p);
+    // the error word travels with the results: one stream synchronisation per call
+    CK(cudaMemcpyAsync(p->h_err, p->sb.err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    const int err = *p->h_err;
+    if (err) {
+        CK(cudaMemsetAsync(p->sb.err, 0, sizeof(int), p->stream));
+        CK(cudaStreamSynchronize(p->stream));
+        return (err & ERR_INTERNAL) ? PPPM_EINTERNAL : PPPM_ENONFINITE;
+    }
+    return PPPM_OK;
 }
 
 int pppm_energy_grad(pppm_plan *p, int64_t n, const void *x, const void *q, void *dEdx, void *dEdq, double *ev) {

@@ -54,8 +54,13 @@ struct Geom {
     R coef[MAXP][MAXP];   // coef[k][l]: weight of stencil point k, power l of delta
     R dcoef[MAXP][MAXP];  // d/ddelta of the same polynomials
     int ff_tiled;         // fieldforce variant: 0 per-particle through L1, 1 tile-staged brick
+    int launch_flags;     // host side: LF_* launch options of this step
     int planar_stride;    // ik field layout: 0 interleaved (Ex,Ey,Ez,pad); > 0 three planes this far apart
 };
+
+// Geom::launch_flags: green / fieldforce may use a programmatic dependent
+// launch (their stream predecessor is a kernel, no event node in between).
+constexpr int LF_PDL_GREEN = 1, LF_PDL_FF = 2;
 
 template <typename R> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
