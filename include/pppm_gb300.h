@@ -140,6 +140,14 @@ int pppm_set_graph(pppm_plan *p, int enable);
 int pppm_energy_grad(pppm_plan *p, int64_t n, const void *x, const void *q,
                      void *dEdx, void *dEdq, double *ev);
 
+/* Electrostatic k-space potential felt by each atom, phi_i = dE/dq_i (the
+ * dEdq of pppm_energy_grad: the mesh potential interpolated with the
+ * assignment stencil of Sec. 3.1, times C, plus the self and neutralising-
+ * background terms), i.e. the vector the backward pass of an energy with
+ * respect to the charges needs.  phi: device, n values of the step type,
+ * caller-owned, overwritten.  Asynchronous. */
+int pppm_potential(pppm_plan *p, int64_t n, const void *x, const void *q, void *phi);
+
 /* Internal arrays, for checking each stage against an independent
  * implementation.  Synchronous device-to-device (or device-to-host when
  * to_host != 0) copy of `bytes` bytes into dst; PPPM_EINVAL if bytes does not

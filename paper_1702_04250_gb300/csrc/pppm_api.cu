@@ -722,6 +722,15 @@ int pppm_energy_grad(pppm_plan *p, int64_t n, const void *x, const void *q, void
     return enqueue(p, n, x, q, dEdx, dEdq, ev, 1);
 }
 
+int pppm_potential(pppm_plan *p, int64_t n, const void *x, const void *q, void *phi) {
+    if (!p || n < 0 || n > p->n_max) return PPPM_EINVAL;
+    if (!valid_ptr_arg(n, x) || !valid_ptr_arg(n, q) || !valid_ptr_arg(n, phi)) return PPPM_EINVAL;
+    p->n_last = n;
+    p->field_is_field = false;
+    p->have_rho = true;
+    return enqueue(p, n, x, q, nullptr, phi, nullptr, 1);
+}
+
 int pppm_get_array(pppm_plan *p, int which, void *dst, size_t bytes, int to_host) {
     if (!p || !dst) return PPPM_EINVAL;
     const size_t rs = p->fp64 ? 8 : 4;

@@ -56,6 +56,7 @@ def lib() -> ctypes.CDLL:
         L.pppm_compute_host.argtypes = [vp, i64, vp, vp, vp, vp]
         L.pppm_sync.argtypes = [vp]
         L.pppm_energy_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.pppm_potential.argtypes = [vp, i64, vp, vp, vp]
         L.pppm_get_array.argtypes = [vp, i32, vp, ctypes.c_size_t, i32]
         L.pppm_plan_info.argtypes = [vp, ctypes.POINTER(i64)]
         L.pppm_set_profiling.argtypes = [vp, i32]
@@ -63,7 +64,8 @@ def lib() -> ctypes.CDLL:
         L.pppm_set_variant.argtypes = [vp, i32]
         L.pppm_autotune.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(i32)]
         for name in ("pppm_estimate_g", "pppm_setup", "pppm_destroy", "pppm_set_stream", "pppm_set_graph",
-                     "pppm_compute", "pppm_compute_host", "pppm_sync", "pppm_energy_grad", "pppm_get_array",
+                     "pppm_compute", "pppm_compute_host", "pppm_sync", "pppm_energy_grad", "pppm_potential",
+                     "pppm_get_array",
                      "pppm_plan_info", "pppm_set_profiling", "pppm_stage_times", "pppm_set_variant",
                      "pppm_autotune"):
             getattr(L, name).restype = i32
@@ -205,6 +207,13 @@ class PPPM:
         _check(lib().pppm_energy_grad(self._h, n, _ptr(x), _ptr(q), _ptr(dx), _ptr(dq), _ptr(self.ev)),
                "pppm_energy_grad")
         return dx, dq, self.ev[:7]
+
+    def potential(self, x, q):
+        """phi_i = dE/dq_i, the k-space potential felt by each atom [n]."""
+        x, q = self._prep(x, q)
+        phi = self.torch.empty((x.shape[0],), dtype=self.dtype, device=self.device)
+        _check(lib().pppm_potential(self._h, x.shape[0], _ptr(x), _ptr(q), _ptr(phi)), "pppm_potential")
+        return phi
 
     STAGES = ("sort", "make_rho", "fft_fwd", "green", "fft_inv", "fieldforce")
 

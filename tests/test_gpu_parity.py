@@ -380,3 +380,7 @@ def test_energy_gradients_match_oracle(torch, mode):
     assert rel_rms(dx.cpu().numpy(), rdx) < 1e-10
     assert rel_rms(dq.cpu().numpy(), rdq) < 1e-10
     assert abs(ev[0].item() - o.compute(x, q)["energy"]) < 1e-10 * abs(ev[0].item())
+    # the per-atom potential entry point is the same dE/dq
+    phi = plan.potential(torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda"))
+    plan.sync()
+    assert rel_rms(phi.cpu().numpy(), rdq) < 1e-10
