@@ -183,8 +183,11 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * does this).  Bit 0: fieldforce stages the tile's field brick in shared
  * memory (1) or reads the field through L1 per particle (0).  Bit 1
  * (mesh tiles 16 points long along z) is reserved: refused with PPPM_EINVAL
- * by every plan of this build.  Default: bit 0 for ik plans whose n_max is at
- * least 16 per tile, else 0.
+ * by every plan of this build.  Bit 2: PPPM_FP32C make_rho accumulates in
+ * four interleaved copies of the tile brick (no shared-memory bank
+ * conflicts, four times the brick's memory) instead of one (PPPM_EINVAL for
+ * other precisions).  Default: bit 0 for ik plans whose n_max is at least 16
+ * per tile, else 0.
  * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a
  * combination the plan does not allow).
  * pppm_autotune times every variant on the caller's inputs (one warm-up and
@@ -216,8 +219,9 @@ int pppm_plan_info(const pppm_plan *p, int64_t info[10]);
  * into the library, held on every device that loads it until exit, and shared
  * by all calls: it keeps the previous call's contents (the call clears what
  * must start at zero), and calls that overlap on the GPU race -- serialise
- * them.  The first call on a device looks the array's address up; make it
- * before any stream capture.  Allocates nothing.  Asynchronous. */
+ * them.  The first call on a device looks the array's address up and sets
+ * the kernels' shared-memory limits; make it before any stream capture.
+ * Allocates nothing.  Asynchronous. */
 int pppm_make_rho_noalloc(const double box[3], const int mesh[3], int order, int precision,
                           int64_t n, const float *x, const float *q, float *rho,
                           void *cuda_stream);

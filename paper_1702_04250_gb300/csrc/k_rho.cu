@@ -52,11 +52,11 @@ __device__ __forceinline__ double absval(double v) { return fabs(v); }
 // Power-of-two fixed-point scale for one tile's particles [start, end):
 // s = 2^e with every contribution |q W s / vcell| < 2^21 (W <= 1) and every
 // brick point's sum < 2^30.  Whole CTA; ends with the CTA synchronised.
-template <typename R>
+template <typename R, int NT = RHO_THREADS>
 __device__ __forceinline__ void fixed_scale(const R *__restrict__ recp, int start, int end, float ivcell,
                                             float &fs, float &ifs) {
-    __shared__ float sh_red[RHO_THREADS / 32];
-    __shared__ float sh_max[RHO_THREADS / 32];
+    __shared__ float sh_red[NT / 32];
+    __shared__ float sh_max[NT / 32];
     float part = 0.0f, pmax = 0.0f;
     for (int j = start + threadIdx.x; j < end; j += blockDim.x) {
         const float a = absval((float)reinterpret_cast<const vec4_t<R> *>(recp)[j].w);
@@ -75,7 +75,7 @@ __device__ __forceinline__ void fixed_scale(const R *__restrict__ recp, int star
     __syncthreads();
     float bound = 0.0f, bmax = 0.0f;
 #pragma unroll
-    for (int w = 0; w < RHO_THREADS / 32; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
         bound += sh_red[w];
         bmax = fmaxf(bmax, sh_max[w]);
     }
@@ -234,6 +234,200 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// FP32C, 8-lane particle groups, four-copy brick (variant bit 2 of a plan,
+// chosen by pppm_autotune; in the batch, the kernel for P <= 5).  Measured
+// on GB300: level with make_rho_body at P = 5 (32k and 100k charges, where
+// make_rho waits on latency, not on the atomic unit), slower at P = 7 on
+// 2M charges (824 vs 685 us: zeroing and flushing four 2744-point copies per
+// 8^3 tile of ~62 particles outweighs the bank conflicts it removes).
+//
+// Same work split and accumulators as make_rho_body<ACC_FIXED>, with four
+// interleaved copies of the brick: the particle group in lanes 8g..8g+7 adds
+// into copy g, word 4e + g of brick point e.  A group's z run e0..e0+7 then
+// covers banks 4(e0 + k) + g, distinct within the group and disjoint between
+// the four groups of a warp, so the atomics never replay on bank conflicts
+// (with one shared brick, the four particles of a warp collided on 60 % of
+// the atomic wavefronts).  The flush sums the copies exactly in integers.
+// Strides are compile-time (E = TILE_B + P - 1 points per dimension, tiles at
+// most TILE_B wide), every atomic is a red.shared.add.u32 at one register
+// plus a compile-time offset, and the contribution t = wa * wy is never
+// rounded on its own (both FMAs of the split see the exact product).
+// ---------------------------------------------------------------------------
+template <int P>
+struct GBrick {
+    static constexpr int NT = RHO_THREADS;
+    static constexpr int E = TILE_B + P - 1;
+    static constexpr int RS = E;          // z row stride (points)
+    static constexpr int PS = E * E;      // x plane stride
+    static constexpr int VOL = E * E * E;
+    static constexpr int COPIES = 4;
+    static constexpr int WORDS = COPIES * VOL;  // per accumulator array (hi or lo)
+    static constexpr size_t BYTES = 2 * WORDS * sizeof(int);
+};
+
+template <int OFF>
+__device__ __forceinline__ void red_shared_s32(unsigned int addr, int v) {
+    asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(addr), "r"(v), "n"(OFF));
+}
+
+// Stencil point I = a * P + c of this lane's z column: hi = rint(t) and
+// lo = rint(frac 2^16), each added as a signed integer.
+template <int I, int P>
+struct Scatter8 {
+    static __device__ __forceinline__ void run(const float (&wa)[P], const float (&wy)[P], unsigned int addr) {
+        using BR = GBrick<P>;
+        constexpr int a = I / P, c = I % P;
+        constexpr int off = 4 * BR::COPIES * (a * BR::PS + c * BR::RS);  // bytes
+        const float r1 = __fmaf_rn(wa[a], wy[c], MAGIC);
+        const float hi = __fadd_rn(r1, -MAGIC);
+        const float fr = __fmaf_rn(wa[a], wy[c], -hi);  // |fr| <= 1/2, rounded once
+        const float r2 = __fmaf_rn(fr, 65536.0f, MAGIC);
+        red_shared_s32<off>(addr, __float_as_int(r1) - MAGIC_BITS);
+        red_shared_s32<off + 4 * BR::WORDS>(addr, __float_as_int(r2) - MAGIC_BITS);
+        Scatter8<I + 1, P>::run(wa, wy, addr);
+    }
+};
+template <int P>
+struct Scatter8<P * P, P> {
+    static __device__ __forceinline__ void run(const float (&)[P], const float (&)[P], unsigned int) {}
+};
+
+template <int P>
+__device__ __forceinline__ void make_rho_fixed_body(const Geom<float> &g, const SortBufs &b,
+                                                    float *__restrict__ rho, int tile) {
+    using BR = GBrick<P>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int *acch = reinterpret_cast<int *>(smem_raw);
+    int *accl = acch + BR::WORDS;
+
+    const int tz = tile % g.T[2];
+    const int ty = (tile / g.T[2]) % g.T[1];
+    const int tx = tile / (g.T[2] * g.T[1]);
+    const int ox = tile_origin(tx, g.T[0], g.M[0]);
+    const int oy = tile_origin(ty, g.T[1], g.M[1]);
+    const int oz = tile_origin(tz, g.T[2], g.M[2]);
+    const int Ex = tile_origin(tx + 1, g.T[0], g.M[0]) - ox + P - 1;
+    const int Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - oy + P - 1;
+    const int Ez = tile_origin(tz + 1, g.T[2], g.M[2]) - oz + P - 1;
+
+    pdl_wait();  // the sort's outputs (and its reads of the histogram) are complete
+    const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
+    if (threadIdx.x == 0) b.tile_count[tile] = 0;  // histogram is clean for the next step
+    if (start == end) return;
+
+    const float4 *__restrict__ rec = reinterpret_cast<const float4 *>(b.rec);
+    float fs, ifs;
+    fixed_scale<float, BR::NT>(reinterpret_cast<const float *>(b.rec), start, end, g.ivcell, fs, ifs);
+    for (int e = threadIdx.x; e < 2 * BR::WORDS; e += BR::NT) acch[e] = 0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int k = lane & (GROUP - 1);            // z stencil offset of this lane
+    const int gbase = lane & ~(GROUP - 1);
+    const int copy = lane >> 3;                  // this group's brick copy
+    const int grp = threadIdx.x / GROUP;         // particle slot in the CTA
+    constexpr int NGRP = BR::NT / GROUP;
+    const float qscale = g.ivcell * fs;
+    float ck[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) ck[l] = (k < P) ? g.coef[k][l] : 0.0f;
+    const unsigned int sbase = (unsigned int)__cvta_generic_to_shared(acch) + 4u * (unsigned int)copy;
+    bool bad = false;  // a particle outside this tile (an inconsistent sort)
+
+    for (int chunk = start; chunk < end; chunk += LO_CHUNK) {
+        const int cend = min(end, chunk + LO_CHUNK);
+        // warp-uniform trip count: all 32 lanes take part in the shuffles
+        for (int base = chunk; base < cend; base += NGRP) {
+            const int j = base + grp;
+            const bool live = j < cend;
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            int ax = 0, ay = 0, az = 0;
+            if (live) {
+                r = rec[j];
+                unpack_anchor(b.cell[j], ax, ay, az);
+                ax -= ox; ay -= oy; az -= oz;        // local anchor in [0, tile size)
+            }
+            const bool out = (unsigned)ax > (unsigned)(Ex - P) || (unsigned)ay > (unsigned)(Ey - P) ||
+                             (unsigned)az > (unsigned)(Ez - P);
+            bad |= live && out;
+            const bool use = live && !out;
+            const float qv = use ? r.w * qscale : 0.0f;
+            // lane k < P evaluates the three weights of stencil offset k
+            const float wx = horner<float, P>(ck, r.x), wy = horner<float, P>(ck, r.y);
+            const float wz = horner<float, P>(ck, r.z);
+            float wa[P], wyk[P];
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                wa[t] = __shfl_sync(0xffffffffu, wx, gbase + t) * qv * wz;
+                wyk[t] = __shfl_sync(0xffffffffu, wy, gbase + t);
+            }
+            if (use && k < P) {
+                const unsigned int addr =
+                    sbase + 4u * BR::COPIES * (unsigned int)(ax * BR::PS + ay * BR::RS + az + k);
+                Scatter8<0, P>::run(wa, wyk, addr);
+            }
+        }
+        if (cend < end) {  // fold lo into hi (every copy) before it can overflow
+            __syncthreads();
+            for (int e = threadIdx.x; e < BR::WORDS; e += BR::NT) {
+                const int l = accl[e];       // signed sum of fractions in [-2^15, 2^15] each
+                acch[e] += l >> 16;          // floor division by 2^16
+                accl[e] = l & 0xffff;
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(b.err, ERR_INTERNAL);
+
+    // flush the brick (tile + halo) into the global mesh: 16 lanes per z row
+    // (Ez <= 14), 16 rows per pass; every wrap is a single conditional since
+    // the brick is never wider than the mesh plus one period
+    // rows (ex, ey) dealt out over NT / 16 row slots
+    const int lz = threadIdx.x & 15, rslot = threadIdx.x >> 4;
+    if (lz < Ez) {
+        int gz = oz - g.rlo + lz;
+        gz += (gz < 0) ? g.M[2] : 0;
+        gz -= (gz >= g.M[2]) ? g.M[2] : 0;
+        for (int row = rslot; row < Ex * Ey; row += BR::NT / 16) {
+            const int ex = row / Ey, ey = row - ex * Ey;
+            int gx = ox - g.rlo + ex;
+            gx += (gx < 0) ? g.M[0] : 0;
+            gx -= (gx >= g.M[0]) ? g.M[0] : 0;
+            {
+                int gy = oy - g.rlo + ey;
+                gy += (gy < 0) ? g.M[1] : 0;
+                gy -= (gy >= g.M[1]) ? g.M[1] : 0;
+                const int w = BR::COPIES * (ex * BR::PS + ey * BR::RS + lz);
+                // the four copies, normalised in integers (exact), then one FP32 rounding
+                int h = 0, fr = 0;
+#pragma unroll
+                for (int cp = 0; cp < BR::COPIES; ++cp) {
+                    const int l = accl[w + cp];
+                    h += acch[w + cp] + (l >> 16);
+                    fr += l & 0xffff;
+                }
+                h += fr >> 16;
+                const float v = fmaf((float)(fr & 0xffff), 1.0f / 65536.0f, (float)h) * ifs;
+                if (v != 0.0f) atomicAdd(&rho[(gx * g.M[1] + gy) * g.M[2] + gz], v);
+            }
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(GBrick<P>::NT) k_make_rho_fixed(Geom<float> g, SortBufs b, float *__restrict__ rho) {
+    make_rho_fixed_body<P>(g, b, rho, blockIdx.x);
+}
+
+template <int P>
+__global__ void __launch_bounds__(GBrick<P>::NT) k_batch_make_rho_fixed(const BatchSys<float> *__restrict__ sys,
+                                                                        BatchList bl) {
+    const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
+    const BatchSys<float> &S = sys[bl.ids[e]];
+    make_rho_fixed_body<P>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);
 }
 
 // ---------------------------------------------------------------------------
@@ -509,11 +703,11 @@ static size_t brick_bytes(int acc) {
 
 template <typename K, typename R>
 static void launch_one(K kernel, bool pdl, dim3 grid, size_t bytes, cudaStream_t s, const Geom<R> &g,
-                       const SortBufs &b, R *rho) {
+                       const SortBufs &b, R *rho, int threads = RHO_THREADS) {
     if (pdl)
-        launch_pdl(kernel, grid, dim3(RHO_THREADS), bytes, s, g, b, rho);
+        launch_pdl(kernel, grid, dim3(threads), bytes, s, g, b, rho);
     else
-        kernel<<<grid, RHO_THREADS, bytes, s>>>(g, b, rho);
+        kernel<<<grid, threads, bytes, s>>>(g, b, rho);
 }
 
 template <typename R, int P>
@@ -522,6 +716,12 @@ static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, int acc, cudaS
     if constexpr (std::is_same<R, float>::value && P >= 5) {
         if (acc == ACC_FIXED && kMakeRhoW) {
             launch_one(k_make_rho_w<P>, pdl, dim3(g.ntiles), 8 * WBrick<P>::VOLW, s, g, b, rho);
+            return;
+        }
+    }
+    if constexpr (std::is_same<R, float>::value) {
+        if (acc == ACC_FIXED && g.rho_copies) {
+            launch_one(k_make_rho_fixed<P>, pdl, dim3(g.ntiles), GBrick<P>::BYTES, s, g, b, rho, GBrick<P>::NT);
             return;
         }
     }
@@ -535,6 +735,16 @@ template <typename R, int P>
 static cudaError_t prepare_p(int acc) {
     const int bytes = (int)brick_bytes<R, P>(acc);
     cudaError_t e;
+    if constexpr (std::is_same<R, float>::value) {
+        if (acc == ACC_FIXED) {
+            e = cudaFuncSetAttribute(k_make_rho_fixed<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)GBrick<P>::BYTES);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_batch_make_rho_fixed<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)GBrick<P>::BYTES);
+            return e;
+        }
+    }
     if (acc == ACC_FIXED) {
         e = cudaFuncSetAttribute(k_make_rho<R, P, ACC_FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e == cudaSuccess)
@@ -555,6 +765,12 @@ static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc,
     if constexpr (std::is_same<R, float>::value && P >= 5) {
         if (acc == ACC_FIXED && kMakeRhoW) {
             k_batch_make_rho_w<P><<<bl.nblocks, RHO_THREADS, 8 * WBrick<P>::VOLW, s>>>(sys, bl);
+            return;
+        }
+    }
+    if constexpr (std::is_same<R, float>::value) {
+        if (acc == ACC_FIXED && P <= 5) {  // the four-copy brick where it measured faster
+            k_batch_make_rho_fixed<P><<<bl.nblocks, GBrick<P>::NT, GBrick<P>::BYTES, s>>>(sys, bl);
             return;
         }
     }

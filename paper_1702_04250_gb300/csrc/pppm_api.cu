@@ -417,7 +417,8 @@ void drop_graph(pppm_plan *p) {
 }
 
 bool variant_ok(const pppm_plan *p, int v) {
-    if (v & ~3) return false;
+    if (v & ~7) return false;
+    if ((v & 4) && !p->comp) return false;  // the four-copy brick is the FP32C accumulator
     if ((v & 2) && !long_tiles_allowed(p->P, p->comp)) return false;
     return !((v & 1) && (v & 2));  // the tile-staged fieldforce brick holds 8^3 tiles only
 }
@@ -434,6 +435,7 @@ void set_variants(pppm_plan *p, int v) {
     }
     p->gf.ntiles = p->gd.ntiles = p->ntiles;
     p->gf.ff_tiled = p->gd.ff_tiled = (v & 1) ? 1 : 0;
+    p->gf.rho_copies = p->gd.rho_copies = (v & 4) ? 1 : 0;
     if (p->sb.tile_count) cudaMemsetAsync(p->sb.tile_count, 0, 4 * (size_t)p->ntiles_alloc, p->stream);
     drop_graph(p);
 }
@@ -603,6 +605,7 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     // default kernel variants (pppm_autotune refines them on real inputs):
     // the ik field (16 bytes a point) is worth staging per tile once tiles
     // hold enough particles; the ad potential (4 bytes) reads best through L1
+    // (the four-copy make_rho brick measured level at P = 5 and slower at P = 7)
     set_variants(p, (p->ik && (double)n_max >= 16.0 * p->ntiles) ? 1 : 0);
     if ((rc = build_tables_and_green(p))) return fail(rc);
     if ((rc = make_ffts(p))) return fail(rc);
@@ -834,7 +837,7 @@ int pppm_autotune(pppm_plan *p, int64_t n, const void *x, const void *q, void *f
     float best = 1e30f;
     int best_v = p->variants;
     int rc = PPPM_OK;
-    for (int v = 0; v <= 3 && rc == PPPM_OK; ++v) {
+    for (int v = 0; v <= 7 && rc == PPPM_OK; ++v) {
         if (!variant_ok(p, v)) continue;
         set_variants(p, v);
         float tot = 0.0f;

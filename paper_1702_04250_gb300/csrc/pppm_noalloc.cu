@@ -54,6 +54,10 @@ int scratch_address(int dev, unsigned char **out) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return PPPM_ECUDA;
+        // kernel attributes (shared-memory sizes) of every order, once per device
+        for (int P = 2; P <= MAXP; ++P)
+            if (prepare_make_rho<float>(P, true) != cudaSuccess || prepare_make_rho<float>(P, false) != cudaSuccess)
+                return PPPM_ECUDA;
         g_addr[dev] = reinterpret_cast<unsigned char *>(p);
     }
     *out = g_addr[dev];

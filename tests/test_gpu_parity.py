@@ -304,26 +304,29 @@ def test_fieldforce_variants_and_autotune(torch, c2_refs, mode):
     x = torch.tensor(w.x, dtype=torch.float32, device="cuda")
     q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
     plan = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode, "fp32c", w.qqrd2e)
-    for v in (0, 1):
+    for v in (0, 1, 4, 5):  # fieldforce per particle / tile-staged x make_rho one / four brick copies
         plan.set_variant(v)
         f, ev = plan.compute(x, q)
         plan.sync()
         check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"variant {v} {mode}")
     choice = plan.autotune(x, q)
-    assert choice in (0, 1)
+    assert choice in (0, 1, 4, 5)
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"autotuned {choice}")
-    for bad in (2, 3, 4):  # long tiles need order >= 6
+    for bad in (2, 3, 6, 7, 8):  # long tiles are reserved; unknown bits
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(bad)
+    p64 = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode, "fp64", w.qqrd2e)
+    with pytest.raises(pppm.PPPMError):
+        p64.set_variant(4)  # the brick copies are the FP32C accumulator
 
 
 @pytest.mark.parametrize("mode", ["ik", "ad"])
 def test_order7_variants(torch, mode):
     """FP32C at P = 7 on the water-like 64^3 system: both fieldforce variants
-    match the oracle, long tiles (bit 1) are refused, autotune keeps a valid
-    variant."""
+    and both make_rho bricks match the oracle, long tiles (bit 1) are
+    refused, autotune keeps a valid variant."""
     from paper_1702_04250_gb300 import pppm
 
     w = config("c2")
@@ -334,7 +337,7 @@ def test_order7_variants(torch, mode):
     q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
     plan = pppm.PPPM(w.box, w.n, 7, w.mesh, g, mode, "fp32c", w.qqrd2e)
     assert plan.info()["tile"] == 8 and plan.info()["ntiles"] == 512
-    for v in (0, 1):
+    for v in (0, 1, 4, 5):
         plan.set_variant(v)
         f, ev = plan.compute(x, q)
         plan.sync()
@@ -343,7 +346,7 @@ def test_order7_variants(torch, mode):
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(bad)
     choice = plan.autotune(x, q)
-    assert choice in (0, 1)
+    assert choice in (0, 1, 4, 5)
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, "fp32c", f"P=7 autotuned {choice}")
