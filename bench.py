@@ -421,6 +421,7 @@ def batch_leg(torch, flush, steps=20):
         b = pppm.PPPMBatch(systems, mode="ik", precision=prec, qqrd2e=C, graph=True)
         x = torch.tensor(xs, dtype=dt, device="cuda")
         q = torch.tensor(qs, dtype=dt, device="cuda")
+        b.autotune(x, q)
         f = torch.empty((ntot, 3), dtype=dt, device="cuda")
         for _ in range(3):
             b.compute(x, q, f)

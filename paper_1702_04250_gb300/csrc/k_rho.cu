@@ -760,7 +760,7 @@ static cudaError_t prepare_p(int acc) {
 }
 
 template <typename R, int P>
-static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc, cudaStream_t s) {
+static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc, bool copies4, cudaStream_t s) {
     const size_t bytes = brick_bytes<R, P>(acc);
     if constexpr (std::is_same<R, float>::value && P >= 5) {
         if (acc == ACC_FIXED && kMakeRhoW) {
@@ -769,7 +769,7 @@ static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc,
         }
     }
     if constexpr (std::is_same<R, float>::value) {
-        if (acc == ACC_FIXED && P <= 5) {  // the four-copy brick where it measured faster
+        if (acc == ACC_FIXED && copies4) {
             k_batch_make_rho_fixed<P><<<bl.nblocks, GBrick<P>::NT, GBrick<P>::BYTES, s>>>(sys, bl);
             return;
         }
@@ -782,21 +782,23 @@ static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc,
 
 // The meshes of the systems in the list must have been cleared.
 template <typename R>
-void launch_batch_make_rho(const BatchSys<R> *sys, const BatchList &bl, int P, bool comp, cudaStream_t s) {
+void launch_batch_make_rho(const BatchSys<R> *sys, const BatchList &bl, int P, bool comp, bool copies4,
+                           cudaStream_t s) {
     if (bl.nblocks == 0) return;
     const int acc = comp ? ACC_FIXED : ACC_NATIVE;
     switch (P) {
-        case 2: launch_batch_p<R, 2>(sys, bl, acc, s); break;
-        case 3: launch_batch_p<R, 3>(sys, bl, acc, s); break;
-        case 4: launch_batch_p<R, 4>(sys, bl, acc, s); break;
-        case 5: launch_batch_p<R, 5>(sys, bl, acc, s); break;
-        case 6: launch_batch_p<R, 6>(sys, bl, acc, s); break;
-        case 7: launch_batch_p<R, 7>(sys, bl, acc, s); break;
+        case 2: launch_batch_p<R, 2>(sys, bl, acc, copies4, s); break;
+        case 3: launch_batch_p<R, 3>(sys, bl, acc, copies4, s); break;
+        case 4: launch_batch_p<R, 4>(sys, bl, acc, copies4, s); break;
+        case 5: launch_batch_p<R, 5>(sys, bl, acc, copies4, s); break;
+        case 6: launch_batch_p<R, 6>(sys, bl, acc, copies4, s); break;
+        case 7: launch_batch_p<R, 7>(sys, bl, acc, copies4, s); break;
         default: break;
     }
 }
-template void launch_batch_make_rho<float>(const BatchSys<float> *, const BatchList &, int, bool, cudaStream_t);
-template void launch_batch_make_rho<double>(const BatchSys<double> *, const BatchList &, int, bool, cudaStream_t);
+template void launch_batch_make_rho<float>(const BatchSys<float> *, const BatchList &, int, bool, bool, cudaStream_t);
+template void launch_batch_make_rho<double>(const BatchSys<double> *, const BatchList &, int, bool, bool,
+                                            cudaStream_t);
 
 template <typename R>
 cudaError_t prepare_make_rho(int P, bool comp) {

@@ -61,6 +61,7 @@ struct pppm_batch {
     bool graph_on = false;
     cudaGraphExec_t gexec = nullptr;
     const void *gkey[4] = {nullptr, nullptr, nullptr, nullptr};
+    int variants = 0;  // bit P: FP32C make_rho of order P in four brick copies
     std::vector<void *> allocs;
 };
 
@@ -323,7 +324,8 @@ int batch_enqueue(pppm_batch *b, const R *x, const R *q, R *f, double *ev) {
     for (auto &mc : b->classes)
         if (cudaMemsetAsync(mc.rho, 0, rs * mc.Mtot * mc.members.size(), s) != cudaSuccess) return PPPM_ECUDA;
     launch_batch_sort<R>(sys, b->map_list, x, q, s);
-    for (int P = 2; P <= MAXP; ++P) launch_batch_make_rho<R>(sys, b->rho_list[P], P, b->comp, s);
+    for (int P = 2; P <= MAXP; ++P)
+        launch_batch_make_rho<R>(sys, b->rho_list[P], P, b->comp, ((b->variants >> P) & 1) != 0, s);
     for (auto &mc : b->classes) {
         cufftResult r = b->fp64 ? cufftExecD2Z(mc.r2c, (cufftDoubleReal *)mc.rho, (cufftDoubleComplex *)mc.rho_hat)
                                 : cufftExecR2C(mc.r2c, (cufftReal *)mc.rho, (cufftComplex *)mc.rho_hat);
@@ -458,6 +460,68 @@ int pppm_batch_compute(pppm_batch *b, const void *x, const void *q, void *f, dou
         for (int i = 0; i < 4; ++i) b->gkey[i] = key[i];
     }
     return cudaGraphLaunch(b->gexec, b->stream) == cudaSuccess ? PPPM_OK : PPPM_ECUDA;
+}
+
+int pppm_batch_set_variant(pppm_batch *b, int variants) {
+    if (!b || (variants & ~0xFC)) return PPPM_EINVAL;
+    if (variants && !b->comp) return PPPM_EINVAL;  // the brick copies are the FP32C accumulator
+    b->variants = variants;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    return PPPM_OK;
+}
+
+int pppm_batch_autotune(pppm_batch *b, const void *x, const void *q, void *f, int *choice_out) {
+    if (!b) return PPPM_EINVAL;
+    if (b->ntot > 0 && (!x || !q || !f)) return PPPM_EINVAL;
+    int best = b->variants;
+    if (b->comp) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PPPM_ECUDA;
+        auto time_calls = [&](int v, float &ms_out) -> int {
+            b->variants = v;
+            float tot = 0.0f;
+            for (int it = 0; it < 6; ++it) {  // one warm-up, five timed (eager launches)
+                if (cudaEventRecord(e0, b->stream) != cudaSuccess) return PPPM_ECUDA;
+                const int rc = batch_enqueue_any(b, x, q, f, nullptr);
+                if (rc) return rc;
+                if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                    return PPPM_ECUDA;
+                float ms = 0.0f;
+                if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return PPPM_ECUDA;
+                if (it > 0) tot += ms;
+            }
+            ms_out = tot;
+            return PPPM_OK;
+        };
+        float t_best = 0.0f;
+        int rc = time_calls(best, t_best);
+        // each order's make_rho is its own launch: choose its brick on its own
+        for (int P = 2; P <= MAXP && rc == PPPM_OK; ++P) {
+            if (b->rho_list[P].nblocks == 0) continue;
+            const int v = best ^ (1 << P);
+            float t = 0.0f;
+            rc = time_calls(v, t);
+            if (rc == PPPM_OK && t < t_best) {
+                t_best = t;
+                best = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->variants = best;
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        if (rc) return rc;
+        // leave f holding the chosen setting's result
+        if ((rc = batch_enqueue_any(b, x, q, f, nullptr))) return rc;
+    }
+    if (choice_out) *choice_out = best;
+    return PPPM_OK;
 }
 
 int pppm_batch_sync(pppm_batch *b) {

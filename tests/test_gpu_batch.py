@@ -87,6 +87,34 @@ def test_small_batch_vs_oracle(torch, mode, prec):
         assert np.linalg.norm(ev[s, 1:] - ref["virial"]) <= tol * np.linalg.norm(ref["virial"]) + 1e-12, s
 
 
+def test_batch_variants_and_autotune(torch):
+    """Every order's make_rho brick (one or four copies) gives the same
+    result; autotune returns a valid mask; FP64 batches refuse the bits."""
+    from paper_1702_04250_gb300 import pppm
+
+    systems = small_batch()
+    x = torch.tensor(np.concatenate([s["x"] for s in systems]).reshape(-1, 3), dtype=torch.float32, device="cuda")
+    q = torch.tensor(np.concatenate([s["q"] for s in systems]), dtype=torch.float32, device="cuda")
+    b = pppm.PPPMBatch(systems, mode="ik", precision="fp32c")
+    outs = []
+    for v in (0, 0xFC):
+        b.set_variant(v)
+        f, ev = b.compute(x, q)
+        b.sync()
+        outs.append((f.double().cpu().numpy(), ev.cpu().numpy().copy()))
+    assert rel_rms(outs[1][0], outs[0][0]) < 1e-5
+    choice = b.autotune(x, q)
+    assert choice & ~0xFC == 0
+    f, ev = b.compute(x, q)
+    b.sync()
+    assert rel_rms(f.double().cpu().numpy(), outs[0][0]) < 1e-5
+    with pytest.raises(pppm.PPPMError):
+        b.set_variant(1)
+    b64 = pppm.PPPMBatch(systems, mode="ik", precision="fp64")
+    with pytest.raises(pppm.PPPMError):
+        b64.set_variant(1 << 5)
+
+
 def test_small_batch_graph_matches(torch):
     systems = small_batch()
     _, f0, ev0 = run_batch(torch, systems, "ik", "fp32c")
