@@ -13,11 +13,12 @@ Also reported on the same line: Mparticles/s, the force error of this FP32C
 form against the FP64 form (same GPU, same inputs), the dominant kernel's
 roofline fraction, the end-to-end rate through the host-buffer C-ABI call,
 the FP64 oracle timed on the host cores, and the same metric for ad / FP64.
-Two more workloads are measured on rank 0 (key "extra", skipped with
---no-extra): the 2,048,001-charge water-like system (256^3, P=7, ad, FP32C;
-the HBM-sized case: per-stage times and the make_rho / fieldforce roofline
-fractions) and the batch of 256 independent systems (one call, one graph;
-against the FP64 batch and against 256 single-system plans).
+More is measured on rank 0 (key "extra", skipped with --no-extra): the
+2,048,001-charge water-like system (256^3, P=7, ad, FP32C; the HBM-sized
+case: per-stage times and the make_rho / fieldforce roofline fractions), the
+batch of 256 independent systems (one call, one graph; against the FP64 batch
+and against 256 single-system plans), and the real-space erfc sum of the
+bench workload (r_C = 10 A), the other half of the Ewald split.
 
 --impl reference times the FP64 CPU oracle on the same workload instead.
 Multi-GPU: the path does not shard (one system); N ranks run N independent
@@ -400,6 +401,50 @@ def large_leg(torch, flush, steps=30):
             "timing": f"{steps} graph steps, L2 flushed before each; stage times from a second pass with stage events"}
 
 
+def real_leg(torch, flush, steps=30):
+    """Real-space part of the Ewald split on the water-like 32,001 charges,
+    r_C = 10 A, FP32, against the FP64 form."""
+    from paper_1702_04250_gb300 import pppm
+    from paper_1702_04250_gb300.workloads import config
+
+    w = config("c2")
+    g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        rs = pppm.RealSpace(w.box, w.n, w.r_cut, g, precision=prec, qqrd2e=w.qqrd2e)
+        x = torch.tensor(w.x, dtype=dt, device="cuda")
+        q = torch.tensor(w.q, dtype=dt, device="cuda")
+        f = torch.empty((w.n, 3), dtype=dt, device="cuda")
+        for _ in range(3):
+            rs.compute(x, q, f)
+        rs.sync()
+        s = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0.record(s)
+            rs.compute(x, q, f)
+            e1.record(s)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        rs.sync()
+        out[prec] = (tot / steps, f.double().cpu().numpy(), rs.info()["cells"])
+        rs.close()
+    ms, f32, cells = out["fp32"]
+    f64 = out["fp64"][1]
+    err = math.sqrt(float(np.sum((f32 - f64) ** 2) / np.sum(f64 ** 2)))
+    V = float(np.prod(w.box))
+    pairs = w.n * (w.n / V) * 4.0 / 3.0 * math.pi * w.r_cut ** 3  # ordered pairs within r_C
+    return {"workload": "water-like 32,001 charges, 68 A cube, r_C = 10 A, erfc real-space sum, FP32",
+            "cells": list(cells), "ms_per_call": round(ms, 4), "calls_per_s": round(1000.0 / ms, 1),
+            "pairs_within_cutoff_per_s": float(f"{pairs / (ms * 1e-3):.4g}"),
+            "fp64_ms_per_call": round(out["fp64"][0], 4), "rel_force_err_fp32_vs_fp64": err,
+            "timing": f"{steps} calls, L2 flushed before each"}
+
+
 def batch_leg(torch, flush, steps=20):
     """256 independent systems in one call and one graph, FP32C ik, against
     the FP64 batch and against one single-system plan per system."""
@@ -558,7 +603,8 @@ def main():
         import torch
 
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-        line["extra"] = {"large": large_leg(torch, flush), "batch": batch_leg(torch, flush)}
+        line["extra"] = {"large": large_leg(torch, flush), "batch": batch_leg(torch, flush),
+                         "real_space": real_leg(torch, flush)}
     if rank == 0:
         if not args.no_cpu_baseline:
             rate, n, dt = oracle_rate(workload())

@@ -260,6 +260,32 @@ int pppm_batch_autotune(pppm_batch *b, const void *x, const void *q, void *f, in
 int pppm_batch_info(const pppm_batch *b, int64_t info[4]);
 int pppm_batch_destroy(pppm_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Real-space part of the Ewald split (Sec. 2.1: the short-range erfc(g r)/r
+ * interaction, summed directly within the cut-off r_C).  With the k-space
+ * result of a plan of the same g_ewald and qqrd2e it gives the total Coulomb
+ * energy, forces and virial of the periodic system:
+ *   E    = (C/2) sum_i sum_{j != i, r_ij < r_C} q_i q_j erfc(g r_ij)/r_ij
+ *   F_i  = C q_i sum_j q_j [erfc(g r)/r + 2g/sqrt(pi) exp(-g^2 r^2)] r_ij/r^2
+ *   W_ab = (1/2) sum_i sum_j (F_ij)_a (r_ij)_b       (r_ij = r_i - r_j)
+ * over minimum images; r_cut must be below half of every box edge
+ * (PPPM_EINVAL otherwise).  Orthorhombic box at the origin, positions
+ * wrapped.  precision: PPPM_FP64 (double) or PPPM_FP32 / PPPM_FP32C (float;
+ * the same float path).  pppm_real_compute: x [n][3], q [n], f [n][3] device
+ * buffers of the step type (caller-owned); f is overwritten, or added to when
+ * accumulate != 0 (e.g. onto pppm_compute's k-space forces); ev (device, 7
+ * doubles, nullable) receives energy then virial xx yy zz xy xz yz.
+ * Asynchronous on the stream given at setup; pppm_real_sync reports the
+ * device error word like pppm_sync.  info: cells per dimension, n_max. */
+typedef struct pppm_real pppm_real;
+int pppm_real_setup(pppm_real **out, const double box[3], int64_t n_max, double r_cut, double g_ewald,
+                    int precision, double qqrd2e, void *cuda_stream);
+int pppm_real_compute(pppm_real *r, int64_t n, const void *x, const void *q, void *f, int accumulate,
+                      double *ev);
+int pppm_real_sync(pppm_real *r);
+int pppm_real_info(const pppm_real *r, int64_t info[4]);
+int pppm_real_destroy(pppm_real *r);
+
 /* Static description of a status code (never NULL). */
 const char *pppm_strerror(int status);
 

@@ -49,18 +49,24 @@ __device__ __forceinline__ int tile_index(const Geom<R> &g, const int (&a)[3]) {
            tile_of(a[2], g.T[2], g.M[2]);
 }
 
-// Block sum: warps reduce in the step type, the per-warp values in FP64.
+// Block sums of two values: warps reduce in the step type, the per-warp
+// values in FP64 (one barrier).  Valid in thread 0.
 template <typename R>
-__device__ double block_sum(R v, double *sh) {
-    v = warp_sum_t<R>(v);
+__device__ void block_sum2(R a, R b, double *sh, double &sa, double &sb) {
+    a = warp_sum_t<R>(a);
+    b = warp_sum_t<R>(b);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sh[2 * w] = (double)a;
+        sh[2 * w + 1] = (double)b;
+    }
     __syncthreads();
-    if (l == 0) sh[w] = (double)v;
-    __syncthreads();
-    double r = 0.0;
+    sa = sb = 0.0;
     if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
-    return r;  // valid in thread 0
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            sa += sh[2 * k];
+            sb += sh[2 * k + 1];
+        }
 }
 
 // lb / nlb: this CTA's index and the CTA count of its system's launch.
@@ -96,8 +102,8 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
         qq = qi * qi;
     }
     // per-block sums of q and q^2, reduced later off the critical path
-    const double s1 = block_sum<R>(qs, sh);
-    const double s2 = block_sum<R>(qq, sh);
+    double s1, s2;
+    block_sum2<R>(qs, qq, sh, s1, s2);
     if (threadIdx.x == 0) {
         b.blk[2 * lb] = s1;
         b.blk[2 * lb + 1] = s2;
@@ -118,10 +124,20 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
 
     // ---- last block: exclusive scan of the tile histogram ---------------
     const int nt = g.ntiles;
-    const int chunk = (nt + blockDim.x - 1) / blockDim.x;
+    // chunks of a multiple of 4 tiles: whole chunks load as int4 (the
+    // histogram comes from cudaMalloc, 16-byte aligned)
+    const int chunk = ((nt + blockDim.x - 1) / blockDim.x + 3) & ~3;
     const int lo = min(nt, (int)threadIdx.x * chunk), hi = min(nt, lo + chunk);
     int local = 0;
-    for (int k = lo; k < hi; ++k) local += __ldcg(&b.tile_count[k]);
+    if (hi - lo == chunk) {
+        const int4 *c4 = reinterpret_cast<const int4 *>(b.tile_count + lo);
+        for (int k = 0; k < chunk / 4; ++k) {
+            const int4 v = __ldcg(c4 + k);
+            local += v.x + v.y + v.z + v.w;
+        }
+    } else {
+        for (int k = lo; k < hi; ++k) local += __ldcg(&b.tile_count[k]);
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int incl = local;
 #pragma unroll

@@ -270,6 +270,71 @@ class PPPM:
         return out
 
 
+class RealSpace:
+    """Real-space (short-range erfc) part of the Ewald split within r_cut;
+    with a PPPM plan of the same g_ewald and qqrd2e it completes the Coulomb
+    interaction."""
+
+    def __init__(self, box, n_max, r_cut, g_ewald, precision="fp32", qqrd2e=1.0, stream=None, device=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        L = lib()
+        L.pppm_real_setup.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_void_p]
+        L.pppm_real_compute.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        L.pppm_real_sync.argtypes = [ctypes.c_void_p]
+        L.pppm_real_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+        L.pppm_real_destroy.argtypes = [ctypes.c_void_p]
+        for nm in ("pppm_real_setup", "pppm_real_compute", "pppm_real_sync", "pppm_real_info", "pppm_real_destroy"):
+            getattr(L, nm).restype = ctypes.c_int
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(L.pppm_real_setup(ctypes.byref(h), _d3(box), int(n_max), float(r_cut), float(g_ewald),
+                                     PRECISIONS[precision], float(qqrd2e), ctypes.c_void_p(self.stream.cuda_stream)),
+                   "pppm_real_setup")
+        self._h = h
+        self.ev = torch.zeros(8, dtype=torch.float64, device=self.device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pppm_real_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        a = (ctypes.c_int64 * 4)()
+        _check(lib().pppm_real_info(self._h, a), "pppm_real_info")
+        return {"cells": (a[0], a[1], a[2]), "n_max": a[3]}
+
+    def compute(self, x, q, f=None, accumulate=False):
+        """Forces [n, 3] (added onto f when accumulate) and energy/virial [7]."""
+        torch = self.torch
+        x = torch.as_tensor(x, device=self.device, dtype=self.dtype).contiguous()
+        q = torch.as_tensor(q, device=self.device, dtype=self.dtype).contiguous()
+        if f is None:
+            if accumulate:
+                raise ValueError("accumulate needs f")
+            f = torch.empty((x.shape[0], 3), dtype=self.dtype, device=self.device)
+        _check(lib().pppm_real_compute(self._h, x.shape[0], _ptr(x), _ptr(q), _ptr(f), int(bool(accumulate)),
+                                       _ptr(self.ev)), "pppm_real_compute")
+        return f, self.ev[:7]
+
+    def sync(self):
+        _check(lib().pppm_real_sync(self._h), "pppm_real_sync")
+
+
 class PPPMBatch:
     """Many independent systems per call (one launch per stage, one graph)."""
 
