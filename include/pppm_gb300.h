@@ -195,6 +195,15 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * runs), keeps the fastest, writes its bitmask to choice_out (nullable), and
  * leaves f holding a valid result.  Both drop any captured graph. */
 int pppm_set_variant(pppm_plan *p, int variants);
+
+/* Lookup-table stencil coefficients (Sec. 3.1 "precompute", Table 1's LUT-500
+ * and LUT-5000): the coefficients are tabulated at `entries` equally spaced
+ * offsets and each particle takes the nearest entry -- every per-particle use
+ * of the stencil offset (weights, derivative weights, the ad self-force
+ * sines) sees the offset rounded to the centre of its bin.  entries = 0
+ * restores the exact polynomials (the default); 2 <= entries <= 2^24, else
+ * PPPM_EINVAL.  Drops any captured graph. */
+int pppm_set_lut(pppm_plan *p, int entries);
 int pppm_autotune(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, int *choice_out);
 
 /* Plan facts: [0..2] mesh, [3] order, [4] ntiles, [5] widest tile along z,

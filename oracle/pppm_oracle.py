@@ -54,6 +54,14 @@ R11 ad force F_i,a = C q_i sum_p (M_P'(p_a - u_a)/h_a) W_b W_c phi(p) minus the
 R12 g_ewald from the real-space force-error estimate
     2 q2 exp(-g^2 rc^2)/sqrt(N rc V) = rel_acc (q2 = sum q^2, in units where
     the force between two unit charges 1 A apart is 1).
+R17 Lookup-table coefficients (Sec. 3.1 "precompute"; Table 1's LUT-500 and
+    LUT-5000): the coefficients are tabulated at K equally spaced offsets and
+    a particle takes the nearest entry.  A nearest-entry table of the exact
+    polynomials is the polynomials evaluated at the offset rounded to the
+    centre of its bin: delta_q = lo + (floor((delta - lo) K) + 1/2)/K over the
+    offset range [lo, lo + 1) (lo = -1/2 for odd P, -1 for even P).  Every
+    per-particle use of the offset takes delta_q, the ad self-force sines
+    included.  K = 0 means exact coefficients.
 
 Every function works in float64 and is written for reading, not speed.
 """
@@ -69,7 +77,7 @@ __all__ = [
     "half_spectrum_weights", "poisson_ik", "poisson_ad", "energy_virial_mesh",
     "fieldforce_ik", "fieldforce_ad", "fieldforce_ad_uncorrected", "interpolate_potential",
     "ad_selfforce_coeffs",
-    "ad_selfforce", "estimate_g_ewald", "OraclePPPM", "self_energy",
+    "ad_selfforce", "estimate_g_ewald", "OraclePPPM", "self_energy", "lut_offset",
     "background_energy",
 ]
 
@@ -125,13 +133,24 @@ def wrap_positions(x, box) -> np.ndarray:
     return np.where(xw >= box, 0.0, xw)
 
 
-def stencil(u, P: int, M: int):
+def lut_offset(delta, P: int, lut: int):
+    """R17: the offset delta = n - u rounded to the centre of its table bin."""
+    lo = -0.5 if P % 2 == 1 else -1.0
+    b = np.clip(np.floor((delta - lo) * lut), 0, lut - 1)
+    return lo + (b + 0.5) / lut
+
+
+def stencil(u, P: int, M: int, lut: int = 0):
     """Stencil of a particle at grid coordinate u (one dimension).
 
-    Returns (points [N, P] wrapped mod M, offsets s = point - u [N, P]).
+    Returns (points [N, P] wrapped mod M, offsets s = point - u [N, P]);
+    with a table of lut entries (R17) the offsets are those of the rounded
+    offset.
     """
     u = np.asarray(u, dtype=np.float64)
     n = np.floor(u + 0.5) if P % 2 == 1 else np.floor(u)
+    if lut:
+        u = n - lut_offset(n - u, P, lut)
     pts = n[:, None] - (P - 1) // 2 + np.arange(P)[None, :]
     s = pts - u[:, None]
     return np.mod(pts, M).astype(np.int64), s
@@ -148,14 +167,14 @@ def _grid_coords(x, box, mesh):
 # ----------------------------------------------------------------------------
 # R3: make_rho (Sec. 3.1 Map-Charge: charge times coefficient added to the grid)
 # ----------------------------------------------------------------------------
-def make_rho(x, q, box, mesh, P: int) -> np.ndarray:
+def make_rho(x, q, box, mesh, P: int, lut: int = 0) -> np.ndarray:
     """Mesh charge density rho[Mx, My, Mz] = (1/h^3) sum_i q_i Wx Wy Wz."""
     q = np.asarray(q, dtype=np.float64)
     Mx, My, Mz = (int(m) for m in mesh)
     u, h = _grid_coords(x, box, mesh)
-    ix, sx = stencil(u[:, 0], P, Mx)
-    iy, sy = stencil(u[:, 1], P, My)
-    iz, sz = stencil(u[:, 2], P, Mz)
+    ix, sx = stencil(u[:, 0], P, Mx, lut)
+    iy, sy = stencil(u[:, 1], P, My, lut)
+    iz, sz = stencil(u[:, 2], P, Mz, lut)
     wx, wy, wz = bspline(P, sx), bspline(P, sy), bspline(P, sz)
     rho = np.zeros(Mx * My * Mz)
     for kx in range(P):
@@ -317,21 +336,21 @@ def energy_virial_mesh(rho_hat, G, box, mesh, g, C):
 # ----------------------------------------------------------------------------
 # R10, R11: Distribute-Force (Sec. 3.1)
 # ----------------------------------------------------------------------------
-def _weights(x, box, mesh, P, deriv=False):
+def _weights(x, box, mesh, P, deriv=False, lut=0):
     u, h = _grid_coords(x, box, mesh)
     out = []
     for d in range(3):
-        idx, s = stencil(u[:, d], P, int(mesh[d]))
+        idx, s = stencil(u[:, d], P, int(mesh[d]), lut)
         w = bspline(P, s)
         dw = bspline_deriv(P, s) if deriv else None
         out.append((idx, w, dw))
     return out, u, h
 
 
-def fieldforce_ik(x, q, fields, box, mesh, P, C):
+def fieldforce_ik(x, q, fields, box, mesh, P, C, lut=0):
     """F_i = C q_i sum over the P^3 stencil of W * (Ex, Ey, Ez)."""
     q = np.asarray(q, dtype=np.float64)
-    (ix, wx, _), (iy, wy, _), (iz, wz, _) = _weights(x, box, mesh, P)[0]
+    (ix, wx, _), (iy, wy, _), (iz, wz, _) = _weights(x, box, mesh, P, lut=lut)[0]
     acc = np.zeros((q.size, 3))
     for kx in range(P):
         for ky in range(P):
@@ -342,9 +361,9 @@ def fieldforce_ik(x, q, fields, box, mesh, P, C):
     return C * q[:, None] * acc
 
 
-def interpolate_potential(x, phi, box, mesh, P):
+def interpolate_potential(x, phi, box, mesh, P, lut=0):
     """phi(x_i) = sum over the stencil of W * phi (transpose of make_rho)."""
-    (ix, wx, _), (iy, wy, _), (iz, wz, _) = _weights(x, box, mesh, P)[0]
+    (ix, wx, _), (iy, wy, _), (iz, wz, _) = _weights(x, box, mesh, P, lut=lut)[0]
     out = np.zeros(ix.shape[0])
     for kx in range(P):
         for ky in range(P):
@@ -352,10 +371,10 @@ def interpolate_potential(x, phi, box, mesh, P):
     return out
 
 
-def fieldforce_ad_uncorrected(x, q, phi, box, mesh, P, C):
+def fieldforce_ad_uncorrected(x, q, phi, box, mesh, P, C, lut=0):
     """C q_i E_a with E_a = sum (M_P'(p_a - u_a)/h_a) W_b W_c phi(p)."""
     q = np.asarray(q, dtype=np.float64)
-    (ix, wx, dx), (iy, wy, dy), (iz, wz, dz) = _weights(x, box, mesh, P, deriv=True)[0]
+    (ix, wx, dx), (iy, wy, dy), (iz, wz, dz) = _weights(x, box, mesh, P, deriv=True, lut=lut)[0]
     h = np.asarray(box, dtype=np.float64) / np.asarray(mesh, dtype=np.float64)
     e = np.zeros((q.size, 3))
     for kx in range(P):
@@ -405,10 +424,14 @@ def ad_selfforce_coeffs(G, box, mesh, P, C) -> np.ndarray:
     return c
 
 
-def ad_selfforce(x, q, coeffs, box, mesh):
-    """q_i^2 sum_n c_{a,n} sin(2 pi n u_a) for each particle and axis."""
+def ad_selfforce(x, q, coeffs, box, mesh, P=None, lut=0):
+    """q_i^2 sum_n c_{a,n} sin(2 pi n u_a) for each particle and axis (with
+    a coefficient table, u from the rounded offset, R17)."""
     q = np.asarray(q, dtype=np.float64)
     u, _ = _grid_coords(x, box, mesh)
+    if lut:
+        n = np.floor(u + 0.5) if P % 2 == 1 else np.floor(u)
+        u = n - lut_offset(n - u, P, lut)
     sf = np.zeros_like(u)
     for a in range(3):
         for n in (1, 2):
@@ -416,10 +439,10 @@ def ad_selfforce(x, q, coeffs, box, mesh):
     return (q * q)[:, None] * sf
 
 
-def fieldforce_ad(x, q, phi, box, mesh, P, C, coeffs=None):
-    F = fieldforce_ad_uncorrected(x, q, phi, box, mesh, P, C)
+def fieldforce_ad(x, q, phi, box, mesh, P, C, coeffs=None, lut=0):
+    F = fieldforce_ad_uncorrected(x, q, phi, box, mesh, P, C, lut)
     if coeffs is not None:
-        F = F - ad_selfforce(x, q, coeffs, box, mesh)
+        F = F - ad_selfforce(x, q, coeffs, box, mesh, P, lut)
     return F
 
 
@@ -441,7 +464,7 @@ def estimate_g_ewald(rel_acc, r_cut, n, q2, box) -> float:
 class OraclePPPM:
     """Set up once per (box, mesh, P, g, mode); ``compute`` runs steps 1-3."""
 
-    def __init__(self, box, mesh, order, g_ewald, mode="ik", qqrd2e=1.0, selfforce=True):
+    def __init__(self, box, mesh, order, g_ewald, mode="ik", qqrd2e=1.0, selfforce=True, lut=0):
         if mode not in ("ik", "ad"):
             raise ValueError(mode)
         if order < 2:
@@ -452,6 +475,7 @@ class OraclePPPM:
         self.g = float(g_ewald)
         self.mode = mode
         self.C = float(qqrd2e)
+        self.lut = int(lut)  # R17: coefficient table entries, 0 = exact
         if mode == "ik":
             self.G = influence_ik(self.box, self.mesh, self.P, self.g)
             self.sf = None
@@ -464,17 +488,17 @@ class OraclePPPM:
         whose forces are wanted (all particles still build the mesh)."""
         x = np.asarray(x, dtype=np.float64)
         q = np.asarray(q, dtype=np.float64)
-        rho = make_rho(x, q, self.box, self.mesh, self.P)
+        rho = make_rho(x, q, self.box, self.mesh, self.P, self.lut)
         xs, qs = (x, q) if subset is None else (x[subset], q[subset])
         out = {}
         if self.mode == "ik":
             rho_hat, fields = poisson_ik(rho, self.G, self.box)
-            f = fieldforce_ik(xs, qs, fields, self.box, self.mesh, self.P, self.C)
+            f = fieldforce_ik(xs, qs, fields, self.box, self.mesh, self.P, self.C, self.lut)
             if keep:
                 out["fields"] = fields
         else:
             rho_hat, phi = poisson_ad(rho, self.G)
-            f = fieldforce_ad(xs, qs, phi, self.box, self.mesh, self.P, self.C, self.sf)
+            f = fieldforce_ad(xs, qs, phi, self.box, self.mesh, self.P, self.C, self.sf, self.lut)
             if keep:
                 out["phi"] = phi
         E_mesh, vir = energy_virial_mesh(rho_hat, self.G, self.box, self.mesh, self.g, self.C)
@@ -486,7 +510,7 @@ class OraclePPPM:
 
     def potential_mesh(self, x, q):
         """phi on the mesh from this plan's G (the ik plan's G for ik)."""
-        rho = make_rho(x, q, self.box, self.mesh, self.P)
+        rho = make_rho(x, q, self.box, self.mesh, self.P, self.lut)
         return np.fft.irfftn(self.G * np.fft.rfftn(rho), s=self.mesh, axes=(0, 1, 2))
 
     def energy_gradients(self, x, q):
@@ -498,9 +522,9 @@ class OraclePPPM:
         x = np.asarray(x, dtype=np.float64)
         q = np.asarray(q, dtype=np.float64)
         phi = self.potential_mesh(x, q)
-        dEdx = -fieldforce_ad_uncorrected(x, q, phi, self.box, self.mesh, self.P, self.C)
+        dEdx = -fieldforce_ad_uncorrected(x, q, phi, self.box, self.mesh, self.P, self.C, self.lut)
         V = float(np.prod(self.box))
-        dEdq = (self.C * interpolate_potential(x, phi, self.box, self.mesh, self.P)
+        dEdq = (self.C * interpolate_potential(x, phi, self.box, self.mesh, self.P, self.lut)
                 - 2.0 * self.C * self.g * q / math.sqrt(math.pi)
                 - self.C * math.pi * float(np.sum(q)) / (self.g * self.g * V))
         return dEdx, dEdq

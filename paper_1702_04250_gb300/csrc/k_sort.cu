@@ -234,6 +234,17 @@ __device__ __forceinline__ void scatter_body(const Geom<R> &g, int n, const R *_
     }
     pdl_trigger();
     if (i >= n) return;
+    if (g.lut_bins > 0) {
+        // table coefficients (Sec. 3.1 "precompute"): the offset rounded to
+        // the centre of its bin, so every later use reads the table's entry
+        const R lo = (g.P & 1) ? R(-0.5) : R(-1), K = (R)g.lut_bins;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R bin = floor((d[k] - lo) * K);
+            bin = bin < R(0) ? R(0) : (bin > K - R(1) ? K - R(1) : bin);
+            d[k] = lo + (bin + R(0.5)) / K;
+        }
+    }
     const uint32_t packed = b.anchor[i];  // same computation as k_particle_map
     int s[3];
     unpack_anchor(packed, s[0], s[1], s[2]);

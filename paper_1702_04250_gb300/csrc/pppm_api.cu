@@ -819,6 +819,13 @@ int pppm_stage_times(pppm_plan *p, float ms[6]) {
     return PPPM_OK;
 }
 
+int pppm_set_lut(pppm_plan *p, int entries) {
+    if (!p || entries < 0 || entries == 1 || entries > (1 << 24)) return PPPM_EINVAL;
+    p->gf.lut_bins = p->gd.lut_bins = entries;
+    drop_graph(p);
+    return PPPM_OK;
+}
+
 int pppm_set_variant(pppm_plan *p, int variants) {
     if (!p || !variant_ok(p, variants)) return PPPM_EINVAL;
     set_variants(p, variants);

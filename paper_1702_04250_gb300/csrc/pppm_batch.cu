@@ -115,6 +115,9 @@ void fill_geom_b(Geom<R> &g, const double box[3], const int M[3], int P, bool co
     g.rlo = (P - 1) / 2;
     g.ivcell = (R)(1.0 / vcell);
     g.ff_tiled = 0;
+    g.rho_copies = 0;
+    g.lut_bins = 0;
+    g.launch_flags = 0;
     g.planar_stride = 0;
     for (int k = 0; k < MAXP; ++k)
         for (int l = 0; l < MAXP; ++l) {

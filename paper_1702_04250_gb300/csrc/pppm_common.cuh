@@ -55,6 +55,7 @@ struct Geom {
     R dcoef[MAXP][MAXP];  // d/ddelta of the same polynomials
     int ff_tiled;         // fieldforce variant: 0 per-particle through L1, 1 tile-staged brick
     int rho_copies;       // FP32C make_rho variant: 0 one shared brick, 1 four interleaved copies
+    int lut_bins;         // coefficient table entries (0: exact polynomials), see pppm_set_lut
     int launch_flags;     // host side: LF_* launch options of this step
     int planar_stride;    // ik field layout: 0 interleaved (Ex,Ey,Ez,pad); > 0 three planes this far apart
 };

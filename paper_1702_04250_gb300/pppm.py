@@ -62,11 +62,12 @@ def lib() -> ctypes.CDLL:
         L.pppm_set_profiling.argtypes = [vp, i32]
         L.pppm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         L.pppm_set_variant.argtypes = [vp, i32]
+        L.pppm_set_lut.argtypes = [vp, i32]
         L.pppm_autotune.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(i32)]
         for name in ("pppm_estimate_g", "pppm_setup", "pppm_destroy", "pppm_set_stream", "pppm_set_graph",
                      "pppm_compute", "pppm_compute_host", "pppm_sync", "pppm_energy_grad", "pppm_potential",
                      "pppm_get_array",
-                     "pppm_plan_info", "pppm_set_profiling", "pppm_stage_times", "pppm_set_variant",
+                     "pppm_plan_info", "pppm_set_profiling", "pppm_stage_times", "pppm_set_variant", "pppm_set_lut",
                      "pppm_autotune"):
             getattr(L, name).restype = i32
         _lib = L
@@ -188,6 +189,10 @@ class PPPM:
 
     def set_variant(self, variants: int):
         _check(lib().pppm_set_variant(self._h, int(variants)), "pppm_set_variant")
+
+    def set_lut(self, entries: int):
+        """Tabulated stencil coefficients with `entries` samples (0: exact)."""
+        _check(lib().pppm_set_lut(self._h, int(entries)), "pppm_set_lut")
 
     def autotune(self, x, q):
         """Time the kernel variants on these inputs, keep the fastest; returns its bitmask."""

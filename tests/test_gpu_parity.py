@@ -352,6 +352,42 @@ def test_order7_variants(torch, mode):
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, "fp32c", f"P=7 autotuned {choice}")
 
 
+@pytest.mark.parametrize("mode", ["ik", "ad"])
+def test_lut_coefficients_vs_oracle(torch, mode):
+    """Table coefficients (LUT-500 / LUT-5000) against the oracle's table,
+    FP64 on c1 and FP32C on c2; entries = 0 restores the exact path."""
+    from paper_1702_04250_gb300 import pppm
+
+    w = config("c1")
+    g = g_of(w)
+    x = torch.tensor(w.x, dtype=torch.float64, device="cuda")
+    q = torch.tensor(w.q, dtype=torch.float64, device="cuda")
+    plan = pppm.PPPM(w.box, w.n, 7, w.mesh, g, mode, "fp64", w.qqrd2e)
+    for K in (500, 5000):
+        plan.set_lut(K)
+        f, ev = plan.compute(x, q)
+        plan.sync()
+        ref = OraclePPPM(w.box, w.mesh, 7, g, mode, w.qqrd2e, lut=K).compute(w.x, w.q)
+        check_all(f.cpu().numpy(), ev.cpu().numpy(), ref, "fp64", f"c1 LUT-{K} {mode}")
+    plan.set_lut(0)
+    f, ev = plan.compute(x, q)
+    plan.sync()
+    check_all(f.cpu().numpy(), ev.cpu().numpy(), OraclePPPM(w.box, w.mesh, 7, g, mode, w.qqrd2e).compute(w.x, w.q),
+              "fp64", f"c1 exact {mode}")
+    with pytest.raises(pppm.PPPMError):
+        plan.set_lut(1)
+    w2 = config("c2")
+    g2 = g_of(w2)
+    p32 = pppm.PPPM(w2.box, w2.n, w2.order, w2.mesh, g2, mode, "fp32c", w2.qqrd2e)
+    p32.set_lut(5000)
+    f, ev = p32.compute(torch.tensor(w2.x, dtype=torch.float32, device="cuda"),
+                        torch.tensor(w2.q, dtype=torch.float32, device="cuda"))
+    p32.sync()
+    xo, qo = oracle_inputs(w2.x, w2.q, "fp32")
+    ref = OraclePPPM(w2.box, w2.mesh, w2.order, g2, mode, w2.qqrd2e, lut=5000).compute(xo, qo)
+    check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, "fp32c", f"c2 LUT-5000 {mode}")
+
+
 def test_fp64_repeatable(torch, c2_refs):
     w, g, refs = c2_refs
     outs = []

@@ -42,7 +42,7 @@ def test_planted_half_spectrum_weight(ref, monkeypatch):
 def test_planted_odd_anchor_floor(ref, monkeypatch):
     real = po.stencil
 
-    def bad(u, P, M):
+    def bad(u, P, M, lut=0):
         u = np.asarray(u, dtype=np.float64)
         n = np.floor(u)  # should round to the nearest point for odd P
         pts = n[:, None] - (P - 1) // 2 + np.arange(P)[None, :]
