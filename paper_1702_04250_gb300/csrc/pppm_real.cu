@@ -7,13 +7,14 @@
 // over minimum images (r_C < L/2).
 //
 // GB300 layout: the particles are binned into cells at least r_C/2 wide with
-// the PPPM sort kernels (order 2: the anchor is the cell, one tile per cell),
-// their wrapped positions written once as float4/double4 (x, y, z, q) in cell
-// order, and one thread per sorted particle walks the 5^3 cells around its
-// own (a dimension with fewer than 5 cells is one cell), reading candidates
-// through L1: consecutive threads share a cell, so a warp's loads are mostly
-// broadcasts.  Each pair is computed from both ends (no atomics); per-CTA
-// energy/virial partials are summed in FP64 in a fixed order.
+// the PPPM sort kernels (order 2: the anchor is the cell, one tile per cell)
+// and their wrapped positions written once as float4/double4 (x, y, z, q) in
+// cell order.  One warp per cell: its lanes hold the cell's particles (32 at
+// a time), and the warp walks the 5^3 cells around it (a dimension with fewer
+// than 5 cells is one cell) in step, so every candidate is one broadcast load
+// for the whole warp and no lane diverges from the loop.  Each pair is
+// computed from both ends (no atomics); per-warp energy/virial partials are
+// summed in FP64 in a fixed order.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -66,84 +67,94 @@ __global__ void __launch_bounds__(256) k_real_positions(RealGeom<R> rg, SortBufs
     pos[j] = o;
 }
 
+constexpr int REAL_WARPS = REAL_THREADS / 32;  // cells per CTA
+
 template <typename R>
-__global__ void __launch_bounds__(REAL_THREADS) k_real_pairs(RealGeom<R> rg, SortBufs b, int n,
+__global__ void __launch_bounds__(REAL_THREADS) k_real_pairs(RealGeom<R> rg, SortBufs b, int ncells,
                                                             const vec4_t<R> *__restrict__ pos, R *__restrict__ f,
                                                             int accumulate, R C, double *__restrict__ part) {
-    __shared__ double sh[7][REAL_THREADS / 32];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    R fx = 0, fy = 0, fz = 0, e = 0, vxx = 0, vyy = 0, vzz = 0, vxy = 0, vxz = 0, vyz = 0;
-    if (j < n) {
-        const vec4_t<R> pi = pos[j];
-        int c[3];
-        unpack_anchor(b.cell[j], c[0], c[1], c[2]);
-        for (int ox = -rg.span[0]; ox <= rg.span[0]; ++ox) {
-            int cx = c[0] + ox;
-            cx += (cx < 0) ? rg.nc[0] : 0;
-            cx -= (cx >= rg.nc[0]) ? rg.nc[0] : 0;
-            for (int oy = -rg.span[1]; oy <= rg.span[1]; ++oy) {
-                int cy = c[1] + oy;
-                cy += (cy < 0) ? rg.nc[1] : 0;
-                cy -= (cy >= rg.nc[1]) ? rg.nc[1] : 0;
-                for (int oz = -rg.span[2]; oz <= rg.span[2]; ++oz) {
-                    int cz = c[2] + oz;
-                    cz += (cz < 0) ? rg.nc[2] : 0;
-                    cz -= (cz >= rg.nc[2]) ? rg.nc[2] : 0;
-                    const int cell = (cx * rg.nc[1] + cy) * rg.nc[2] + cz;
-                    const int s = b.tile_start[cell], t = b.tile_start[cell + 1];
-                    for (int k = s; k < t; ++k) {
-                        const vec4_t<R> pj = pos[k];
-                        R dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-                        dx -= rg.L[0] * rint_t(dx * rg.iL[0]);
-                        dy -= rg.L[1] * rint_t(dy * rg.iL[1]);
-                        dz -= rg.L[2] * rint_t(dz * rg.iL[2]);
-                        const R r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < rg.rc2 && k != j) {
-                            const R ir = rsqrt_t(r2);
-                            const R r = r2 * ir;
-                            const R qq = pi.w * pj.w;
-                            const R et = erfc_t(rg.g * r) * ir;
-                            const R fr = qq * (et + rg.c2g * exp_t(-rg.g2 * r2)) * ir * ir;
-                            fx += fr * dx;
-                            fy += fr * dy;
-                            fz += fr * dz;
-                            e += qq * et;
-                            vxx += fr * dx * dx;
-                            vyy += fr * dy * dy;
-                            vzz += fr * dz * dz;
-                            vxy += fr * dx * dy;
-                            vxz += fr * dx * dz;
-                            vyz += fr * dy * dz;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cell = blockIdx.x * REAL_WARPS + w;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (cell < ncells) {
+        const int cz = cell % rg.nc[2];
+        const int cy = (cell / rg.nc[2]) % rg.nc[1];
+        const int cx = cell / (rg.nc[2] * rg.nc[1]);
+        const int hs = b.tile_start[cell], he = b.tile_start[cell + 1];
+        for (int h0 = hs; h0 < he; h0 += 32) {   // the cell's particles, a warp-full at a time
+            const int j = h0 + lane;
+            const bool live = j < he;
+            const vec4_t<R> pi = pos[live ? j : hs];
+            R fx = 0, fy = 0, fz = 0, e = 0, vxx = 0, vyy = 0, vzz = 0, vxy = 0, vxz = 0, vyz = 0;
+            for (int ox = -rg.span[0]; ox <= rg.span[0]; ++ox) {
+                int nx = cx + ox;
+                nx += (nx < 0) ? rg.nc[0] : 0;
+                nx -= (nx >= rg.nc[0]) ? rg.nc[0] : 0;
+                for (int oy = -rg.span[1]; oy <= rg.span[1]; ++oy) {
+                    int ny = cy + oy;
+                    ny += (ny < 0) ? rg.nc[1] : 0;
+                    ny -= (ny >= rg.nc[1]) ? rg.nc[1] : 0;
+                    for (int oz = -rg.span[2]; oz <= rg.span[2]; ++oz) {
+                        int nz = cz + oz;
+                        nz += (nz < 0) ? rg.nc[2] : 0;
+                        nz -= (nz >= rg.nc[2]) ? rg.nc[2] : 0;
+                        const int nb = (nx * rg.nc[1] + ny) * rg.nc[2] + nz;
+                        const int s = b.tile_start[nb], t = b.tile_start[nb + 1];
+                        for (int k = s; k < t; ++k) {   // warp-uniform: one broadcast load per candidate
+                            const vec4_t<R> pj = pos[k];
+                            R dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                            dx -= rg.L[0] * rint_t(dx * rg.iL[0]);
+                            dy -= rg.L[1] * rint_t(dy * rg.iL[1]);
+                            dz -= rg.L[2] * rint_t(dz * rg.iL[2]);
+                            const R r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < rg.rc2 && k != j && live) {
+                                const R ir = rsqrt_t(r2);
+                                const R r = r2 * ir;
+                                const R qq = pi.w * pj.w;
+                                const R et = erfc_t(rg.g * r) * ir;
+                                const R fr = qq * (et + rg.c2g * exp_t(-rg.g2 * r2)) * ir * ir;
+                                fx += fr * dx;
+                                fy += fr * dy;
+                                fz += fr * dz;
+                                e += qq * et;
+                                vxx += fr * dx * dx;
+                                vyy += fr * dy * dy;
+                                vzz += fr * dz * dz;
+                                vxy += fr * dx * dy;
+                                vxz += fr * dx * dz;
+                                vyz += fr * dy * dz;
+                            }
                         }
                     }
                 }
             }
-        }
-        R *fo = f + 3 * (int64_t)b.perm[j];
-        if (accumulate) {
-            fo[0] += C * fx;
-            fo[1] += C * fy;
-            fo[2] += C * fz;
-        } else {
-            fo[0] = C * fx;
-            fo[1] = C * fy;
-            fo[2] = C * fz;
-        }
-    }
-    // block partials: FP32 paths reduce within the warp in FP32 (GB300's FP64
-    // rate is a small fraction of its FP32 rate), the per-warp values in FP64
-    const R vals[7] = {e, vxx, vyy, vzz, vxy, vxz, vyz};
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+            if (live) {
+                R *fo = f + 3 * (int64_t)b.perm[j];
+                if (accumulate) {
+                    fo[0] += C * fx;
+                    fo[1] += C * fy;
+                    fo[2] += C * fz;
+                } else {
+                    fo[0] = C * fx;
+                    fo[1] = C * fy;
+                    fo[2] = C * fz;
+                }
+            }
+            // FP32 paths reduce within the warp in FP32 (GB300's FP64 rate is a
+            // small fraction of its FP32 rate), the per-warp values in FP64
+            const R vals[7] = {e, vxx, vyy, vzz, vxy, vxz, vyz};
 #pragma unroll
-    for (int m = 0; m < 7; ++m) {
-        const R v = warp_sum_t<R>(vals[m]);
-        if (lane == 0) sh[m][w] = (double)v;
+            for (int mm = 0; mm < 7; ++mm) acc[mm] += (double)warp_sum_t<R>(vals[mm]);
+        }
     }
+    __shared__ double sh[7][REAL_WARPS];
+    if (lane == 0)
+        for (int mm = 0; mm < 7; ++mm) sh[mm][w] = acc[mm];
     __syncthreads();
     if (threadIdx.x < 7) {
-        double acc = 0.0;
-        for (int k = 0; k < REAL_THREADS / 32; ++k) acc += sh[threadIdx.x][k];
-        part[7 * (int64_t)blockIdx.x + threadIdx.x] = 0.5 * acc * (double)C;
+        double a = 0.0;
+        for (int k = 0; k < REAL_WARPS; ++k) a += sh[threadIdx.x][k];
+        part[7 * (int64_t)blockIdx.x + threadIdx.x] = 0.5 * a * (double)C;
     }
 }
 
@@ -241,10 +252,10 @@ int real_enqueue(pppm_real *r, const RealGeom<R> &rg, const Geom<R> &g, int64_t 
     launch_sort<R>(g, n, (const R *)x, (const R *)q, r->sb, s);
     const int nb = (int)((n + 255) / 256);
     k_real_positions<R><<<nb, 256, 0, s>>>(rg, r->sb, (int)n, (vec4_t<R> *)r->pos);
-    const int np = (int)((n + REAL_THREADS - 1) / REAL_THREADS);
+    const int np = (g.ntiles + REAL_WARPS - 1) / REAL_WARPS;  // one warp per cell
     // the sort's histogram is cleared by make_rho in the PPPM step; here after the pairs
-    k_real_pairs<R><<<np, REAL_THREADS, 0, s>>>(rg, r->sb, (int)n, (const vec4_t<R> *)r->pos, (R *)f, accumulate,
-                                                (R)r->C, r->part);
+    k_real_pairs<R><<<np, REAL_THREADS, 0, s>>>(rg, r->sb, g.ntiles, (const vec4_t<R> *)r->pos, (R *)f,
+                                                accumulate, (R)r->C, r->part);
     if (cudaMemsetAsync(r->sb.tile_count, 0, 4 * (size_t)g.ntiles, s) != cudaSuccess) return PPPM_ECUDA;
     k_real_final<<<1, 224, 0, s>>>(r->part, np, r->ev, ev);
     const cudaError_t e = cudaGetLastError();
@@ -270,7 +281,7 @@ int pppm_real_setup(pppm_real **out, const double box[3], int64_t n_max, double 
     for (int d = 0; d < 3; ++d) {
         if (!(box[d] > 0) || !std::isfinite(box[d])) return PPPM_EINVAL;
         if (r_cut >= 0.5 * box[d]) return PPPM_EINVAL;  // minimum images
-        int c = (int)std::floor(box[d] / (0.5 * r_cut));
+        int c = (int)std::floor(box[d] / (0.5 * r_cut));  // cells at least r_C/2 wide
         c = std::min(c, MAX_MESH);
         nc[d] = c >= 5 ? c : 1;
     }
@@ -286,7 +297,7 @@ int pppm_real_setup(pppm_real **out, const double box[3], int64_t n_max, double 
     const size_t rs = r->fp64 ? 8 : 4;
     const int64_t nm = std::max<int64_t>(n_max, 1);
     const int ncell = nc[0] * nc[1] * nc[2];
-    r->nb_max = (int)((nm + REAL_THREADS - 1) / REAL_THREADS);
+    r->nb_max = (ncell + REAL_WARPS - 1) / REAL_WARPS;
     int rc = PPPM_OK;
     do {
         if ((rc = rmalloc(r, (void **)&r->sb.anchor, 4 * nm))) break;
