@@ -186,8 +186,13 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * by every plan of this build.  Bit 2: PPPM_FP32C make_rho accumulates in
  * four interleaved copies of the tile brick (no shared-memory bank
  * conflicts, four times the brick's memory) instead of one (PPPM_EINVAL for
- * other precisions).  Default: bit 0 for ik plans whose n_max is at least 16
- * per tile, else 0.
+ * other precisions).  Bit 3: the Poisson solve (forward FFT, influence
+ * function with the energy/virial sums, inverse FFT(s); Sec. 2.1 step 2) runs
+ * as three hand-written kernels instead of cuFFT plus two kernels; allowed
+ * for PPPM_FP32 / PPPM_FP32C plans whose three mesh edges are each 16, 32, 64
+ * or 128 (PPPM_EINVAL otherwise).  Results agree with the cuFFT path to FP32
+ * rounding.  Default: bit 0 for ik plans whose n_max is at least 16 per tile,
+ * plus bit 3 where it is allowed.
  * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a
  * combination the plan does not allow).
  * pppm_autotune times every variant on the caller's inputs (one warm-up and

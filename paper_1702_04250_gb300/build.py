@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpppm_gb300.so")
 SOURCES = ["coeffs.cu", "k_sort.cu", "k_rho.cu", "k_green.cu", "k_force.cu", "pppm_api.cu", "pppm_batch.cu",
-           "pppm_noalloc.cu", "pppm_real.cu"]
+           "pppm_noalloc.cu", "pppm_real.cu", "k_fft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -226,42 +226,6 @@ int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec, con
     return nb;
 }
 
-// warp c < 7 sums energy/virial component c over the green partials, warp 7
-// sums q and q^2 over the particle_map partials; fixed order, one CTA.
-__device__ __forceinline__ void energy_final_body(const GreenBufs &b, const EnergyConsts &ec, int gn, int mn,
-                                                  double *ev_user) {
-    __shared__ double qs[2];
-    __shared__ double comp[7];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (w == 7) {
-        double a = 0.0, c = 0.0;
-        for (int k = lane; k < mn; k += 32) {
-            a += b.map_part[2 * k];
-            c += b.map_part[2 * k + 1];
-        }
-        a = warp_sum(a);
-        c = warp_sum(c);
-        if (lane == 0) {
-            qs[0] = a;
-            qs[1] = c;
-            b.qsum[0] = a;
-            b.qsum[1] = c;
-        }
-    } else {
-        double v = 0.0;
-        for (int k = lane; k < gn; k += 32) v += b.part[7 * k + w];
-        v = warp_sum(v);
-        if (lane == 0) comp[w] = v * ec.epref;
-    }
-    __syncthreads();
-    if (threadIdx.x < 7) {
-        double v = comp[threadIdx.x];
-        if (threadIdx.x == 0) v += ec.eself * qs[1] + ec.ebg * qs[0] * qs[0];
-        b.ev[threadIdx.x] = v;
-        if (ev_user) ev_user[threadIdx.x] = v;
-    }
-}
-
 __global__ void __launch_bounds__(256) k_energy_final(GreenBufs b, EnergyConsts ec, int gn, int mn,
                                                       double *ev_user) {
     energy_final_body(b, ec, gn, mn, ev_user);

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "pppm_common.cuh"
@@ -78,7 +79,9 @@ struct pppm_plan {
     static constexpr int kGraphSlots = 4;
     GraphSlot graphs[kGraphSlots];
     uint64_t graph_clock = 0;
-    int variants = 0;  // bit 0: tile-staged fieldforce, bit 1: long tiles along z
+    int variants = 0;  // bit 0: tile-staged fieldforce, 1: long tiles along z, 2: four-copy
+                       // make_rho brick, 3: hand-written Poisson solve (k_fft.cu)
+    bool fft_own = false;  // the plan's mesh and precision admit variant bit 3
     std::vector<void *> allocs;
 };
 
@@ -358,15 +361,46 @@ int enqueue_t(pppm_plan *p, const Geom<R> &gp, int64_t n, const void *x, const v
     // programmatic launch straight after the scatter unless a stage event sits between them
     launch_make_rho<R>(g, n, p->sb, (R *)p->rho, p->comp, s, true, !need_mark(1) && !chk);
     if ((rc = check("make_rho"))) return rc;
+    const bool ik_spec = (kind == 0) && p->ik;
+    const int mn = (int)((n + 255) / 256);
+    if constexpr (std::is_same<R, float>::value) {
+        if (p->variants & 8) {
+            // forward plane pass | x pass with G, energy and its final sum | inverse plane pass
+            mark(2);
+            launch_custom_fft(0, g, ik_spec, (const float *)p->rho, p->rho_hat, p->spec, (float *)p->field, p->gb,
+                              p->ec, mn, ev, !need_mark(2) && !chk, s);
+            if ((rc = check("forward FFT"))) return rc;
+            mark(3);
+            launch_custom_fft(1, g, ik_spec, (const float *)p->rho, p->rho_hat, p->spec, (float *)p->field, p->gb,
+                              p->ec, mn, ev, !need_mark(3) && !chk, s);
+            if ((rc = check("green"))) return rc;
+            mark(4);
+            launch_custom_fft(2, g, ik_spec, (const float *)p->rho, p->rho_hat, p->spec, (float *)p->field, p->gb,
+                              p->ec, mn, ev, !need_mark(4) && !chk, s);
+            if ((rc = check("inverse FFT"))) return rc;
+            mark(5);
+            if (kind == 0) {
+                launch_fieldforce<R>(g, p->ik, n, p->sb, (const R *)p->field, (R *)f, (R)p->C, p->sf, s);
+            } else {
+                const double gself = -2.0 * p->C * p->g / std::sqrt(M_PI);
+                const double gbg = -p->C * M_PI / (p->g * p->g * p->V);
+                launch_energy_grad<R>(g, n, p->sb, (const R *)p->field, (R *)f, (R *)dq, (R)p->C, p->sb.qsum,
+                                      gself, gbg, s);
+            }
+            if ((rc = check("fieldforce"))) return rc;
+            mark(6);
+            p->prof_valid = pmask;
+            CK(cudaGetLastError());
+            return PPPM_OK;
+        }
+    }
     mark(2);
     if ((rc = exec_r2c(p))) return rc;
     if ((rc = check("forward FFT"))) return rc;
     mark(3);
-    const bool ik_spec = (kind == 0) && p->ik;
     const int gn = launch_green<R>(g, ik_spec, p->rho_hat, p->spec, p->gb, p->ec, s);
     if ((rc = check("green"))) return rc;
     mark(4);
-    const int mn = (int)((n + 255) / 256);
     if (kind == 0) {
         // the final energy/virial sum runs beside the inverse FFTs and fieldforce
         CK(cudaEventRecord(p->fork, s));
@@ -417,14 +451,16 @@ void drop_graph(pppm_plan *p) {
 }
 
 bool variant_ok(const pppm_plan *p, int v) {
-    if (v & ~7) return false;
+    if (v & ~15) return false;
+    if ((v & 8) && !p->fft_own) return false;  // FP32 plans with power-of-two mesh edges 16..128
     if ((v & 4) && !p->comp) return false;  // the four-copy brick is the FP32C accumulator
     if ((v & 2) && !long_tiles_allowed(p->P, p->comp)) return false;
     return !((v & 1) && (v & 2));  // the tile-staged fieldforce brick holds 8^3 tiles only
 }
 
-// Variant bits: 0 tile-staged fieldforce, 1 long tiles (16 along z).  The
-// tile shape changes the sort; the histogram is cleared for the new shape.
+// Variant bits: 0 tile-staged fieldforce, 1 long tiles (16 along z), 2
+// four-copy make_rho brick, 3 hand-written Poisson solve.  The tile shape
+// changes the sort; the histogram is cleared for the new shape.
 void set_variants(pppm_plan *p, int v) {
     p->variants = v;
     tile_shape(p->M, (v & 2) != 0, p->T, p->TE);
@@ -601,12 +637,15 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         return fail(PPPM_ECUDA);
     cudaError_t pe = p->fp64 ? prepare_make_rho<double>(order, false) : prepare_make_rho<float>(order, p->comp);
     if (pe == cudaSuccess) pe = p->fp64 ? prepare_fieldforce<double>(order) : prepare_fieldforce<float>(order);
+    p->fft_own = !p->fp64 && custom_fft_supported(p->M);
+    if (pe == cudaSuccess && p->fft_own) pe = prepare_custom_fft(p->M);
     if (pe != cudaSuccess) return fail(PPPM_ECUDA);
     // default kernel variants (pppm_autotune refines them on real inputs):
     // the ik field (16 bytes a point) is worth staging per tile once tiles
     // hold enough particles; the ad potential (4 bytes) reads best through L1
     // (the four-copy make_rho brick measured level at P = 5 and slower at P = 7)
-    set_variants(p, (p->ik && (double)n_max >= 16.0 * p->ntiles) ? 1 : 0);
+    // the hand-written Poisson solve replaces seven cuFFT/green launches by three
+    set_variants(p, ((p->ik && (double)n_max >= 16.0 * p->ntiles) ? 1 : 0) | (p->fft_own ? 8 : 0));
     if ((rc = build_tables_and_green(p))) return fail(rc);
     if ((rc = make_ffts(p))) return fail(rc);
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(PPPM_ECUDA);
@@ -844,7 +883,7 @@ int pppm_autotune(pppm_plan *p, int64_t n, const void *x, const void *q, void *f
     float best = 1e30f;
     int best_v = p->variants;
     int rc = PPPM_OK;
-    for (int v = 0; v <= 7 && rc == PPPM_OK; ++v) {
+    for (int v = 0; v <= 15 && rc == PPPM_OK; ++v) {
         if (!variant_ok(p, v)) continue;
         set_variants(p, v);
         float tot = 0.0f;

@@ -241,7 +241,7 @@ struct GreenBufs {
     const void *kvec;      // [Mx + My + Mzh] wavenumbers (step type), Nyquist negative
     const void *kdiff;     // same with the Nyquist entries zeroed (ik differentiation)
     double *part;          // [7 * nblk] per-block partial energy/virial
-    unsigned int *counter; // [1] (unused since the final sum moved to k_energy_final)
+    unsigned int *counter; // [1] last-CTA ticket of the fused FFT x pass (zero between steps)
     double *qsum;          // [2] sum q, sum q^2 (written by k_energy_final)
     const double *map_part;// [2 * map_nblk] per-block sum q, sum q^2 of k_particle_map
     double *ev;            // [8] energy + virial
@@ -253,6 +253,43 @@ struct EnergyConsts {
     double ebg;    // -C pi / (2 g^2 V), times Q^2
 };
 
+// Final energy/virial of one system, by one whole 256-thread CTA: warp c < 7
+// sums energy/virial component c over the gn green partials, warp 7 sums q
+// and q^2 over the mn particle_map partials; fixed order.
+__device__ __forceinline__ void energy_final_body(const GreenBufs &b, const EnergyConsts &ec, int gn, int mn,
+                                                  double *ev_user) {
+    __shared__ double qs[2];
+    __shared__ double comp[7];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w == 7) {
+        double a = 0.0, c = 0.0;
+        for (int k = lane; k < mn; k += 32) {
+            a += b.map_part[2 * k];
+            c += b.map_part[2 * k + 1];
+        }
+        a = warp_sum(a);
+        c = warp_sum(c);
+        if (lane == 0) {
+            qs[0] = a;
+            qs[1] = c;
+            b.qsum[0] = a;
+            b.qsum[1] = c;
+        }
+    } else {
+        double v = 0.0;
+        for (int k = lane; k < gn; k += 32) v += b.part[7 * k + w];
+        v = warp_sum(v);
+        if (lane == 0) comp[w] = v * ec.epref;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = comp[threadIdx.x];
+        if (threadIdx.x == 0) v += ec.eself * qs[1] + ec.ebg * qs[0] * qs[0];
+        b.ev[threadIdx.x] = v;
+        if (ev_user) ev_user[threadIdx.x] = v;
+    }
+}
+
 // Returns the number of CTAs launched (the count of energy/virial partials).
 template <typename R>
 int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec,
@@ -261,6 +298,18 @@ int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec,
 // fixed order; one CTA.  ev_user may be NULL.
 void launch_energy_final(const GreenBufs &b, const EnergyConsts &ec, int green_nblk, int map_nblk,
                          double *ev_user, cudaStream_t s);
+
+// Hand-written Poisson solve for FP32 plans with power-of-two mesh edges
+// 16..128 (k_fft.cu): step 0 forward plane pass (rho -> rho_hat), step 1 x
+// pass with the influence function, the energy/virial partials and their
+// final sum into b.ev / ev_user (replaces launch_green + launch_energy_final),
+// step 2 inverse plane pass (spec -> field).  pdl: the launch directly
+// follows its stream predecessor kernel.
+bool custom_fft_supported(const int M[3]);
+cudaError_t prepare_custom_fft(const int M[3]);  // shared-memory opt-in, before capture
+void launch_custom_fft(int step, const Geom<float> &g, bool ik_spec, const float *rho, void *rho_hat, void *spec,
+                       float *field, const GreenBufs &b, const EnergyConsts &ec, int map_nblk, double *ev_user,
+                       bool pdl, cudaStream_t s);
 
 template <typename R>
 cudaError_t prepare_fieldforce(int P);  // shared-memory opt-in of the tile-staged kernels

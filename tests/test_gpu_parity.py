@@ -304,22 +304,25 @@ def test_fieldforce_variants_and_autotune(torch, c2_refs, mode):
     x = torch.tensor(w.x, dtype=torch.float32, device="cuda")
     q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
     plan = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode, "fp32c", w.qqrd2e)
-    for v in (0, 1, 4, 5):  # fieldforce per particle / tile-staged x make_rho one / four brick copies
+    # fieldforce per particle / tile-staged x make_rho one / four brick copies
+    # x cuFFT / hand-written Poisson solve
+    for v in (0, 1, 4, 5, 8, 9, 12, 13):
         plan.set_variant(v)
         f, ev = plan.compute(x, q)
         plan.sync()
         check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"variant {v} {mode}")
     choice = plan.autotune(x, q)
-    assert choice in (0, 1, 4, 5)
+    assert choice in (0, 1, 4, 5, 8, 9, 12, 13)
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"autotuned {choice}")
-    for bad in (2, 3, 6, 7, 8):  # long tiles are reserved; unknown bits
+    for bad in (2, 3, 6, 7, 10, 16):  # long tiles are reserved; unknown bits
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(bad)
     p64 = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode, "fp64", w.qqrd2e)
-    with pytest.raises(pppm.PPPMError):
-        p64.set_variant(4)  # the brick copies are the FP32C accumulator
+    for bad in (4, 8):  # the brick copies are the FP32C accumulator; the own FFT is FP32
+        with pytest.raises(pppm.PPPMError):
+            p64.set_variant(bad)
 
 
 @pytest.mark.parametrize("mode", ["ik", "ad"])
@@ -337,7 +340,7 @@ def test_order7_variants(torch, mode):
     q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
     plan = pppm.PPPM(w.box, w.n, 7, w.mesh, g, mode, "fp32c", w.qqrd2e)
     assert plan.info()["tile"] == 8 and plan.info()["ntiles"] == 512
-    for v in (0, 1, 4, 5):
+    for v in (0, 1, 4, 5, 8, 13):
         plan.set_variant(v)
         f, ev = plan.compute(x, q)
         plan.sync()
@@ -346,7 +349,7 @@ def test_order7_variants(torch, mode):
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(bad)
     choice = plan.autotune(x, q)
-    assert choice in (0, 1, 4, 5)
+    assert choice in (0, 1, 4, 5, 8, 9, 12, 13)
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, "fp32c", f"P=7 autotuned {choice}")
