@@ -2,26 +2,30 @@
 // mesh charge, multiply by the influence function, one (ad) or three (ik)
 // inverse 3-D FFTs -- as three kernels for FP32 plans whose mesh edges are
 // powers of two from 16 to 128:
-//   plane forward   CTA per x-plane: z real-to-complex of every row, then the
-//                   y transform of every kz column      rho -> A[x][ky][kz]
-//   x + Green       CTA per (ky, component): x transform, energy/virial
-//                   partials (component 0; the last such CTA also sums them),
-//                   multiply by G (and -i k_a for ik), x inverse
-//                                                       A -> S_a[x][ky][kz]
+//   plane forward   CTA per x-plane: z real-to-complex of every row (two
+//                   rows packed in one complex transform), then the y
+//                   transform of every kz column         rho -> A[x][ky][kz]
+//   x + Green       a group of lanes per (ky, kz) line and component: x
+//                   transform, energy/virial partials (component 0), multiply
+//                   by G (and -i k_a for ik), x inverse A -> S_a[x][ky][kz]
 //   plane inverse   CTA per (x-plane, component): y inverse of every column,
-//                   then z complex-to-real of every row
+//                   then z complex-to-real of every row pair
 //                                                       S_a -> field / phi
 // Same conventions as the cuFFT path (both directions unnormalised, G/M
 // carries the 1/M), the same spectrum buffers, energy partials, final sums
 // and field layout (ik: interleaved (E_x, E_y, E_z, pad) per point; ad and
 // the potential: one value per point).  cuFFT serves other meshes and FP64.
 //
-// One 1-D transform of length N per warp: element i lives in lane i % 32,
-// register i / 32, loaded in bit-reversed order; log2(N) radix-2
-// decimation-in-time stages follow, a stage whose butterfly partner is in
-// another lane exchanging through a shuffle and one whose partner is in the
-// same lane working in registers.  Twiddles w_N^t = exp(-2 pi i t / N) come
-// from a per-CTA table filled with sincospif.
+// One 1-D transform of length N = E L runs on a group of L lanes holding E
+// points each (E = 8, or 16 for N = 128), as the four-step factorisation
+// with n = j + L a and k = b + E c (j: lane in the group):
+//   X[b + E c] = sum_j W_L^(j c) W_N^(j b) sum_a W_E^(a b) x[j + L a]
+// i.e. an E-point DFT in registers, the twiddle W_N^(j b), a transpose
+// through shared memory, and L-point DFTs in registers.  "In" layout: lane j
+// register a holds index j + L a; "out" layout: lane j' holds the E/L lines
+// b = j' E/L + u, register u L + c holds index b + E c.  The forward runs in
+// -> out, and the inverse runs the same steps backwards (out -> in), so a
+// forward transform, a pointwise product and an inverse need no permutation.
 #include <cmath>
 #include <type_traits>
 
@@ -33,230 +37,359 @@ constexpr int FFT_THREADS = 256;
 constexpr int FFT_WARPS = FFT_THREADS / 32;
 
 template <int N>
-struct FftLen {
+struct Fft {
     static_assert(N == 16 || N == 32 || N == 64 || N == 128, "power-of-two length 16..128");
-    static constexpr int R = N >= 32 ? N / 32 : 1;  // elements per lane
-    static constexpr int LOG = N == 16 ? 4 : N == 32 ? 5 : N == 64 ? 6 : 7;
+    static constexpr int E = (N == 128) ? 16 : 8;  // points per lane
+    static constexpr int L = N / E;                 // lanes per line
+    static constexpr int LINES = E / L;             // b-lines per lane in the out layout
+    static constexpr int G = 32 / L;                // lines per warp
+    static constexpr int P = L + 1;                 // transpose scratch: pitch of a b-row
+    // a line's scratch, E*P complex rounded up to 8 mod 16, so that the two
+    // halves of a 64-bit shared access touch disjoint banks
+    static constexpr int S = E * P + (((8 - E * P) % 16) + 16) % 16;
+    static constexpr int WARP_SCRATCH = G * S;      // complex per warp
 };
 
-template <int N>
-__device__ __forceinline__ int bitrev(int i) {
-    return (int)(__brev((unsigned)i) >> (32 - FftLen<N>::LOG));
+// cos / sin of 2 pi q / 16, q = 0..7
+__device__ __forceinline__ constexpr float c16(int q) {
+    return q == 0 ? 1.0f : q == 1 ? 0.923879532511286756f : q == 2 ? 0.707106781186547524f
+         : q == 3 ? 0.382683432365089772f : q == 4 ? 0.0f : q == 5 ? -0.382683432365089772f
+         : q == 6 ? -0.707106781186547524f : -0.923879532511286756f;
+}
+__device__ __forceinline__ constexpr float s16(int q) {
+    return q == 0 ? 0.0f : q == 1 ? 0.382683432365089772f : q == 2 ? 0.707106781186547524f
+         : q == 3 ? 0.923879532511286756f : q == 4 ? 1.0f : q == 5 ? 0.923879532511286756f
+         : q == 6 ? 0.707106781186547524f : 0.382683432365089772f;
+}
+// i with its low `bits` (<= 4) bits reversed
+__host__ __device__ constexpr int brev_bits(int i, int bits) {
+    return (((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3)) >> (4 - bits);
 }
 
-// tw[t] = exp(-2 pi i t / N), t < N/2 (whole CTA; the caller synchronises)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+    return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+
+// a * W_16^q with W = exp(-2 pi i q / 16) (forward) or its conjugate (INV)
+template <bool INV>
+__device__ __forceinline__ float2 mul_w16(float2 a, int q) {
+    if (q == 0) return a;
+    if (q == 4) return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);  // * (+i) / * (-i)
+    const float c = c16(q), s = INV ? s16(q) : -s16(q);
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+// One radix-2 stage (butterfly span H) of an M-point in-register transform.
+template <int M, int H, bool INV>
+__device__ __forceinline__ void dit_stage(float2 (&t)[M]) {
+#pragma unroll
+    for (int k = 0; k < M; k += 2 * H) {
+#pragma unroll
+        for (int q = 0; q < H; ++q) {
+            const float2 u = t[k + q];
+            const float2 w = mul_w16<INV>(t[k + q + H], q * (8 / H));
+            t[k + q] = cadd(u, w);
+            t[k + q + H] = csub(u, w);
+        }
+    }
+}
+
+// In-register DFT of M = 2, 4, 8, 16 points at v[OFF .. OFF + M), natural
+// order in and out (radix 2, the bit reversal is a renaming of registers).
+template <int M, bool INV, int OFF = 0, int K>
+__device__ __forceinline__ void dft_reg(float2 (&v)[K]) {
+    constexpr int LOGM = M == 2 ? 1 : M == 4 ? 2 : M == 8 ? 3 : 4;
+    float2 t[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) t[i] = v[OFF + brev_bits(i, LOGM)];
+    dit_stage<M, 1, INV>(t);
+    if constexpr (M >= 4) dit_stage<M, 2, INV>(t);
+    if constexpr (M >= 8) dit_stage<M, 4, INV>(t);
+    if constexpr (M >= 16) dit_stage<M, 8, INV>(t);
+#pragma unroll
+    for (int i = 0; i < M; ++i) v[OFF + i] = t[i];
+}
+
+// dft_reg<L> on each of the LINES consecutive L-register lines of v
+template <int L, int LINES, bool INV, int K>
+__device__ __forceinline__ void line_dfts(float2 (&v)[K]) {
+    dft_reg<L, INV, 0>(v);
+    if constexpr (LINES > 1) dft_reg<L, INV, L>(v);
+    if constexpr (LINES > 2) {
+        dft_reg<L, INV, 2 * L>(v);
+        dft_reg<L, INV, 3 * L>(v);
+    }
+}
+
+// index held by register r of lane j in the out layout
+template <int N>
+__device__ __forceinline__ int out_index(int j, int r) {
+    using F = Fft<N>;
+    return (j * F::LINES + r / F::L) + F::E * (r % F::L);
+}
+
+// in layout -> out layout (forward with INV = false).  scr: this line's
+// scratch (Fft<N>::S complex); tw[t] = W_N^t, t < N.  Every lane of the warp
+// calls it (it synchronises the warp).
+template <int N, bool INV>
+__device__ __forceinline__ void fft_in_out(float2 (&v)[Fft<N>::E], float2 *scr, const float2 *tw, int j) {
+    using F = Fft<N>;
+    dft_reg<F::E, INV>(v);
+#pragma unroll
+    for (int b = 1; b < F::E; ++b) {
+        float2 w = tw[j * b];
+        if (INV) w.y = -w.y;
+        v[b] = cmul(v[b], w);
+    }
+#pragma unroll
+    for (int b = 0; b < F::E; ++b) scr[b * F::P + j] = v[b];
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < F::LINES; ++u)
+#pragma unroll
+        for (int c = 0; c < F::L; ++c) v[u * F::L + c] = scr[(j * F::LINES + u) * F::P + c];
+    __syncwarp();
+    line_dfts<F::L, F::LINES, INV>(v);
+}
+
+// out layout -> in layout: the steps of fft_in_out backwards (the inverse
+// transform with INV = true).
+template <int N, bool INV>
+__device__ __forceinline__ void fft_out_in(float2 (&v)[Fft<N>::E], float2 *scr, const float2 *tw, int j) {
+    using F = Fft<N>;
+    line_dfts<F::L, F::LINES, INV>(v);
+#pragma unroll
+    for (int u = 0; u < F::LINES; ++u)
+#pragma unroll
+        for (int c = 0; c < F::L; ++c) scr[(j * F::LINES + u) * F::P + c] = v[u * F::L + c];
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < F::E; ++b) v[b] = scr[b * F::P + j];
+    __syncwarp();
+#pragma unroll
+    for (int b = 1; b < F::E; ++b) {
+        float2 w = tw[j * b];
+        if (INV) w.y = -w.y;
+        v[b] = cmul(v[b], w);
+    }
+    dft_reg<F::E, INV>(v);
+}
+
+// tw[t] = W_N^t = exp(-2 pi i t / N), t < N (whole CTA; the caller synchronises)
 template <int N>
 __device__ __forceinline__ void fill_twiddles(float2 *tw) {
-    for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
         float s, c;
         sincospif(-2.0f * (float)t / (float)N, &s, &c);
         tw[t] = make_float2(c, s);
     }
 }
 
-// In-place length-N transform of this warp's elements (bit-reversed input,
-// natural-order output); INV takes exp(+2 pi i ...).  For N = 16 lanes 16..31
-// carry no element but take part in the shuffles.
-template <int N, bool INV>
-__device__ __forceinline__ void warp_fft(float (&re)[FftLen<N>::R], float (&im)[FftLen<N>::R],
-                                         const float2 *__restrict__ tw, int lane) {
-    constexpr int R = FftLen<N>::R, LOG = FftLen<N>::LOG;
-#pragma unroll
-    for (int s = 1; s <= LOG; ++s) {
-        const int half = 1 << (s - 1);
-        const int tstep = N >> s;  // w_{2 half}^t = w_N^(t tstep)
-        float nre[R], nim[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int i = lane + 32 * r;
-            float pre, pim;
-            if (half < 32) {
-                pre = __shfl_xor_sync(0xffffffffu, re[r], half);
-                pim = __shfl_xor_sync(0xffffffffu, im[r], half);
-            } else {
-                const int rp = r ^ (half >> 5);
-                pre = re[rp];
-                pim = im[rp];
-            }
-            const float2 w = tw[(i & (half - 1)) * tstep];
-            const float wr = w.x, wi = INV ? -w.y : w.y;
-            if ((i & half) == 0) {  // upper: self + w * partner
-                nre[r] = re[r] + (wr * pre - wi * pim);
-                nim[r] = im[r] + (wr * pim + wi * pre);
-            } else {                // lower: partner - w * self
-                nre[r] = pre - (wr * re[r] - wi * im[r]);
-                nim[r] = pim - (wr * im[r] + wi * re[r]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            re[r] = nre[r];
-            im[r] = nim[r];
-        }
-    }
-}
-
-// Transform every column of a [N][ld] complex tile in shared memory in
-// place, one warp per column.
-template <int N, bool INV>
-__device__ __forceinline__ void tile_columns(float2 *tile, int ld, const float2 *tw) {
-    constexpr int R = FftLen<N>::R;
-    const int lane = threadIdx.x & 31;
-    for (int col = threadIdx.x >> 5; col < ld; col += FFT_WARPS) {
-        float re[R], im[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int i = lane + 32 * r;
-            const float2 v = (i < N) ? tile[bitrev<N>(i & (N - 1)) * ld + col] : make_float2(0.f, 0.f);
-            re[r] = v.x;
-            im[r] = v.y;
-        }
-        __syncwarp();
-        warp_fft<N, INV>(re, im, tw, lane);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int i = lane + 32 * r;
-            if (i < N) tile[i * ld + col] = make_float2(re[r], im[r]);
-        }
-    }
-}
-
-template <int N>
-__host__ __device__ constexpr size_t tile_bytes(int ld) {
-    return sizeof(float2) * (size_t)N * ld;
-}
-
-// dst[e] = src(e) for e < NEL by the whole CTA, up to eight loads in flight
-// per thread before their stores (the sources sit in L2: one round trip per
-// eight elements a thread instead of one per element).
-template <int NEL, typename T, typename F>
-__device__ __forceinline__ void stage(T *dst, F src) {
-    constexpr int IT = (NEL + FFT_THREADS - 1) / FFT_THREADS;
+// dst[di(e)] = src(e) for e < NEL by the whole CTA, up to eight loads in
+// flight per thread before their stores (the sources sit in L2).
+template <int NEL, int NT, typename T, typename F, typename D>
+__device__ __forceinline__ void stage(T *dst, F src, D di) {
+    constexpr int IT = (NEL + NT - 1) / NT;
     constexpr int CH = IT < 8 ? IT : 8;
 #pragma unroll
     for (int k0 = 0; k0 < IT; k0 += CH) {
         T v[CH];
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
-            const int e = threadIdx.x + (k0 + k) * FFT_THREADS;
+            const int e = threadIdx.x + (k0 + k) * NT;
             if (k0 + k < IT && e < NEL) v[k] = src(e);
         }
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
-            const int e = threadIdx.x + (k0 + k) * FFT_THREADS;
-            if (k0 + k < IT && e < NEL) dst[e] = v[k];
+            const int e = threadIdx.x + (k0 + k) * NT;
+            if (k0 + k < IT && e < NEL) dst[di(e)] = v[k];
         }
     }
 }
 
-template <int NY, int NZ>
-constexpr size_t plane_fwd_smem() {  // complex tile + the real plane
-    return tile_bytes<NY>(NZ / 2 + 1) + sizeof(float) * (size_t)NY * NZ;
+template <int A, int B>
+__host__ __device__ constexpr int imax() {
+    return A > B ? A : B;
 }
-template <int NX, int MZH>
-constexpr size_t x_green_smem() {  // complex tile + G of the ky plane
-    return tile_bytes<NX>(MZH) + sizeof(float) * (size_t)NX * MZH;
+
+// Warps of a plane CTA: enough that the z row pairs (NY / 2) and the kz
+// columns (NZ / 2 + 1) each take one pass.
+template <int NY, int NZ>
+__host__ __device__ constexpr int plane_warps() {
+    return imax<(NZ / 2 + 1 + Fft<NY>::G - 1) / Fft<NY>::G, (NY / 2 + Fft<NZ>::G - 1) / Fft<NZ>::G>();
+}
+
+// ---- shared-memory budgets (bytes) ----------------------------------------
+template <int NY, int NZ>
+constexpr size_t plane_fwd_smem() {  // complex tile, real plane (pitch NZ + 8), line scratch
+    return sizeof(float2) * (size_t)NY * (NZ / 2 + 1) + sizeof(float) * (size_t)NY * (NZ + 8) +
+           sizeof(float2) * (size_t)plane_warps<NY, NZ>() * imax<Fft<NY>::WARP_SCRATCH, Fft<NZ>::WARP_SCRATCH>();
+}
+template <int NY, int NZ>
+constexpr size_t plane_inv_smem() {  // complex tile, line scratch
+    return sizeof(float2) * (size_t)NY * (NZ / 2 + 1) +
+           sizeof(float2) * (size_t)plane_warps<NY, NZ>() * imax<Fft<NY>::WARP_SCRATCH, Fft<NZ>::WARP_SCRATCH>();
+}
+template <int NX>
+constexpr size_t x_green_smem() {  // line scratch
+    return sizeof(float2) * (size_t)FFT_WARPS * Fft<NX>::WARP_SCRATCH;
 }
 
 // ---- plane forward: z real-to-complex rows, then y columns ----------------
 template <int NY, int NZ>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_plane_fwd(const float *__restrict__ rho,
-                                                              float2 *__restrict__ A) {
-    constexpr int RZ = FftLen<NZ>::R, MZH = NZ / 2 + 1;
+__global__ void __launch_bounds__(32 * plane_warps<NY, NZ>()) k_fft_plane_fwd(const float *__restrict__ rho,
+                                                                            float2 *__restrict__ A) {
+    using FZ = Fft<NZ>;
+    using FY = Fft<NY>;
+    constexpr int MZH = NZ / 2 + 1, RP = NZ + 8;  // RP: real-plane pitch
+    constexpr int NW = plane_warps<NY, NZ>(), NT = 32 * NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *tile = reinterpret_cast<float2 *>(smem_raw);                    // [NY][MZH]
-    float *real = reinterpret_cast<float *>(smem_raw + tile_bytes<NY>(MZH));  // [NY][NZ]
-    __shared__ float2 twz[NZ / 2];
-    __shared__ float2 twy[NY / 2];
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);                      // [NY][MZH]
+    float *real = reinterpret_cast<float *>(tile + NY * MZH);                  // [NY][RP]
+    float2 *scr_all = reinterpret_cast<float2 *>(real + NY * RP);             // per warp
+    __shared__ float2 twz[NZ];
+    __shared__ float2 twy[NY];
     fill_twiddles<NZ>(twz);
     fill_twiddles<NY>(twy);
     pdl_wait();  // the mesh charge of make_rho is complete
     pdl_trigger();
     const int x = blockIdx.x;
-    const int lane = threadIdx.x & 31;
-    const float4 *plane = reinterpret_cast<const float4 *>(rho + (int64_t)x * NY * NZ);
-    stage<NY * NZ / 4>(reinterpret_cast<float4 *>(real), [&](int e) { return __ldg(plane + e); });
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 *wscr = scr_all + warp * imax<FY::WARP_SCRATCH, FZ::WARP_SCRATCH>();
+    {
+        const float4 *plane = reinterpret_cast<const float4 *>(rho + (int64_t)x * NY * NZ);
+        float4 *r4 = reinterpret_cast<float4 *>(real);
+        stage<NY * NZ / 4, NT>(r4, [&](int e) { return __ldg(plane + e); },
+                           [](int e) { return (e / (NZ / 4)) * (RP / 4) + e % (NZ / 4); });
+    }
     __syncthreads();
-    for (int y = threadIdx.x >> 5; y < NY; y += FFT_WARPS) {
-        const float *row = real + y * NZ;
-        float re[RZ], im[RZ];
+
+    // z: rows 2p and 2p + 1 as the real and imaginary parts of one transform
+    {
+        const int g = lane / FZ::L, j = lane % FZ::L;
+        float2 *scr = wscr + g * FZ::S;
+        for (int p0 = warp * FZ::G; p0 < NY / 2; p0 += NW * FZ::G) {
+            const int p = p0 + g;
+            const bool ok = p < NY / 2;
+            float2 v[FZ::E];
 #pragma unroll
-        for (int r = 0; r < RZ; ++r) {
-            const int i = lane + 32 * r;
-            re[r] = (i < NZ) ? row[bitrev<NZ>(i & (NZ - 1))] : 0.0f;
-            im[r] = 0.0f;
-        }
-        warp_fft<NZ, false>(re, im, twz, lane);
+            for (int a = 0; a < FZ::E; ++a) {
+                const int n = j + FZ::L * a;
+                v[a] = ok ? make_float2(real[(2 * p) * RP + n], real[(2 * p + 1) * RP + n]) : make_float2(0.f, 0.f);
+            }
+            fft_in_out<NZ, false>(v, scr, twz, j);
+            // Z[k] in natural order, then X1 = (Z[k] + conj Z[-k]) / 2, X2 = (Z[k] - conj Z[-k]) / 2i
 #pragma unroll
-        for (int r = 0; r < RZ; ++r) {
-            const int i = lane + 32 * r;
-            if (i < MZH) tile[y * MZH + i] = make_float2(re[r], im[r]);
+            for (int r = 0; r < FZ::E; ++r) scr[out_index<NZ>(j, r)] = v[r];
+            __syncwarp();
+            constexpr int T = (MZH + FZ::L - 1) / FZ::L;
+            float2 x1[T], x2[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const int k = j + FZ::L * t;
+                if (k < MZH) {
+                    const float2 zk = scr[k], zm = scr[(NZ - k) & (NZ - 1)];
+                    x1[t] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+                    x2[t] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+                }
+            }
+            __syncwarp();
+            if (ok) {
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const int k = j + FZ::L * t;
+                    if (k < MZH) {
+                        tile[(2 * p) * MZH + k] = x1[t];
+                        tile[(2 * p + 1) * MZH + k] = x2[t];
+                    }
+                }
+            }
         }
     }
     __syncthreads();
-    tile_columns<NY, false>(tile, MZH, twy);
+
+    // y: every kz column
+    {
+        const int g = lane / FY::L, j = lane % FY::L;
+        float2 *scr = wscr + g * FY::S;
+        for (int c0 = warp * FY::G; c0 < MZH; c0 += NW * FY::G) {
+            const int col = c0 + g;
+            const bool ok = col < MZH;
+            float2 v[FY::E];
+#pragma unroll
+            for (int a = 0; a < FY::E; ++a) v[a] = ok ? tile[(j + FY::L * a) * MZH + col] : make_float2(0.f, 0.f);
+            fft_in_out<NY, false>(v, scr, twy, j);
+            if (ok) {
+#pragma unroll
+                for (int r = 0; r < FY::E; ++r) tile[out_index<NY>(j, r) * MZH + col] = v[r];
+            }
+        }
+    }
     __syncthreads();
     float2 *o = A + (int64_t)x * NY * MZH;
-    for (int e = threadIdx.x; e < NY * MZH; e += FFT_THREADS) o[e] = tile[e];
+    for (int e = threadIdx.x; e < NY * MZH; e += NT) o[e] = tile[e];
 }
 
 // ---- x transform, influence function, energy/virial, x inverse ------------
-// Grid My * ncomp; CTA (ky, a).  A = [NX][My][MZH], S = [ncomp][NX][My][MZH].
+// A group of lanes per (ky, kz) line; CTA (line block lb < nlb, component a),
+// grid nlb * ncomp.  A = [NX][My][MZH], S = [ncomp][NX][My][MZH].
 template <int NX, int MZH, bool IK>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_x_green(int My, const float2 *__restrict__ A,
-                                                            float2 *__restrict__ S, GreenBufs b, EnergyConsts ec,
-                                                            int map_nblk, double *ev_user) {
-    constexpr int NEL = NX * MZH;
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_x_green(int My, int nlb, const float2 *__restrict__ A,
+                                                            float2 *__restrict__ S, GreenBufs b, EnergyConsts ec) {
+    using F = Fft<NX>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *tile = reinterpret_cast<float2 *>(smem_raw);                   // [NX][MZH]
-    float *gpl = reinterpret_cast<float *>(smem_raw + tile_bytes<NX>(MZH));  // [NX][MZH] G / M
-    __shared__ float2 tw[NX / 2];
-    __shared__ float kvx[NX], kdx[NX], kvz[MZH], kdz[MZH];
+    __shared__ float2 tw[NX];
     __shared__ double sh[7][FFT_WARPS];
-    __shared__ int last;
     fill_twiddles<NX>(tw);
-    const int ky = blockIdx.x % My, a = blockIdx.x / My;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / F::L, j = lane % F::L;
+    float2 *scr = reinterpret_cast<float2 *>(smem_raw) + warp * F::WARP_SCRATCH + g * F::S;
+    const int lb = blockIdx.x % nlb, a = blockIdx.x / nlb;
+    const int line = (lb * FFT_WARPS + warp) * F::G + g;
+    const bool ok = line < My * MZH;
+    const int ky = ok ? line / MZH : 0, kz = ok ? line - ky * MZH : 0;
     const float *__restrict__ Gs = reinterpret_cast<const float *>(b.Gs);
     const float *__restrict__ kv = reinterpret_cast<const float *>(b.kvec);
     const float *__restrict__ kd = reinterpret_cast<const float *>(b.kdiff);
-    // plan constants (not written by the step): before the wait
-    for (int t = threadIdx.x; t < NX; t += FFT_THREADS) {
-        kvx[t] = __ldg(kv + t);
-        kdx[t] = __ldg(kd + t);
+    const int64_t total = (int64_t)NX * My * MZH;
+    // plan constants (nothing in the step writes them), loaded before the
+    // wait: G / M and the kx wavenumbers (energy) or derivative factors of
+    // this lane's out-layout points
+    float Gk[F::E], kx[F::E];
+#pragma unroll
+    for (int r = 0; r < F::E; ++r) {
+        const int k = out_index<NX>(j, r);
+        Gk[r] = ok ? __ldg(Gs + ((int64_t)k * My + ky) * MZH + kz) : 0.0f;
+        kx[r] = (a == 0) ? __ldg(kv + k) : 0.0f;
     }
-    for (int t = threadIdx.x; t < MZH; t += FFT_THREADS) {
-        kvz[t] = __ldg(kv + NX + My + t);
-        kdz[t] = __ldg(kd + NX + My + t);
+    const float kyv = __ldg(kv + NX + ky), kzv = __ldg(kv + NX + My + kz);
+    const float dky = __ldg(kd + NX + ky), dkz = __ldg(kd + NX + My + kz);
+    float dkx[F::E];
+    if (IK && a == 0) {
+#pragma unroll
+        for (int r = 0; r < F::E; ++r) dkx[r] = __ldg(kd + out_index<NX>(j, r));
     }
-    const float kyv = __ldg(kv + NX + ky), dky = __ldg(kd + NX + ky);
-    stage<NEL>(gpl, [&](int e) {
-        const int x = e / MZH, kz = e - x * MZH;
-        return __ldg(Gs + ((int64_t)x * My + ky) * MZH + kz);
-    });
+    __syncthreads();  // twiddles
     pdl_wait();
     pdl_trigger();
-    const int64_t total = (int64_t)NX * My * MZH;
-    stage<NEL>(tile, [&](int e) {
-        const int x = e / MZH, kz = e - x * MZH;
-        return A[((int64_t)x * My + ky) * MZH + kz];
-    });
-    __syncthreads();
-    tile_columns<NX, false>(tile, MZH, tw);
-    __syncthreads();
+    float2 v[F::E];
+#pragma unroll
+    for (int q = 0; q < F::E; ++q)
+        v[q] = ok ? A[((int64_t)(j + F::L * q) * My + ky) * MZH + kz] : make_float2(0.f, 0.f);
+    fft_in_out<NX, false>(v, scr, tw, j);
 
     if (a == 0) {
-        // the energy/virial sums of k_green over this ky plane (Mz is even:
-        // kz = 0 and kz = Mz/2 count once, the others twice)
+        // the energy/virial sums of k_green (Mz is even: kz = 0 and kz = Mz/2
+        // count once, the others twice)
         const float i4g2 = (float)ec.inv4g2;
+        const float w = (kz == 0 || kz == MZH - 1) ? 1.0f : 2.0f;
         float acc[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int e = threadIdx.x; e < NEL; e += FFT_THREADS) {
-            const int kx = e / MZH, kz = e - kx * MZH;
-            const float2 r = tile[e];
-            const float G = gpl[e];
-            const float w = (kz == 0 || kz == MZH - 1) ? 1.0f : 2.0f;
-            const float s = w * G * (r.x * r.x + r.y * r.y);
-            const float kxv = kvx[kx], kzv = kvz[kz];
+#pragma unroll
+        for (int r = 0; r < F::E; ++r) {
+            const float s = w * Gk[r] * (v[r].x * v[r].x + v[r].y * v[r].y);
+            const float kxv = kx[r];
             const float k2 = kxv * kxv + kyv * kyv + kzv * kzv;
             const float fac = (k2 > 0.0f) ? 2.0f * (1.0f + k2 * i4g2) / k2 : 0.0f;
             const float sf = s * fac;
@@ -270,117 +403,123 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_green(int My, const float
         }
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
-            const float v = warp_sum_t<float>(acc[c]);
-            if (lane == 0) sh[c][warp] = (double)v;
+            const float t = warp_sum_t<float>(acc[c]);
+            if (lane == 0) sh[c][warp] = (double)t;
         }
         __syncthreads();
         if (threadIdx.x < 7) {
-            double v = 0.0;
-            for (int w2 = 0; w2 < FFT_WARPS; ++w2) v += sh[threadIdx.x][w2];
-            b.part[7 * ky + threadIdx.x] = v;
-            __threadfence();
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) last = (atomicAdd(b.counter, 1u) == (unsigned)(My - 1)) ? 1 : 0;
-        __syncthreads();
-        if (last) {  // every ky plane's partials are written: the final sums, fixed order
-            __threadfence();
-            energy_final_body(b, ec, My, map_nblk, ev_user);
-            if (threadIdx.x == 0) *b.counter = 0u;
+            double t = 0.0;
+            for (int w2 = 0; w2 < FFT_WARPS; ++w2) t += sh[threadIdx.x][w2];
+            b.part[7 * lb + threadIdx.x] = t;
         }
     }
 
-    // multiply and inverse, column by column in place (each warp owns its
-    // columns; the energy pass above read the tile before its barrier)
-    {
-        constexpr int R = FftLen<NX>::R;
-        for (int col = warp; col < MZH; col += FFT_WARPS) {
-            const float dkz = kdz[col];
-            float re[R], im[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int i = lane + 32 * r;
-                const int kx = bitrev<NX>(i & (NX - 1));
-                float vr = 0.f, vi = 0.f;
-                if (i < NX) {
-                    const float2 v = tile[kx * MZH + col];
-                    const float G = gpl[kx * MZH + col];
-                    const float pr = G * v.x, pi = G * v.y;
-                    if (IK) {
-                        // E_a = -i k_a G rho_hat / M  ->  (k_a pi, -k_a pr), Nyquist zeroed
-                        const float dk = (a == 0) ? kdx[kx] : ((a == 1) ? dky : dkz);
-                        vr = dk * pi;
-                        vi = -dk * pr;
-                    } else {
-                        vr = pr;
-                        vi = pi;
-                    }
-                }
-                re[r] = vr;
-                im[r] = vi;
-            }
-            __syncwarp();
-            warp_fft<NX, true>(re, im, tw, lane);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int i = lane + 32 * r;
-                if (i < NX) tile[i * MZH + col] = make_float2(re[r], im[r]);
-            }
+    for (int r = 0; r < F::E; ++r) {
+        const float pr = Gk[r] * v[r].x, pi = Gk[r] * v[r].y;
+        if (IK) {
+            // E_a = -i k_a G rho_hat / M  ->  (k_a pi, -k_a pr), Nyquist zeroed
+            const float dk = (a == 0) ? dkx[r] : ((a == 1) ? dky : dkz);
+            v[r] = make_float2(dk * pi, -dk * pr);
+        } else {
+            v[r] = make_float2(pr, pi);
         }
     }
-    __syncthreads();
-    float2 *o = S + a * total;
-    for (int e = threadIdx.x; e < NEL; e += FFT_THREADS) {
-        const int x = e / MZH, kz = e - x * MZH;
-        o[((int64_t)x * My + ky) * MZH + kz] = tile[e];
+    fft_out_in<NX, true>(v, scr, tw, j);
+    if (ok) {
+        float2 *o = S + a * total;
+#pragma unroll
+        for (int q = 0; q < F::E; ++q) o[((int64_t)(j + F::L * q) * My + ky) * MZH + kz] = v[q];
     }
 }
 
-// ---- plane inverse: y columns, then z complex-to-real rows -----------------
+// ---- plane inverse: y columns, then z complex-to-real row pairs ------------
 // Grid Mx * ncomp; CTA (x, a).  Output: out[((x NY + y) NZ + z) * stride + a].
 template <int NY, int NZ>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_plane_inv(const float2 *__restrict__ S, float *__restrict__ out,
-                                                              int Mx, int64_t comp_stride, int stride) {
-    constexpr int RZ = FftLen<NZ>::R, MZH = NZ / 2 + 1;
+__global__ void __launch_bounds__(32 * plane_warps<NY, NZ>()) k_fft_plane_inv(const float2 *__restrict__ S,
+                                                                            float *__restrict__ out, int Mx,
+                                                                            int64_t comp_stride, int stride) {
+    using FZ = Fft<NZ>;
+    using FY = Fft<NY>;
+    constexpr int MZH = NZ / 2 + 1;
+    constexpr int NW = plane_warps<NY, NZ>(), NT = 32 * NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);  // [NY][MZH]
-    __shared__ float2 twz[NZ / 2];
-    __shared__ float2 twy[NY / 2];
+    float2 *scr_all = tile + NY * MZH;
+    __shared__ float2 twz[NZ];
+    __shared__ float2 twy[NY];
     fill_twiddles<NZ>(twz);
     fill_twiddles<NY>(twy);
     pdl_wait();
     pdl_trigger();
     const int x = blockIdx.x % Mx, a = blockIdx.x / Mx;
-    const int lane = threadIdx.x & 31;
-    const float2 *g = S + a * comp_stride + (int64_t)x * NY * MZH;
-    stage<NY * MZH>(tile, [&](int e) { return g[e]; });
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 *wscr = scr_all + warp * imax<FY::WARP_SCRATCH, FZ::WARP_SCRATCH>();
+    {
+        const float2 *g = S + a * comp_stride + (int64_t)x * NY * MZH;
+        stage<NY * MZH, NT>(tile, [&](int e) { return g[e]; }, [](int e) { return e; });
+    }
     __syncthreads();
-    tile_columns<NY, true>(tile, MZH, twy);
-    __syncthreads();
-    float *plane = out + (int64_t)x * NY * NZ * stride + a;
-    for (int y = threadIdx.x >> 5; y < NY; y += FFT_WARPS) {
-        float re[RZ], im[RZ];
+
+    // y inverse: every kz column (out layout in, in layout out)
+    {
+        const int g = lane / FY::L, j = lane % FY::L;
+        float2 *scr = wscr + g * FY::S;
+        for (int c0 = warp * FY::G; c0 < MZH; c0 += NW * FY::G) {
+            const int col = c0 + g;
+            const bool ok = col < MZH;
+            float2 v[FY::E];
 #pragma unroll
-        for (int r = 0; r < RZ; ++r) {
-            const int i = lane + 32 * r;
-            const int k = bitrev<NZ>(i & (NZ - 1));
-            float2 v = make_float2(0.f, 0.f);
-            if (i < NZ) {  // the Hermitian extension of the half spectrum
-                if (k < MZH) {
-                    v = tile[y * MZH + k];
-                } else {
-                    v = tile[y * MZH + (NZ - k)];
-                    v.y = -v.y;
+            for (int r = 0; r < FY::E; ++r)
+                v[r] = ok ? tile[out_index<NY>(j, r) * MZH + col] : make_float2(0.f, 0.f);
+            fft_out_in<NY, true>(v, scr, twy, j);
+            if (ok) {
+#pragma unroll
+                for (int q = 0; q < FY::E; ++q) tile[(j + FY::L * q) * MZH + col] = v[q];
+            }
+        }
+    }
+    __syncthreads();
+
+    // z: rows 2p, 2p + 1 from one inverse of Z = X1 + i X2 (both Hermitian-
+    // extended; the imaginary parts of the k = 0 and k = Mz/2 terms, which a
+    // real row cannot carry, are dropped)
+    {
+        const int g = lane / FZ::L, j = lane % FZ::L;
+        float2 *scr = wscr + g * FZ::S;
+        float *plane = out + (int64_t)x * NY * NZ * stride + a;
+        for (int p0 = warp * FZ::G; p0 < NY / 2; p0 += NW * FZ::G) {
+            const int p = p0 + g;
+            const bool ok = p < NY / 2;
+            float2 v[FZ::E];
+#pragma unroll
+            for (int r = 0; r < FZ::E; ++r) {
+                const int k = out_index<NZ>(j, r);
+                float2 x1 = make_float2(0.f, 0.f), x2 = make_float2(0.f, 0.f);
+                if (ok) {
+                    const int kk = (k < MZH) ? k : NZ - k;
+                    x1 = tile[(2 * p) * MZH + kk];
+                    x2 = tile[(2 * p + 1) * MZH + kk];
+                    if (k >= MZH) {
+                        x1.y = -x1.y;
+                        x2.y = -x2.y;
+                    }
+                    if (k == 0 || k == NZ / 2) {
+                        x1.y = 0.f;
+                        x2.y = 0.f;
+                    }
+                }
+                v[r] = make_float2(x1.x - x2.y, x1.y + x2.x);
+            }
+            fft_out_in<NZ, true>(v, scr, twz, j);
+            if (ok) {
+#pragma unroll
+                for (int q = 0; q < FZ::E; ++q) {
+                    const int n = j + FZ::L * q;
+                    plane[(int64_t)((2 * p) * NZ + n) * stride] = v[q].x;
+                    plane[(int64_t)((2 * p + 1) * NZ + n) * stride] = v[q].y;
                 }
             }
-            re[r] = v.x;
-            im[r] = v.y;
-        }
-        warp_fft<NZ, true>(re, im, twz, lane);
-#pragma unroll
-        for (int r = 0; r < RZ; ++r) {
-            const int i = lane + 32 * r;
-            if (i < NZ) plane[(int64_t)(y * NZ + i) * stride] = re[r];
         }
     }
 }
@@ -397,14 +536,15 @@ bool custom_fft_supported(const int M[3]) {
 namespace {
 
 template <typename... KArgs, typename... Args>
-void launch_k(void (*kernel)(KArgs...), bool pdl, int grid, size_t smem, cudaStream_t s, Args... args) {
+void launch_k(void (*kernel)(KArgs...), bool pdl, int grid, int threads, size_t smem, cudaStream_t s,
+              Args... args) {
     if (pdl)
-        launch_pdl(kernel, dim3(grid), dim3(FFT_THREADS), smem, s, args...);
+        launch_pdl(kernel, dim3(grid), dim3(threads), smem, s, args...);
     else
-        kernel<<<grid, FFT_THREADS, smem, s>>>(args...);
+        kernel<<<grid, threads, smem, s>>>(args...);
 }
 
-// Calls fn.template operator()<N>() for N = n in {16, 32, 64, 128}.
+// fn(std::integral_constant<int, n>) for n in {16, 32, 64, 128}
 template <typename F>
 void pow2_dispatch(int n, F &&fn) {
     switch (n) {
@@ -413,6 +553,12 @@ void pow2_dispatch(int n, F &&fn) {
         case 64: fn(std::integral_constant<int, 64>{}); break;
         default: fn(std::integral_constant<int, 128>{}); break;
     }
+}
+
+template <int NX>
+int x_line_blocks(int My, int mzh) {
+    const int lines_per_cta = FFT_WARPS * Fft<NX>::G;
+    return (My * mzh + lines_per_cta - 1) / lines_per_cta;
 }
 
 }  // namespace
@@ -428,13 +574,13 @@ cudaError_t prepare_custom_fft(const int M[3]) {
                                          (int)plane_fwd_smem<NY, NZ>());
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_fft_plane_inv<NY, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tile_bytes<NY>(NZ / 2 + 1));
+                                         (int)plane_inv_smem<NY, NZ>());
         });
     });
     pow2_dispatch(M[0], [&](auto nx) {
         pow2_dispatch(M[2], [&](auto nz) {
             constexpr int NX = decltype(nx)::value, MZH = decltype(nz)::value / 2 + 1;
-            const int sm = (int)x_green_smem<NX, MZH>();
+            const int sm = (int)x_green_smem<NX>();
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_fft_x_green<NX, MZH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          sm);
@@ -446,43 +592,47 @@ cudaError_t prepare_custom_fft(const int M[3]) {
     return e;
 }
 
-void launch_custom_fft(int step, const Geom<float> &g, bool ik_spec, const float *rho, void *rho_hat, void *spec,
-                       float *field, const GreenBufs &b, const EnergyConsts &ec, int map_nblk, double *ev_user,
-                       bool pdl, cudaStream_t s) {
+int launch_custom_fft(int step, const Geom<float> &g, bool ik_spec, const float *rho, void *rho_hat, void *spec,
+                      float *field, const GreenBufs &b, const EnergyConsts &ec, bool pdl, cudaStream_t s) {
     float2 *A = reinterpret_cast<float2 *>(rho_hat);
     float2 *S = reinterpret_cast<float2 *>(spec);
     const int Mx = g.M[0], My = g.M[1];
     const int ncomp = ik_spec ? 3 : 1;
     const int64_t total = (int64_t)Mx * My * (g.M[2] / 2 + 1);
+    int nparts = 0;
     if (step == 0) {
         pow2_dispatch(My, [&](auto ny) {
             pow2_dispatch(g.M[2], [&](auto nz) {
                 constexpr int NY = decltype(ny)::value, NZ = decltype(nz)::value;
-                launch_k(k_fft_plane_fwd<NY, NZ>, pdl, Mx, plane_fwd_smem<NY, NZ>(), s, rho, A);
+                launch_k(k_fft_plane_fwd<NY, NZ>, pdl, Mx, 32 * plane_warps<NY, NZ>(), plane_fwd_smem<NY, NZ>(), s,
+                         rho, A);
             });
         });
     } else if (step == 1) {
         pow2_dispatch(Mx, [&](auto nx) {
             pow2_dispatch(g.M[2], [&](auto nz) {
                 constexpr int NX = decltype(nx)::value, MZH = decltype(nz)::value / 2 + 1;
-                const size_t sm = x_green_smem<NX, MZH>();
+                const int nlb = x_line_blocks<NX>(My, MZH);
+                const size_t sm = x_green_smem<NX>();
                 if (ik_spec)
-                    launch_k(k_fft_x_green<NX, MZH, true>, pdl, My * ncomp, sm, s, My, (const float2 *)A, S, b,
-                             ec, map_nblk, ev_user);
+                    launch_k(k_fft_x_green<NX, MZH, true>, pdl, nlb * ncomp, FFT_THREADS, sm, s, My, nlb,
+                             (const float2 *)A, S, b, ec);
                 else
-                    launch_k(k_fft_x_green<NX, MZH, false>, pdl, My * ncomp, sm, s, My, (const float2 *)A, S, b,
-                             ec, map_nblk, ev_user);
+                    launch_k(k_fft_x_green<NX, MZH, false>, pdl, nlb * ncomp, FFT_THREADS, sm, s, My, nlb,
+                             (const float2 *)A, S, b, ec);
+                nparts = nlb;
             });
         });
     } else {
         pow2_dispatch(My, [&](auto ny) {
             pow2_dispatch(g.M[2], [&](auto nz) {
                 constexpr int NY = decltype(ny)::value, NZ = decltype(nz)::value;
-                launch_k(k_fft_plane_inv<NY, NZ>, pdl, Mx * ncomp, tile_bytes<NY>(NZ / 2 + 1), s,
-                         (const float2 *)S, field, Mx, total, ncomp == 3 ? 4 : 1);
+                launch_k(k_fft_plane_inv<NY, NZ>, pdl, Mx * ncomp, 32 * plane_warps<NY, NZ>(),
+                         plane_inv_smem<NY, NZ>(), s, (const float2 *)S, field, Mx, total, ncomp == 3 ? 4 : 1);
             });
         });
     }
+    return nparts;
 }
 
 }  // namespace pppm

@@ -365,18 +365,31 @@ int enqueue_t(pppm_plan *p, const Geom<R> &gp, int64_t n, const void *x, const v
     const int mn = (int)((n + 255) / 256);
     if constexpr (std::is_same<R, float>::value) {
         if (p->variants & 8) {
-            // forward plane pass | x pass with G, energy and its final sum | inverse plane pass
+            // forward plane pass | x pass with G and the energy partials | inverse plane pass
             mark(2);
             launch_custom_fft(0, g, ik_spec, (const float *)p->rho, p->rho_hat, p->spec, (float *)p->field, p->gb,
-                              p->ec, mn, ev, !need_mark(2) && !chk, s);
+                              p->ec, !need_mark(2) && !chk, s);
             if ((rc = check("forward FFT"))) return rc;
             mark(3);
-            launch_custom_fft(1, g, ik_spec, (const float *)p->rho, p->rho_hat, p->spec, (float *)p->field, p->gb,
-                              p->ec, mn, ev, !need_mark(3) && !chk, s);
+            const int gn = launch_custom_fft(1, g, ik_spec, (const float *)p->rho, p->rho_hat, p->spec,
+                                             (float *)p->field, p->gb, p->ec, !need_mark(3) && !chk, s);
             if ((rc = check("green"))) return rc;
             mark(4);
+            bool pdl_inv = !need_mark(4) && !chk;
+            if (kind == 0) {
+                // the final energy/virial sum runs beside the inverse pass and fieldforce
+                CK(cudaEventRecord(p->fork, s));
+                CK(cudaStreamWaitEvent(p->side, p->fork, 0));
+                launch_energy_final(p->gb, p->ec, gn, mn, ev, p->side);
+                CK(cudaEventRecord(p->join, p->side));
+                pdl_inv = false;  // an event record sits between the x pass and the inverse pass
+            } else {
+                launch_energy_final(p->gb, p->ec, gn, mn, ev, s);  // dE/dq needs sum q first
+                pdl_inv = false;
+            }
+            if ((rc = check("energy_final"))) return rc;
             launch_custom_fft(2, g, ik_spec, (const float *)p->rho, p->rho_hat, p->spec, (float *)p->field, p->gb,
-                              p->ec, mn, ev, !need_mark(4) && !chk, s);
+                              p->ec, pdl_inv, s);
             if ((rc = check("inverse FFT"))) return rc;
             mark(5);
             if (kind == 0) {
@@ -389,6 +402,7 @@ int enqueue_t(pppm_plan *p, const Geom<R> &gp, int64_t n, const void *x, const v
             }
             if ((rc = check("fieldforce"))) return rc;
             mark(6);
+            if (kind == 0) CK(cudaStreamWaitEvent(s, p->join, 0));
             p->prof_valid = pmask;
             CK(cudaGetLastError());
             return PPPM_OK;

@@ -241,7 +241,7 @@ struct GreenBufs {
     const void *kvec;      // [Mx + My + Mzh] wavenumbers (step type), Nyquist negative
     const void *kdiff;     // same with the Nyquist entries zeroed (ik differentiation)
     double *part;          // [7 * nblk] per-block partial energy/virial
-    unsigned int *counter; // [1] last-CTA ticket of the fused FFT x pass (zero between steps)
+    unsigned int *counter; // [1] unused
     double *qsum;          // [2] sum q, sum q^2 (written by k_energy_final)
     const double *map_part;// [2 * map_nblk] per-block sum q, sum q^2 of k_particle_map
     double *ev;            // [8] energy + virial
@@ -261,11 +261,23 @@ __device__ __forceinline__ void energy_final_body(const GreenBufs &b, const Ener
     __shared__ double qs[2];
     __shared__ double comp[7];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // each lane adds its entries k = lane, lane + 32, ... in order, loading
+    // eight of them before adding (one memory round trip per eight)
     if (w == 7) {
         double a = 0.0, c = 0.0;
-        for (int k = lane; k < mn; k += 32) {
-            a += b.map_part[2 * k];
-            c += b.map_part[2 * k + 1];
+        for (int k0 = lane; k0 < mn; k0 += 256) {
+            double va[8], vc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + 32 * u;
+                va[u] = (k < mn) ? b.map_part[2 * k] : 0.0;
+                vc[u] = (k < mn) ? b.map_part[2 * k + 1] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                a += va[u];
+                c += vc[u];
+            }
         }
         a = warp_sum(a);
         c = warp_sum(c);
@@ -277,7 +289,13 @@ __device__ __forceinline__ void energy_final_body(const GreenBufs &b, const Ener
         }
     } else {
         double v = 0.0;
-        for (int k = lane; k < gn; k += 32) v += b.part[7 * k + w];
+        for (int k0 = lane; k0 < gn; k0 += 256) {
+            double vv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) vv[u] = (k0 + 32 * u < gn) ? b.part[7 * (k0 + 32 * u) + w] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v += vv[u];
+        }
         v = warp_sum(v);
         if (lane == 0) comp[w] = v * ec.epref;
     }
@@ -301,15 +319,14 @@ void launch_energy_final(const GreenBufs &b, const EnergyConsts &ec, int green_n
 
 // Hand-written Poisson solve for FP32 plans with power-of-two mesh edges
 // 16..128 (k_fft.cu): step 0 forward plane pass (rho -> rho_hat), step 1 x
-// pass with the influence function, the energy/virial partials and their
-// final sum into b.ev / ev_user (replaces launch_green + launch_energy_final),
+// pass with the influence function and the energy/virial partials (in place
+// of launch_green; returns the number of partials, for launch_energy_final),
 // step 2 inverse plane pass (spec -> field).  pdl: the launch directly
 // follows its stream predecessor kernel.
 bool custom_fft_supported(const int M[3]);
 cudaError_t prepare_custom_fft(const int M[3]);  // shared-memory opt-in, before capture
-void launch_custom_fft(int step, const Geom<float> &g, bool ik_spec, const float *rho, void *rho_hat, void *spec,
-                       float *field, const GreenBufs &b, const EnergyConsts &ec, int map_nblk, double *ev_user,
-                       bool pdl, cudaStream_t s);
+int launch_custom_fft(int step, const Geom<float> &g, bool ik_spec, const float *rho, void *rho_hat, void *spec,
+                      float *field, const GreenBufs &b, const EnergyConsts &ec, bool pdl, cudaStream_t s);
 
 template <typename R>
 cudaError_t prepare_fieldforce(int P);  // shared-memory opt-in of the tile-staged kernels

@@ -150,8 +150,8 @@ def test_energy_grad_and_potential(torch, mode):
 
 
 def test_repeated_steps_graph_and_profiling(torch):
-    """The x pass's last-CTA ticket resets every step: changing charges change
-    the energy on every call, eagerly, inside a graph and with stage events."""
+    """The energy follows the charges on every call (no stale partials or
+    sums), eagerly, inside a graph and with stage events."""
     from paper_1702_04250_gb300 import pppm
 
     mesh, box = (64, 64, 64), (40.0, 40.0, 40.0)
