@@ -125,9 +125,10 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def known_traffic(stage, workload_name):
-    """DRAM bytes per launch from profiles/dram_traffic.txt, or None when the
-    kernel's sources changed since that capture (the line stores their hash)."""
+def known_traffic(stage, workload_name, source):
+    """DRAM bytes per launch from profiles/dram_traffic.txt for this stage as
+    implemented in `source`, or None when no capture of it exists or the
+    kernel's sources changed since (the line stores their hash)."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
@@ -139,7 +140,7 @@ def known_traffic(stage, workload_name):
         if ln.startswith("#") or not ln.strip():
             continue
         st, wl, src, sha, nbytes = ln.split()
-        if st == stage and wl == workload_name:
+        if st == stage and wl == workload_name and src == source:
             m = hashlib.sha1()
             for f in (src, "paper_1702_04250_gb300/csrc/pppm_common.cuh"):
                 m.update(open(os.path.join(ROOT, f), "rb").read())
@@ -270,7 +271,8 @@ def gpu_arm(args, rank, world):
     clocks.start()
     # which of our kernels dominates (all stage events on, short untimed pass)
     _, disc = time_steps(torch, plan, x32, q32, f, ev, 20, 3, flush, profile=True)
-    own = {k: disc[k] for k in ("sort", "make_rho", "green", "fieldforce")}
+    own_fft = bool(variant & 8)  # the hand-written Poisson solve (else cuFFT + k_green)
+    own = {k: disc[k] for k in ("sort", "make_rho", "green", "fieldforce") + (("fft_fwd", "fft_inv") if own_fft else ())}
     dom = max(own, key=own.get)
 
     # the timed region: K steps; every 10th carries events around the dominant kernel
@@ -292,16 +294,22 @@ def gpu_arm(args, rank, world):
     stage_ms = dict(disc)        # all stages, discovery pass (events inflate each)
     stage_ms[dom] = stages[dom]  # the dominant kernel, timed region (every 10th step)
     N, M = w.n, int(np.prod(w.mesh))
+    MH = (M // w.mesh[2]) * (w.mesh[2] // 2 + 1)  # half spectrum
     alg_bytes = {
         "sort": (12 + 4) * N * 2 + (16 + 4 + 4 + 4 + 4) * N,   # x,q read twice; record, anchor, perm, rank writes
         "make_rho": (16 + 4) * N + 4 * M,                        # sorted records + anchors in, mesh out once
-        "green": (8 * (M // w.mesh[2]) * (w.mesh[2] // 2 + 1)) * (1 + 3) + 4 * (M // w.mesh[2]) * (w.mesh[2] // 2 + 1),
+        "green": 8 * MH * (1 + 3) + 4 * MH,                      # rho_hat in, three spectra out, G in
+        "fft_fwd": 4 * M + 8 * MH,                               # mesh in, rho_hat out
+        "fft_inv": 8 * MH * 3 + 12 * M,                          # three spectra in, three field components out
         "fieldforce": 16 * M + (16 + 4 + 4 + 12) * N,            # float4 field once, records, anchors, perm, forces
     }[dom]
+    source = {"sort": "k_sort.cu", "make_rho": "k_rho.cu", "fieldforce": "k_force.cu", "fft_fwd": "k_fft.cu",
+              "fft_inv": "k_fft.cu", "green": "k_fft.cu" if own_fft else "k_green.cu"}[dom]
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (stage_ms[dom] * 1e-3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": known_traffic(dom, WORKLOAD), "peak_source": peak_kind,
+            "frac": round(achieved / peak, 4), "traffic": known_traffic(dom, WORKLOAD, "paper_1702_04250_gb300/csrc/" + source),
+            "peak_source": peak_kind,
             "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(stage_ms[dom], 5),
             "launches_timed": f"every {PROFILE_EVERY}th timed step carries events around this kernel",
             "stage_ms": {k: round(v, 5) for k, v in stage_ms.items()}}
@@ -328,14 +336,16 @@ def gpu_arm(args, rank, world):
         variants[f"{mode}_{prec}"] = {"steps_per_s": round(1000.0 / (tv / max(20, args.steps // 4)), 1)}
         pv.close()
 
-    # particle_map, scatter, make_rho, green, energy_final, fieldforce (cuFFT and the memset are not ours)
-    launches_per_step = 6
+    # particle_map, scatter, make_rho, energy_final, fieldforce, and either green (the 3-D
+    # transforms in cuFFT, not ours) or the three hand-written Poisson-solve kernels
+    launches_per_step = 8 if own_fft else 6
     line = {
         "metric": metric_name(), "value": round(steps_per_s, 2), "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32c", "data": "synthetic",
         "config": config_dict(w, {"parallelism": "replicas" if world > 1 else "single",
-                                  "fieldforce_variant": "tile-staged" if variant & 1 else "per-particle L1"}),
+                                  "fieldforce_variant": "tile-staged" if variant & 1 else "per-particle L1",
+                                  "poisson_solve": "hand-written FFT" if own_fft else "cuFFT"}),
         "mparticles_per_s": round(world * N / (ms_per_step * 1e-3) / 1e6, 2),
         "rel_force_err_vs_fp64": rel_err, "rel_energy_err_vs_fp64": e_err,
         "ms_per_step_without_kernel_events": round(ms_plain, 5),

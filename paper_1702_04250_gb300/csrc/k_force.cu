@@ -9,12 +9,12 @@
 //      factor each), then per-particle work after the loop: scaling and the
 //      self-force correction (the paper's "split atom" epilogue, fused here).
 //
-// Layout: 8 lanes per particle, lane k owning stencil offset k along z (lanes
-// k >= P idle: the zero-padded "simd8" inner loop).  Each lane sums its z
-// column separably -- first over y into per-x partials, then over x -- so the
-// ad gather costs two FMAs per stencil point; the eight lane partials are
-// combined with warp shuffles and the force is written to the particle's
-// input position.
+// Layout: P lanes per particle (32 / P particles per warp), lane k owning
+// stencil offset k along z -- no lane spent on the paper's zero padding of the
+// inner loop to 8 ("simd8").  Each lane sums its z column separably -- first
+// over y into per-x partials, then over x -- so the ad gather costs two FMAs
+// per stencil point; the P lane partials are combined with warp shuffles and
+// the force is written to the particle's input position.
 //
 // Two variants (chosen per plan, see pppm_autotune):
 //  k_fieldforce        particles in tile order, field rows read through L1.
@@ -31,7 +31,6 @@
 namespace pppm {
 
 constexpr int FF_THREADS = 256;
-constexpr int FGROUP = 8;
 
 __device__ __forceinline__ float ldf(const float *p) { return __ldg(p); }
 __device__ __forceinline__ double ldf(const double *p) { return __ldg(p); }
@@ -59,8 +58,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Per-particle weights shared inside an 8-lane group: lane t < P evaluates
-// stencil offset t, every lane receives the x and y sets.
 template <typename R, int P>
 __device__ __forceinline__ R horner_r(const R (&c)[P], R d) {
     R w = c[P - 1];
@@ -82,8 +79,9 @@ struct LaneCoef {
     }
 };
 
-// Per-particle weights shared inside an 8-lane group: lane t < P evaluates
-// stencil offset t, every lane receives the x and y sets.
+// Per-particle weights shared inside a group of P lanes (32 / P groups per
+// warp; the lanes past the last whole group idle): lane t evaluates stencil
+// offset t, every lane receives the x and y sets.
 template <typename R, int P, int MODE>
 struct GroupWeights {
     R wx[P], wy[P], wdx[P], wdy[P];
@@ -122,11 +120,13 @@ struct GroupWeights {
     __device__ __forceinline__ void share(int gbase, R wxl, R wyl, R dxl, R dyl) {
 #pragma unroll
         for (int t = 0; t < P; ++t) {
-            wx[t] = __shfl_sync(0xffffffffu, wxl, gbase + t);
-            wy[t] = __shfl_sync(0xffffffffu, wyl, gbase + t);
+            // an idle lane's source wraps within the warp; it is not used
+            const int src = (gbase + t) & 31;
+            wx[t] = __shfl_sync(0xffffffffu, wxl, src);
+            wy[t] = __shfl_sync(0xffffffffu, wyl, src);
             if (MODE != 0) {
-                wdx[t] = __shfl_sync(0xffffffffu, dxl, gbase + t);
-                wdy[t] = __shfl_sync(0xffffffffu, dyl, gbase + t);
+                wdx[t] = __shfl_sync(0xffffffffu, dxl, src);
+                wdy[t] = __shfl_sync(0xffffffffu, dyl, src);
             }
         }
     }
@@ -169,7 +169,8 @@ __device__ __forceinline__ void gather_column(const GroupWeights<R, P, MODE> &w,
     }
 }
 
-// Combine the 8 lanes, finish the per-particle epilogue and store.
+// Combine the group's P lanes into its lane 0, finish the per-particle
+// epilogue and store.
 template <typename R, int P, int MODE>
 __device__ __forceinline__ void finish_particle(const Geom<R> &g, const SortBufs &b, bool live, int k, int j,
                                                 const GroupWeights<R, P, MODE> &w, R e0, R e1, R e2, R dx, R dy,
@@ -183,12 +184,22 @@ __device__ __forceinline__ void finish_particle(const Geom<R> &g, const SortBufs
         e3 = e2 * w.wz;  // potential at the particle (MODE 2)
         e2 *= w.dwz;
     }
+    // tree over offsets 4, 2, 1: lane k adds lane k + o while that lane is in
+    // its group (k + o < P); lane 0 ends with the sum of all P (P <= 8)
 #pragma unroll
-    for (int o = FGROUP / 2; o > 0; o >>= 1) {
-        e0 += __shfl_xor_sync(0xffffffffu, e0, o);
-        e1 += __shfl_xor_sync(0xffffffffu, e1, o);
-        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-        if (MODE == 2) e3 += __shfl_xor_sync(0xffffffffu, e3, o);
+    for (int o = 4; o > 0; o >>= 1) {
+        if (o >= P) continue;
+        const R v0 = __shfl_down_sync(0xffffffffu, e0, o);
+        const R v1 = __shfl_down_sync(0xffffffffu, e1, o);
+        const R v2 = __shfl_down_sync(0xffffffffu, e2, o);
+        R v3 = R(0);
+        if (MODE == 2) v3 = __shfl_down_sync(0xffffffffu, e3, o);
+        if (k + o < P) {
+            e0 += v0;
+            e1 += v1;
+            e2 += v2;
+            if (MODE == 2) e3 += v3;
+        }
     }
     if (!live || k != 0) return;
     const int dst = b.perm[j];
@@ -238,13 +249,15 @@ __device__ __forceinline__ void fieldforce_body(const Geom<R> &g, const SortBufs
                                                 const R *__restrict__ field, R *__restrict__ f,
                                                 R *__restrict__ dq, R qC, const double *c, R gself, R gbg,
                                                 int lb) {
+    constexpr int NG = 32 / P;  // particles per warp
     const int lane = threadIdx.x & 31;
-    const int k = lane & (FGROUP - 1);
-    const int gbase = lane & ~(FGROUP - 1);
-    const int64_t gid = (lb * (int64_t)blockDim.x + threadIdx.x) / FGROUP;
-    const int64_t warp_first = (lb * (int64_t)blockDim.x + (threadIdx.x & ~31)) / FGROUP;
+    const int k = lane % P;
+    const int gbase = lane - k;
+    const int64_t gwarp = (lb * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t gid = gwarp * NG + lane / P;
+    const int64_t warp_first = gwarp * NG;
     if (warp_first >= n) return;  // whole warp idle
-    const bool live = gid < n;
+    const bool live = lane < NG * P && gid < n;
     const int j = live ? (int)gid : 0;
 
     const vec4_t<R> r = reinterpret_cast<const vec4_t<R> *>(b.rec)[j];
@@ -257,7 +270,7 @@ __device__ __forceinline__ void fieldforce_body(const Geom<R> &g, const SortBufs
     w.build(g, k, gbase, r.x, r.y, r.z);
     pdl_wait();  // weights come from the sort's records; the field from the inverse transform
     R e0 = 0, e1 = 0, e2 = 0;
-    if (live && inmesh && k < P) {
+    if (live && inmesh) {
         const int My = g.M[1], Mz = g.M[2];
         const int iz = wrap1(az - g.rlo + k, Mz);
         int yoff[P], xoff[P];
@@ -350,16 +363,18 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, Sort
     }
     __syncthreads();
 
+    constexpr int NG = 32 / P;  // particles per warp
     const int lane = threadIdx.x & 31;
-    const int k = lane & (FGROUP - 1);
-    const int gbase = lane & ~(FGROUP - 1);
-    const int grp = threadIdx.x / FGROUP;
-    const int ngrp = FF_THREADS / FGROUP;
+    const int k = lane % P;
+    const int gbase = lane - k;
+    const int grp = (threadIdx.x >> 5) * NG + lane / P;
+    const int ngrp = (FF_THREADS >> 5) * NG;
+    const bool lane_on = lane < NG * P;
     LaneCoef<R, P> lc;
     lc.load(g, k);
     for (int base = start; base < end; base += ngrp) {
         const int j = base + grp;
-        const bool live = j < end;
+        const bool live = lane_on && j < end;
         const int jj = live ? j : start;
         const vec4_t<R> r = reinterpret_cast<const vec4_t<R> *>(b.rec)[jj];
         int ax, ay, az;
@@ -371,7 +386,7 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, Sort
         GroupWeights<R, P, MODE> w;
         w.build(lc, gbase, r.x, r.y, r.z);
         R e0 = 0, e1 = 0, e2 = 0;
-        if (live && intile && k < P) {
+        if (live && intile) {
             const int row0 = (ax * Ey + ay) * Ez + az + k;
             gather_column<R, P, MODE>(w, [&](int a, int c) {
                 const int e = row0 + (a * Ey + c) * Ez;
@@ -406,9 +421,9 @@ static void launch_ff(const Geom<R> &g, int64_t n, const SortBufs &b, const R *f
                 g, b, field, f, dq, qC, sc, gs, gb);
         return;
     }
-    // one group of 8 lanes per particle, a full grid
-    const int64_t threads = n * FGROUP;
-    const int nb = (int)((threads + FF_THREADS - 1) / FF_THREADS);
+    // one group of P lanes per particle, a full grid
+    const int64_t per_cta = ff_particles_per_cta(P);
+    const int nb = (int)((n + per_cta - 1) / per_cta);
     if (pdl)
         launch_pdl(k_fieldforce<R, P, MODE>, dim3(nb), dim3(FF_THREADS), 0, s, g, b, (int)n, field, f, dq, qC, sc,
                    gs, gb);
@@ -484,7 +499,7 @@ static void launch_batch_ff(const BatchSys<R> *sys, const BatchList &bl, bool ik
         k_batch_fieldforce<R, P, 1><<<bl.nblocks, FF_THREADS, 0, s>>>(sys, bl, f, qC);
 }
 
-// CTA counts in bl are ceil(8 n / FF_THREADS) per system (one 8-lane group per particle).
+// CTA counts in bl are ceil(n / ff_particles_per_cta(P)) per system (one group of P lanes per particle).
 template <typename R>
 void launch_batch_fieldforce(const BatchSys<R> *sys, const BatchList &bl, int P, bool ik, R *f, R qC,
                              cudaStream_t s) {

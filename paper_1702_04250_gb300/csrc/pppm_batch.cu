@@ -284,7 +284,9 @@ int batch_build(pppm_batch *b, const double *box, const int64_t *n, const int *o
             if (order[s] == P) ids.push_back(s);
         if (ids.empty()) continue;
         pend.push_back({&b->rho_list[P], add_list(b->rho_list[P], ids, [&](int s) { return hs[s].g.ntiles; })});
-        pend.push_back({&b->ff_list[P], add_list(b->ff_list[P], ids, [&](int s) { return (8 * hs[s].n + 255) / 256; })});
+        pend.push_back({&b->ff_list[P], add_list(b->ff_list[P], ids, [&](int s) {
+                           return (hs[s].n + ff_particles_per_cta(P) - 1) / ff_particles_per_cta(P);
+                       })});
     }
     if ((rc = bmalloc(b, (void **)&b->d_lists, sizeof(int) * std::max<size_t>(host.size(), 1)))) return rc;
     if (!host.empty() &&

@@ -328,6 +328,9 @@ cudaError_t prepare_custom_fft(const int M[3]);  // shared-memory opt-in, before
 int launch_custom_fft(int step, const Geom<float> &g, bool ik_spec, const float *rho, void *rho_hat, void *spec,
                       float *field, const GreenBufs &b, const EnergyConsts &ec, bool pdl, cudaStream_t s);
 
+// Particles one fieldforce CTA of the per-particle kernel serves (groups of
+// P lanes, 32 / P per warp, 8 warps).
+inline int ff_particles_per_cta(int P) { return 8 * (32 / P); }
 template <typename R>
 cudaError_t prepare_fieldforce(int P);  // shared-memory opt-in of the tile-staged kernels
 template <typename R>
