@@ -455,6 +455,42 @@ def real_leg(torch, flush, steps=30):
             "timing": f"{steps} calls, L2 flushed before each"}
 
 
+def mesh_leg(torch, flush, steps=40):
+    """Mesh choice for a target accuracy on the water-like 32,001 charges
+    (r_C = 10 A, 1e-4; the error estimate runs as one FP64 kernel per mesh
+    tried), and why FFT-friendly sizes matter: the same FP32C ik step on
+    mesh edges 64 (a power of two), 67 and 71 (primes), 70 (2 5 7) and 72
+    (2^3 3^2), with g held fixed."""
+    from paper_1702_04250_gb300 import pppm
+    from paper_1702_04250_gb300.workloads import config
+
+    w = config("c2")
+    q2 = float(np.sum(w.q ** 2))
+    choice = {}
+    for name, kind in (("primes_le_7", pppm.FFT_SMOOTH), ("powers_of_two", pppm.FFT_POW2)):
+        t0 = time.perf_counter()
+        mesh, g, err = pppm.choose_mesh(w.box, w.n, q2, w.order, w.r_cut, w.rel_acc, kind)
+        choice[name] = {"mesh": list(mesh), "g_ewald": round(g, 6), "est_rms_force_err": float(f"{err:.4g}"),
+                        "choose_ms": round((time.perf_counter() - t0) * 1e3, 1)}
+    g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, q2, w.box)
+    x = torch.tensor(w.x, dtype=torch.float32, device="cuda")
+    q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
+    f = torch.empty((w.n, 3), dtype=torch.float32, device="cuda")
+    ev = torch.zeros(8, dtype=torch.float64, device="cuda")
+    sizes = {}
+    for m in (64, 67, 70, 71, 72):
+        plan = pppm.PPPM(w.box, w.n, w.order, (m, m, m), g, mode="ik", precision="fp32c", qqrd2e=w.qqrd2e,
+                         graph=True)
+        plan.autotune(x, q)
+        tot, _ = time_steps(torch, plan, x, q, f, ev, steps, 3, flush, sync_ranks=False)
+        sizes[str(m)] = {"us_per_step": round(tot / steps * 1e3, 1),
+                         "est_rms_force_err": float(f"{pppm.kspace_error(w.box, (m,) * 3, w.order, g, w.n, q2):.4g}")}
+        plan.close()
+    return {"workload": "water-like 32,001 charges, 68 A cube, P=5, ik, r_C = 10 A, target 1e-4",
+            "choice": choice, "step_by_mesh_edge_fp32c": sizes,
+            "timing": f"{steps} graph steps per mesh, L2 flushed before each"}
+
+
 def batch_leg(torch, flush, steps=20):
     """256 independent systems in one call and one graph, FP32C ik, against
     the FP64 batch and against one single-system plan per system."""
@@ -614,7 +650,7 @@ def main():
 
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         line["extra"] = {"large": large_leg(torch, flush), "batch": batch_leg(torch, flush),
-                         "real_space": real_leg(torch, flush)}
+                         "real_space": real_leg(torch, flush), "mesh_choice": mesh_leg(torch, flush)}
     if rank == 0:
         if not args.no_cpu_baseline:
             rate, n, dt = oracle_rate(workload())

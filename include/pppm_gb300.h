@@ -73,6 +73,42 @@ enum pppm_precision { PPPM_FP64 = 0, PPPM_FP32C = 1, PPPM_FP32 = 2 };
 int pppm_estimate_g(double rel_acc, double r_cut, int64_t n, double q2,
                     const double box[3], double *g_out);
 
+/* FFT-friendly mesh edge (the analogue of Sec. 5's "adjust grid sizes", which
+ * works around sizes its FFT library handled badly): *out = the smallest
+ * m >= n that is n itself (kind 0), has no prime factor above 7 (kind 1, the
+ * sizes cuFFT runs in its fast kernels), or is a power of two (kind 2, the
+ * sizes of the hand-written Poisson solve, variant bit 3).  Host only.
+ * PPPM_EINVAL for n < 1, an unknown kind or out == NULL. */
+int pppm_fft_size(int n, int kind, int *out);
+
+/* RMS k-space force error of an ik mesh (Sec. 2.3 / Sec. 4: the accuracy a
+ * mesh, order and g deliver; the paper leaves the estimate to LAMMPS).
+ * Reading: the Hockney-Eastwood functional of the optimal influence function,
+ *   Q = (1/V) sum_{k != 0} { sum_m |R(k_m)|^2 - [sum_m U^2(k_m) (k.k_m)
+ *       phi(k_m)]^2 / (k^2 [sum_m U^2(k_m)]^2) },
+ *   phi = 4 pi exp(-k^2/4g^2)/k^2, |R|^2 = k^2 phi^2, U = prod sinc^P(k h/2),
+ * aliases |m_d| <= 2 (the denominator sum exact), over this mesh's
+ * wavevectors; *err_out = q2 sqrt(Q / (n V)), the RMS force error of n
+ * randomly placed charges with sum q^2 = q2, in units of C e^2 / A^2 (the
+ * units of pppm_estimate_g's rel_acc).  Computed in FP64 by one kernel on
+ * the current device (temporary device memory, synchronous).
+ * PPPM_EINVAL for diff_mode != PPPM_IK (no ad estimate is provided), order
+ * outside 2..7, a mesh edge < order or > 1024, or an argument <= 0;
+ * PPPM_ENOMEM / PPPM_ECUDA from the device. */
+int pppm_kspace_error(const double box[3], const int mesh[3], int order, double g_ewald, int diff_mode,
+                      int64_t n, double q2, double *err_out);
+
+/* Mesh and g for a target accuracy (Sec. 2.3, Sec. 4: LAMMPS chooses the mesh
+ * from the accuracy; a larger stencil allows a coarser mesh).  g from
+ * pppm_estimate_g(rel_acc, r_cut, n, q2, box); then for c = order, order + 1,
+ * ... points along the longest edge, mesh_d = max(order,
+ * pppm_fft_size(ceil(box_d c / L_max), kind)), skipping repeats, until
+ * pppm_kspace_error(...) <= rel_acc.  Writes mesh_out[3], *g_out and
+ * (nullable) *err_out.  Synchronous.  PPPM_EINVAL as for the two calls it
+ * uses, or when no mesh with edges <= 1024 meets rel_acc. */
+int pppm_choose_mesh(const double box[3], int64_t n, double q2, int order, int diff_mode, double r_cut,
+                     double rel_acc, int kind, int mesh_out[3], double *g_out, double *err_out);
+
 /* Create a plan (Sec. 2.1 setup before step 1): the order-P assignment
  * polynomials (Sec. 3.1: product of three 1-D polynomials of order S = P),
  * the influence function G(k) on the half spectrum, the ad self-force

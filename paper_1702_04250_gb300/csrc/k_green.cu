@@ -107,6 +107,70 @@ void launch_green_setup(const GreenSetup &gs, double *G64, double *sf_sums, cuda
 }
 
 // ---------------------------------------------------------------------------
+// Setup-time k-space error estimate of an ik mesh (mesh choice for a target
+// accuracy): per half-spectrum k != 0, with weight w,
+//   w { sum_m 16 pi^2 exp(-k_m^2/2g^2) / k_m^2
+//       - [sum_m U^2(k_m) (k.k_m) 4 pi exp(-k_m^2/4g^2)/k_m^2]^2 / (k^2 D(k)^2) }
+// (the Hockney-Eastwood functional of the optimal influence function; D =
+// the full alias sum of U^2).  One FP64 partial per CTA, summed by the host
+// in CTA order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(GREEN_THREADS) k_kspace_error(KErrSetup ks, double *__restrict__ part) {
+    __shared__ double sh[GREEN_THREADS / 32];
+    const int Mx = ks.M[0], My = ks.M[1], Mzh = ks.Mzh;
+    const int64_t total = (int64_t)Mx * My * Mzh;
+    const int off[3] = {0, Mx, Mx + My};
+    const int len = Mx + My + Mzh;
+    const double twopi = 2.0 * M_PI;
+    double acc = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int iz = (int)(e % Mzh);
+        const int iy = (int)((e / Mzh) % My);
+        const int ix = (int)(e / ((int64_t)Mzh * My));
+        const double k[3] = {ks.ktab[ix], ks.ktab[off[1] + iy], ks.ktab[off[2] + iz]};
+        const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        if (k2 == 0.0) continue;
+        double num = 0.0, s1 = 0.0;
+        for (int mx = -2; mx <= 2; ++mx) {
+            const double kmx = k[0] + twopi * mx / ks.h[0];
+            const double ax = ks.atab[(mx + 2) * len + ix], ex = ks.etab[(mx + 2) * len + ix];
+            for (int my = -2; my <= 2; ++my) {
+                const double kmy = k[1] + twopi * my / ks.h[1];
+                const double ay = ks.atab[(my + 2) * len + off[1] + iy], ey = ks.etab[(my + 2) * len + off[1] + iy];
+                for (int mz = -2; mz <= 2; ++mz) {
+                    const double kmz = k[2] + twopi * mz / ks.h[2];
+                    const double az = ks.atab[(mz + 2) * len + off[2] + iz];
+                    const double ez = ks.etab[(mz + 2) * len + off[2] + iz];
+                    const double km2 = kmx * kmx + kmy * kmy + kmz * kmz;
+                    s1 += 16.0 * M_PI * M_PI * ex * ey * ez / km2;
+                    num += 4.0 * M_PI * ax * ay * az / km2 * (k[0] * kmx + k[1] * kmy + k[2] * kmz);
+                }
+            }
+        }
+        const double D = ks.dtab[ix] * ks.dtab[off[1] + iy] * ks.dtab[off[2] + iz];
+        const double w = (iz == 0 || (2 * (Mzh - 1) == ks.M[2] && iz == Mzh - 1)) ? 1.0 : 2.0;
+        acc += w * (s1 - num * num / (k2 * D * D));
+    }
+    const double v = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < GREEN_THREADS / 32; ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+int launch_kspace_error(const KErrSetup &ks, double *part, cudaStream_t s) {
+    const int64_t total = (int64_t)ks.M[0] * ks.M[1] * ks.Mzh;
+    int nb = (int)std::min<int64_t>((total + GREEN_THREADS - 1) / GREEN_THREADS, KERR_MAX_BLOCKS);
+    if (nb < 1) nb = 1;
+    k_kspace_error<<<nb, GREEN_THREADS, 0, s>>>(ks, part);
+    return nb;
+}
+
+// ---------------------------------------------------------------------------
 // Per step
 // ---------------------------------------------------------------------------
 template <typename R, bool IK>

@@ -177,19 +177,24 @@ void release(pppm_plan *p) {
 
 namespace pppm {
 
-// FP64 influence function and ad self-force coefficients of one system
-// (used by single plans and by batches).  Temporary device tables are
-// allocated and freed here; G64 must hold Mx*My*(Mz/2+1) doubles.
-int green_setup_fp64(const int M[3], const double h[3], double V, int P, bool ik, double g, double C,
-                     double *G64, double sf_out[6], std::vector<double> &ktab, std::vector<double> &kdiff,
-                     cudaStream_t stream) {
+// Per-dimension wavenumber and alias tables over (Mx, My, Mz/2 + 1), laid out
+// [x | y | z]: ktab = k (Nyquist negative), kdiff = k with the Nyquist entry
+// zeroed, atab[m + 2] = exp(-k_m^2/4g^2) U1^2(k_m) for aliases |m| <= 2,
+// dtab = the full alias sum of U1^2 (a finite cosine series), and on request
+// btab[n] (ad self-force sums) and etab[m + 2] = exp(-k_m^2/2g^2).
+void alias_tables(const int M[3], const double h[3], int P, double g, std::vector<double> &ktab,
+                  std::vector<double> &kdiff, std::vector<double> &atab, std::vector<double> &dtab,
+                  std::vector<double> *btab, std::vector<double> *etab) {
     const int Mx = M[0], My = M[1], Mzh = M[2] / 2 + 1;
     const int len = Mx + My + Mzh;
     const int dimlen[3] = {Mx, My, Mzh};
     const int off[3] = {0, Mx, Mx + My};
     ktab.assign(len, 0.0);
     kdiff.assign(len, 0.0);
-    std::vector<double> atab(5 * (size_t)len), dtab(len), btab(3 * (size_t)len);
+    atab.assign(5 * (size_t)len, 0.0);
+    dtab.assign(len, 0.0);
+    if (btab) btab->assign(3 * (size_t)len, 0.0);
+    if (etab) etab->assign(5 * (size_t)len, 0.0);
     double m2p[MAXP + 1];
     spline2p_at_integers(P, m2p);
     for (int d = 0; d < 3; ++d) {
@@ -202,13 +207,27 @@ int green_setup_fp64(const int M[3], const double h[3], double V, int P, bool ik
                 const double km = k + 2.0 * M_PI * m / h[d];
                 const double u = alias_cross(kappa + 2.0 * M_PI * m, 0, P, 0);  // U1^2 at this alias
                 atab[(size_t)(m + 2) * len + off[d] + i] = std::exp(-km * km / (4.0 * g * g)) * u;
+                if (etab) (*etab)[(size_t)(m + 2) * len + off[d] + i] = std::exp(-km * km / (2.0 * g * g));
             }
             double D = m2p[0];
             for (int gg = 1; gg < P; ++gg) D += 2.0 * m2p[gg] * std::cos(kappa * gg);
             dtab[off[d] + i] = D;
-            for (int n = 0; n <= 2; ++n) btab[(size_t)n * len + off[d] + i] = alias_cross(kappa, n, P, 50);
+            if (btab)
+                for (int n = 0; n <= 2; ++n) (*btab)[(size_t)n * len + off[d] + i] = alias_cross(kappa, n, P, 50);
         }
     }
+}
+
+// FP64 influence function and ad self-force coefficients of one system
+// (used by single plans and by batches).  Temporary device tables are
+// allocated and freed here; G64 must hold Mx*My*(Mz/2+1) doubles.
+int green_setup_fp64(const int M[3], const double h[3], double V, int P, bool ik, double g, double C,
+                     double *G64, double sf_out[6], std::vector<double> &ktab, std::vector<double> &kdiff,
+                     cudaStream_t stream) {
+    const int Mzh = M[2] / 2 + 1;
+    const int len = M[0] + M[1] + Mzh;
+    std::vector<double> atab, dtab, btab;
+    alias_tables(M, h, P, g, ktab, kdiff, atab, dtab, &btab, nullptr);
     double *tmp = nullptr;  // ktab | atab | dtab | btab | sf sums
     const size_t words = (size_t)len * 10 + 6;
     if (cudaMalloc(&tmp, words * sizeof(double)) != cudaSuccess) {
@@ -250,6 +269,77 @@ int green_setup_fp64(const int M[3], const double h[3], double V, int P, bool ik
     if (rc) return rc;
     for (int a = 0; a < 3; ++a)
         for (int n = 1; n <= 2; ++n) sf_out[a * 2 + n - 1] = 2.0 * M_PI * n * C / (h[a] * V) * sums[a * 2 + n - 1];
+    return PPPM_OK;
+}
+
+// Smallest FFT-friendly edge >= n: kind 0 n itself, 1 prime factors 2, 3, 5, 7,
+// 2 a power of two.  -1 for n < 1 or an unknown kind.
+int fft_size_host(int n, int kind) {
+    if (n < 1 || kind < 0 || kind > 2) return -1;
+    if (kind == 0) return n;
+    for (int m = n;; ++m) {
+        int r = m;
+        while (r % 2 == 0) r /= 2;
+        if (kind == 1) {
+            while (r % 3 == 0) r /= 3;
+            while (r % 5 == 0) r /= 5;
+            while (r % 7 == 0) r /= 7;
+        }
+        if (r == 1) return m;
+    }
+}
+
+// RMS k-space force error of an ik mesh for n random charges with
+// sum q^2 = q2 (units C e^2 / A^2): q2 sqrt(Q / (n V)), Q the
+// Hockney-Eastwood functional of k_kspace_error divided by V.  Synchronous,
+// on the calling thread's default stream.
+int kspace_error_ik(const int M[3], const double box[3], int P, double g, int64_t n, double q2, double *err) {
+    double h[3];
+    for (int d = 0; d < 3; ++d) h[d] = box[d] / M[d];
+    const double V = box[0] * box[1] * box[2];
+    const int Mzh = M[2] / 2 + 1;
+    const int len = M[0] + M[1] + Mzh;
+    std::vector<double> ktab, kdiff, atab, dtab, etab;
+    alias_tables(M, h, P, g, ktab, kdiff, atab, dtab, nullptr, &etab);
+    double *tmp = nullptr;  // ktab | atab | dtab | etab | partials
+    const size_t words = (size_t)len * 12 + KERR_MAX_BLOCKS;
+    if (cudaMalloc(&tmp, words * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return PPPM_ENOMEM;
+    }
+    double *d_ktab = tmp, *d_atab = tmp + len, *d_dtab = d_atab + 5 * (size_t)len, *d_etab = d_dtab + len;
+    double *d_part = d_etab + 5 * (size_t)len;
+    std::vector<double> part(KERR_MAX_BLOCKS, 0.0);
+    int rc = PPPM_OK, nb = 0;
+    do {
+        if (cudaMemcpy(d_ktab, ktab.data(), sizeof(double) * len, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d_atab, atab.data(), sizeof(double) * 5 * len, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d_dtab, dtab.data(), sizeof(double) * len, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d_etab, etab.data(), sizeof(double) * 5 * len, cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = PPPM_ECUDA;
+            break;
+        }
+        KErrSetup ks{};
+        for (int d = 0; d < 3; ++d) {
+            ks.M[d] = M[d];
+            ks.h[d] = h[d];
+        }
+        ks.Mzh = Mzh;
+        ks.ktab = d_ktab;
+        ks.atab = d_atab;
+        ks.dtab = d_dtab;
+        ks.etab = d_etab;
+        nb = launch_kspace_error(ks, d_part, 0);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(part.data(), d_part, sizeof(double) * nb, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = PPPM_ECUDA;
+    } while (0);
+    cudaFree(tmp);
+    if (rc) return rc;
+    double sum = 0.0;
+    for (int b = 0; b < nb; ++b) sum += part[b];  // fixed order
+    const double Q = sum / V;
+    *err = q2 * std::sqrt(std::max(Q, 0.0) / ((double)n * V));
     return PPPM_OK;
 }
 
@@ -530,6 +620,56 @@ int pppm_estimate_g(double rel_acc, double r_cut, int64_t n, double q2, const do
     if (!(arg > 0.0 && arg < 1.0)) return PPPM_EINVAL;
     *g_out = std::sqrt(-std::log(arg)) / r_cut;
     return PPPM_OK;
+}
+
+int pppm_fft_size(int n, int kind, int *out) {
+    if (!out) return PPPM_EINVAL;
+    const int m = fft_size_host(n, kind);
+    if (m < 0) return PPPM_EINVAL;
+    *out = m;
+    return PPPM_OK;
+}
+
+int pppm_kspace_error(const double box[3], const int mesh[3], int order, double g_ewald, int diff_mode, int64_t n,
+                      double q2, double *err_out) {
+    if (!box || !mesh || !err_out || n <= 0 || !(q2 > 0) || !(g_ewald > 0) || !std::isfinite(g_ewald))
+        return PPPM_EINVAL;
+    if (order < 2 || order > MAXP || diff_mode != PPPM_IK) return PPPM_EINVAL;
+    for (int d = 0; d < 3; ++d) {
+        if (!(box[d] > 0) || !std::isfinite(box[d])) return PPPM_EINVAL;
+        if (mesh[d] < order || mesh[d] > MAX_MESH) return PPPM_EINVAL;
+    }
+    return kspace_error_ik(mesh, box, order, g_ewald, n, q2, err_out);
+}
+
+int pppm_choose_mesh(const double box[3], int64_t n, double q2, int order, int diff_mode, double r_cut,
+                     double rel_acc, int kind, int mesh_out[3], double *g_out, double *err_out) {
+    if (!box || !mesh_out || !g_out || order < 2 || order > MAXP || diff_mode != PPPM_IK || kind < 0 || kind > 2)
+        return PPPM_EINVAL;
+    double g = 0.0;
+    int rc = pppm_estimate_g(rel_acc, r_cut, n, q2, box, &g);
+    if (rc) return rc;
+    const double lmax = std::max(box[0], std::max(box[1], box[2]));
+    int prev[3] = {0, 0, 0};
+    for (int c = order;; ++c) {
+        int mesh[3];
+        for (int d = 0; d < 3; ++d) {
+            const double want = std::ceil(box[d] * c / lmax);
+            if (want > MAX_MESH) return PPPM_EINVAL;  // no mesh up to the size limit meets the accuracy
+            mesh[d] = std::max(order, fft_size_host((int)want, kind));
+            if (mesh[d] > MAX_MESH) return PPPM_EINVAL;
+        }
+        if (mesh[0] == prev[0] && mesh[1] == prev[1] && mesh[2] == prev[2]) continue;
+        double err = 0.0;
+        if ((rc = kspace_error_ik(mesh, box, order, g, n, q2, &err))) return rc;
+        if (err <= rel_acc) {
+            for (int d = 0; d < 3; ++d) mesh_out[d] = mesh[d];
+            *g_out = g;
+            if (err_out) *err_out = err;
+            return PPPM_OK;
+        }
+        for (int d = 0; d < 3; ++d) prev[d] = mesh[d];
+    }
 }
 
 int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, const int mesh[3], double g_ewald,

@@ -406,6 +406,17 @@ struct GreenSetup {
     const double *btab;    // [3 n][Mx + My + Mzh] self-force alias sums, n = 0,1,2
 };
 void launch_green_setup(const GreenSetup &gs, double *G64, double *sf_sums, cudaStream_t s);
+// Setup-time k-space error estimate of an ik mesh: tables as for GreenSetup
+// plus etab[5][Mx + My + Mzh] = exp(-k_m^2 / 2g^2) per dimension and alias.
+// Writes one partial sum of the error functional per CTA (at most
+// KERR_MAX_BLOCKS) and returns the CTA count.
+constexpr int KERR_MAX_BLOCKS = 152 * 8;
+struct KErrSetup {
+    int M[3], Mzh;
+    double h[3];
+    const double *ktab, *atab, *dtab, *etab;
+};
+int launch_kspace_error(const KErrSetup &ks, double *part, cudaStream_t s);
 // Host driver of the above for one system (pppm_api.cu): G64 on the device,
 // the ad self-force coefficients c[a][n-1] and the wavenumber tables on the host.
 int green_setup_fp64(const int M[3], const double h[3], double V, int P, bool ik, double g, double C,

@@ -48,6 +48,9 @@ def lib() -> ctypes.CDLL:
         L.pppm_last_cuda_error.restype = ctypes.c_char_p
         L.pppm_last_cuda_error.argtypes = []
         L.pppm_estimate_g.argtypes = [dbl, dbl, i64, dbl, dptr, dptr]
+        L.pppm_fft_size.argtypes = [i32, i32, ctypes.POINTER(i32)]
+        L.pppm_kspace_error.argtypes = [dptr, ctypes.POINTER(i32), i32, dbl, i32, i64, dbl, dptr]
+        L.pppm_choose_mesh.argtypes = [dptr, i64, dbl, i32, i32, dbl, dbl, i32, ctypes.POINTER(i32), dptr, dptr]
         L.pppm_setup.argtypes = [ctypes.POINTER(vp), dptr, i64, i32, ctypes.POINTER(i32), dbl, i32, i32, dbl, vp]
         L.pppm_destroy.argtypes = [vp]
         L.pppm_set_stream.argtypes = [vp, vp]
@@ -64,7 +67,7 @@ def lib() -> ctypes.CDLL:
         L.pppm_set_variant.argtypes = [vp, i32]
         L.pppm_set_lut.argtypes = [vp, i32]
         L.pppm_autotune.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(i32)]
-        for name in ("pppm_estimate_g", "pppm_setup", "pppm_destroy", "pppm_set_stream", "pppm_set_graph",
+        for name in ("pppm_estimate_g", "pppm_fft_size", "pppm_kspace_error", "pppm_choose_mesh", "pppm_setup", "pppm_destroy", "pppm_set_stream", "pppm_set_graph",
                      "pppm_compute", "pppm_compute_host", "pppm_sync", "pppm_energy_grad", "pppm_potential",
                      "pppm_get_array",
                      "pppm_plan_info", "pppm_set_profiling", "pppm_stage_times", "pppm_set_variant", "pppm_set_lut",
@@ -92,6 +95,37 @@ def estimate_g(rel_acc: float, r_cut: float, n: int, q2: float, box) -> float:
     _check(lib().pppm_estimate_g(float(rel_acc), float(r_cut), int(n), float(q2), _d3(box), ctypes.byref(out)),
            "pppm_estimate_g")
     return out.value
+
+
+FFT_ANY, FFT_SMOOTH, FFT_POW2 = 0, 1, 2  # kinds of pppm_fft_size
+
+
+def fft_size(n: int, kind: int = FFT_SMOOTH) -> int:
+    """Smallest FFT-friendly mesh edge >= n (kind: 0 any, 1 primes <= 7, 2 powers of two)."""
+    out = ctypes.c_int()
+    _check(lib().pppm_fft_size(int(n), int(kind), ctypes.byref(out)), "pppm_fft_size")
+    return out.value
+
+
+def kspace_error(box, mesh, order: int, g_ewald: float, n: int, q2: float, mode: str = "ik") -> float:
+    """Estimated RMS k-space force error of an ik mesh (units of C e^2 / A^2)."""
+    out = ctypes.c_double()
+    m = (ctypes.c_int * 3)(*[int(v) for v in mesh])
+    _check(lib().pppm_kspace_error(_d3(box), m, int(order), float(g_ewald), MODES[mode], int(n), float(q2),
+                                   ctypes.byref(out)), "pppm_kspace_error")
+    return out.value
+
+
+def choose_mesh(box, n: int, q2: float, order: int, r_cut: float, rel_acc: float, kind: int = FFT_SMOOTH,
+                mode: str = "ik"):
+    """(mesh, g_ewald, estimated error) meeting rel_acc with the coarsest FFT-friendly mesh of the scan."""
+    mesh = (ctypes.c_int * 3)()
+    g = ctypes.c_double()
+    err = ctypes.c_double()
+    _check(lib().pppm_choose_mesh(_d3(box), int(n), float(q2), int(order), MODES[mode], float(r_cut),
+                                  float(rel_acc), int(kind), mesh, ctypes.byref(g), ctypes.byref(err)),
+           "pppm_choose_mesh")
+    return tuple(mesh), g.value, err.value
 
 
 def _ptr(t):
