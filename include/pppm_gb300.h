@@ -227,8 +227,11 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * as three hand-written kernels instead of cuFFT plus two kernels; allowed
  * for PPPM_FP32 / PPPM_FP32C plans whose three mesh edges are each 16, 32, 64
  * or 128 (PPPM_EINVAL otherwise).  Results agree with the cuFFT path to FP32
- * rounding.  Default: bit 0 for ik plans whose n_max is at least 16 per tile,
- * plus bit 3 where it is allowed.
+ * rounding.  Bit 4: mesh tiles of 4 points per edge instead of 8 (eight
+ * times the tiles and CTAs of the sort, make_rho and the tile-staged
+ * fieldforce, a larger halo share); not with bit 1.  Default: bit 4 when the
+ * mesh has fewer than 304 tiles of 8^3 (two per SM), bit 0 for ik plans whose
+ * n_max is at least 16 per tile, bit 3 where it is allowed.
  * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a
  * combination the plan does not allow).
  * pppm_autotune times every variant on the caller's inputs (one warm-up and

@@ -40,7 +40,7 @@ struct pppm_plan {
     int M[3] = {0, 0, 0}, Mzh = 0;
     int64_t Mtot = 0, Mhalf = 0;
     int T[3] = {0, 0, 0}, TE[3] = {0, 0, 0}, ntiles = 0;
-    int ntiles_alloc = 0;              // tile arrays are sized for 8^3 tiles, the most numerous shape
+    int ntiles_alloc = 0;              // tile arrays are sized for 4^3 tiles, the most numerous shape
     double box[3] = {0, 0, 0}, h[3] = {0, 0, 0}, g = 0, C = 0, V = 0, vcell = 0;
     int64_t n_max = 0, n_last = -1;
     Geom<float> gf{};
@@ -555,7 +555,8 @@ void drop_graph(pppm_plan *p) {
 }
 
 bool variant_ok(const pppm_plan *p, int v) {
-    if (v & ~15) return false;
+    if (v & ~31) return false;
+    if ((v & 16) && (v & 2)) return false;      // one tile shape at a time
     if ((v & 8) && !p->fft_own) return false;  // FP32 plans with power-of-two mesh edges 16..128
     if ((v & 4) && !p->comp) return false;  // the four-copy brick is the FP32C accumulator
     if ((v & 2) && !long_tiles_allowed(p->P, p->comp)) return false;
@@ -563,11 +564,11 @@ bool variant_ok(const pppm_plan *p, int v) {
 }
 
 // Variant bits: 0 tile-staged fieldforce, 1 long tiles (16 along z), 2
-// four-copy make_rho brick, 3 hand-written Poisson solve.  The tile shape
-// changes the sort; the histogram is cleared for the new shape.
+// four-copy make_rho brick, 3 hand-written Poisson solve, 4 small tiles (4^3).
+// The tile shape changes the sort; the histogram is cleared for the new shape.
 void set_variants(pppm_plan *p, int v) {
     p->variants = v;
-    tile_shape(p->M, (v & 2) != 0, p->T, p->TE);
+    tile_shape(p->M, (v & 2) != 0, p->T, p->TE, (v & 16) != 0);
     p->ntiles = p->T[0] * p->T[1] * p->T[2];
     for (int d = 0; d < 3; ++d) {
         p->gf.T[d] = p->gd.T[d] = p->T[d];
@@ -705,11 +706,13 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         p->h[d] = box[d] / mesh[d];
     }
     tile_shape(p->M, false, p->T, p->TE);
+    int T4[3], TE4[3];
+    tile_shape(p->M, false, T4, TE4, true);
     p->Mzh = mesh[2] / 2 + 1;
     p->Mtot = (int64_t)mesh[0] * mesh[1] * mesh[2];
     p->Mhalf = (int64_t)mesh[0] * mesh[1] * p->Mzh;
     p->ntiles = p->T[0] * p->T[1] * p->T[2];
-    p->ntiles_alloc = p->ntiles;
+    p->ntiles_alloc = T4[0] * T4[1] * T4[2];
     p->V = box[0] * box[1] * box[2];
     p->vcell = p->h[0] * p->h[1] * p->h[2];
 
@@ -799,7 +802,12 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     // hold enough particles; the ad potential (4 bytes) reads best through L1
     // (the four-copy make_rho brick measured level at P = 5 and slower at P = 7)
     // the hand-written Poisson solve replaces seven cuFFT/green launches by three
-    set_variants(p, ((p->ik && (double)n_max >= 16.0 * p->ntiles) ? 1 : 0) | (p->fft_own ? 8 : 0));
+    // with fewer 8^3 tiles than two per SM, 4^3 tiles give the mesh stages enough CTAs
+    const bool small_tiles = p->ntiles < 2 * 152;
+    int T0[3], TE0[3];
+    tile_shape(p->M, false, T0, TE0, small_tiles);
+    const int nt0 = T0[0] * T0[1] * T0[2];
+    set_variants(p, ((p->ik && (double)n_max >= 16.0 * nt0) ? 1 : 0) | (p->fft_own ? 8 : 0) | (small_tiles ? 16 : 0));
     if ((rc = build_tables_and_green(p))) return fail(rc);
     if ((rc = make_ffts(p))) return fail(rc);
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(PPPM_ECUDA);
@@ -1037,7 +1045,7 @@ int pppm_autotune(pppm_plan *p, int64_t n, const void *x, const void *q, void *f
     float best = 1e30f;
     int best_v = p->variants;
     int rc = PPPM_OK;
-    for (int v = 0; v <= 15 && rc == PPPM_OK; ++v) {
+    for (int v = 0; v <= 31 && rc == PPPM_OK; ++v) {
         if (!variant_ok(p, v)) continue;
         set_variants(p, v);
         float tot = 0.0f;
