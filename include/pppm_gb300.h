@@ -152,9 +152,13 @@ int pppm_set_stream(pppm_plan *p, void *cuda_stream);
  * replaced), so alternating profiled and plain steps captures nothing new. */
 int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f, double *ev);
 
-/* pppm_compute on HOST buffers: copies x and q to the device, computes, copies
+/* pppm_compute on HOST buffers: moves x and q to the device, computes, moves
  * f and the 7 energy/virial doubles back, synchronises and returns the device
- * status (PPPM_ENONFINITE if an input was not finite).  ev_host may be NULL. */
+ * status (PPPM_ENONFINITE if an input was not finite).  ev_host may be NULL.
+ * Buffers in pinned host memory that the device can address (cudaHostAlloc,
+ * cudaHostRegister) are read (x, q) and written (ev) by the kernels directly
+ * over the host-device link; other buffers are copied through device
+ * staging.  f always comes back as one device-to-host copy. */
 int pppm_compute_host(pppm_plan *p, int64_t n, const void *x_host, const void *q_host,
                       void *f_host, double *ev_host);
 

@@ -581,6 +581,19 @@ void set_variants(pppm_plan *p, int v) {
     drop_graph(p);
 }
 
+// The device address of a caller's host buffer when the current device can
+// dereference it (pinned host memory mapped into the unified address space,
+// e.g. from cudaHostAlloc or cudaHostRegister), else nullptr.  Asked on every
+// call: a cached answer could outlive the buffer.
+void *device_alias(const void *host) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -897,14 +910,23 @@ int pppm_compute_host(pppm_plan *p, int64_t n, const void *x_host, const void *q
     if (!p || n < 0 || n > p->n_max) return PPPM_EINVAL;
     if (!valid_ptr_arg(n, x_host) || !valid_ptr_arg(n, q_host) || !valid_ptr_arg(n, f_host)) return PPPM_EINVAL;
     const size_t rs = p->fp64 ? 8 : 4;
-    if (n > 0) {
+    // Pinned buffers mapped into the device's address space are read (x, q)
+    // and written (energy/virial) by the kernels themselves over the
+    // host-device link; other buffers go through the plan's device staging.
+    const void *xa = (n > 0) ? device_alias(x_host) : nullptr;
+    const void *qa = (n > 0) ? device_alias(q_host) : nullptr;
+    double *eva = (n > 0 && ev_host) ? static_cast<double *>(device_alias(ev_host)) : nullptr;
+    const bool direct_in = xa && qa;
+    if (n > 0 && !direct_in) {
         CK(cudaMemcpyAsync(p->hx, x_host, 3 * rs * n, cudaMemcpyHostToDevice, p->stream));
         CK(cudaMemcpyAsync(p->hq, q_host, rs * n, cudaMemcpyHostToDevice, p->stream));
     }
-    int rc = pppm_compute(p, n, p->hx, p->hq, p->hf, p->hev);
+    // f comes back as one bulk copy: fieldforce's stores are scattered in
+    // input order, and writing them straight to host memory measured no faster
+    int rc = pppm_compute(p, n, direct_in ? xa : p->hx, direct_in ? qa : p->hq, p->hf, eva ? eva : p->hev);
     if (rc) return rc;
     if (n > 0) CK(cudaMemcpyAsync(f_host, p->hf, 3 * rs * n, cudaMemcpyDeviceToHost, p->stream));
-    if (ev_host) CK(cudaMemcpyAsync(ev_host, p->hev, 7 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    if (ev_host && !eva) CK(cudaMemcpyAsync(ev_host, p->hev, 7 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     // the error word travels with the results: one stream synchronisation per call
     CK(cudaMemcpyAsync(p->h_err, p->sb.err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));

@@ -299,6 +299,39 @@ def test_graph_mode_and_host_path_match(torch, c2_refs):
     check_all(fh.astype(np.float64), evh, refs[("ik", "fp32")], "fp32c", "c2 host path")
 
 
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_host_call_with_pinned_buffers(torch, c2_refs, prec):
+    """Pinned host buffers (read and written by the kernels over the link) and
+    pageable ones (staged copies) give the device call's results, in graph
+    mode too; a non-finite input still comes back as a status."""
+    w, g, refs = c2_refs
+    from paper_1702_04250_gb300 import pppm
+
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, "ik", prec, w.qqrd2e, graph=True)
+    f0, ev0 = plan.compute(torch.tensor(w.x, dtype=dt, device="cuda"), torch.tensor(w.q, dtype=dt, device="cuda"))
+    plan.sync()
+    f0 = f0.double().cpu().numpy()
+    ev0 = ev0.cpu().numpy().copy()
+    xh = torch.tensor(w.x, dtype=dt).pin_memory()
+    qh = torch.tensor(w.q, dtype=dt).pin_memory()
+    fh = torch.empty((w.n, 3), dtype=dt).pin_memory()
+    evh = torch.zeros(8, dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        fh.zero_()
+        evh.zero_()
+        plan.compute_host_into(w.n, xh.data_ptr(), qh.data_ptr(), fh.data_ptr(), evh.data_ptr())
+        assert rel_rms(fh.double().numpy(), f0) < 1e-5
+        assert abs(evh[0].item() - ev0[0]) <= 1e-6 * abs(ev0[0])
+    npdt = np.float64 if prec == "fp64" else np.float32
+    fp, _ = plan.compute_host(np.asarray(w.x, dtype=npdt), np.asarray(w.q, dtype=npdt))  # pageable: staged
+    assert rel_rms(fp.astype(np.float64), f0) < 1e-5
+    xh[5, 1] = float("nan")
+    with pytest.raises(pppm.PPPMError):
+        plan.compute_host_into(w.n, xh.data_ptr(), qh.data_ptr(), fh.data_ptr(), evh.data_ptr())
+    plan.close()
+
+
 @pytest.mark.parametrize("mode", ["ik", "ad"])
 def test_fieldforce_variants_and_autotune(torch, c2_refs, mode):
     """Both fieldforce variants (per-particle through L1, tile-staged brick)
