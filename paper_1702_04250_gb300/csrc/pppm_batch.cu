@@ -52,6 +52,12 @@ struct pppm_batch {
     int64_t ntot = 0;
     cudaStream_t stream = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // parallel branches for independent launches (one per mesh class or
+    // order): up to kLanes streams, forked from and joined back to `stream`
+    static constexpr int kLanes = 8;
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> lane_done;
+    cudaEvent_t fan = nullptr;
     void *d_sys = nullptr;              // BatchSys<R>[nsys]
     int *d_lists = nullptr;
     BatchList map_list{}, green_list{};
@@ -89,6 +95,9 @@ void batch_release(pppm_batch *b) {
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->join) cudaEventDestroy(b->join);
     if (b->side) cudaStreamDestroy(b->side);
+    if (b->fan) cudaEventDestroy(b->fan);
+    for (auto e : b->lane_done) cudaEventDestroy(e);
+    for (auto st : b->lanes) cudaStreamDestroy(st);
     for (void *v : b->allocs) cudaFree(v);
     delete b;
 }
@@ -179,7 +188,8 @@ int batch_build(pppm_batch *b, const double *box, const int64_t *n, const int *o
         poff += n[s];
         S.map_nb = (int)((n[s] + 255) / 256);
         const int rows = M[0] * M[1];
-        S.green_nb = std::min(std::max((rows + 7) / 8, 1), 152 * 8);
+        // eight z rows per warp before the CTA's energy/virial reduction
+        S.green_nb = std::min(std::max((rows + 63) / 64, 1), 152 * 8);
         const int64_t nn = std::max<int64_t>(n[s], 1);
         void *p;
         if ((rc = bmalloc(b, &p, 4 * nn))) return rc;
@@ -321,27 +331,53 @@ int batch_build(pppm_batch *b, const double *box, const int64_t *n, const int *o
     return PPPM_OK;
 }
 
+// Fork the lanes off `s` / join them back (graph branches under capture).
+bool fan_out(pppm_batch *b, cudaStream_t s) {
+    if (cudaEventRecord(b->fan, s) != cudaSuccess) return false;
+    for (auto st : b->lanes)
+        if (cudaStreamWaitEvent(st, b->fan, 0) != cudaSuccess) return false;
+    return true;
+}
+bool fan_in(pppm_batch *b, cudaStream_t s) {
+    for (size_t i = 0; i < b->lanes.size(); ++i)
+        if (cudaEventRecord(b->lane_done[i], b->lanes[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(s, b->lane_done[i], 0) != cudaSuccess)
+            return false;
+    return true;
+}
+
 template <typename R>
 int batch_enqueue(pppm_batch *b, const R *x, const R *q, R *f, double *ev) {
     cudaStream_t s = b->stream;
     const auto *sys = reinterpret_cast<const BatchSys<R> *>(b->d_sys);
     const size_t rs = sizeof(R);
+    const int nl = (int)b->lanes.size();
     for (auto &mc : b->classes)
         if (cudaMemsetAsync(mc.rho, 0, rs * mc.Mtot * mc.members.size(), s) != cudaSuccess) return PPPM_ECUDA;
     launch_batch_sort<R>(sys, b->map_list, x, q, s);
+    // make_rho per order, then each class's forward transform: independent
+    // systems and meshes, one branch each
+    if (!fan_out(b, s)) return PPPM_ECUDA;
     for (int P = 2; P <= MAXP; ++P)
-        launch_batch_make_rho<R>(sys, b->rho_list[P], P, b->comp, ((b->variants >> P) & 1) != 0, s);
-    for (auto &mc : b->classes) {
+        launch_batch_make_rho<R>(sys, b->rho_list[P], P, b->comp, ((b->variants >> P) & 1) != 0, b->lanes[P % nl]);
+    if (!fan_in(b, s) || !fan_out(b, s)) return PPPM_ECUDA;
+    for (size_t i = 0; i < b->classes.size(); ++i) {
+        auto &mc = b->classes[i];
+        if (cufftSetStream(mc.r2c, b->lanes[i % nl]) != CUFFT_SUCCESS) return PPPM_ECUFFT;
         cufftResult r = b->fp64 ? cufftExecD2Z(mc.r2c, (cufftDoubleReal *)mc.rho, (cufftDoubleComplex *)mc.rho_hat)
                                 : cufftExecR2C(mc.r2c, (cufftReal *)mc.rho, (cufftComplex *)mc.rho_hat);
         if (r != CUFFT_SUCCESS) return PPPM_ECUFFT;
     }
+    if (!fan_in(b, s)) return PPPM_ECUDA;
     launch_batch_green<R>(sys, b->green_list, b->ik, s);
     if (cudaEventRecord(b->fork, s) != cudaSuccess || cudaStreamWaitEvent(b->side, b->fork, 0) != cudaSuccess)
         return PPPM_ECUDA;
     launch_batch_energy_final<R>(sys, b->nsys, ev, b->side);
     if (cudaEventRecord(b->join, b->side) != cudaSuccess) return PPPM_ECUDA;
-    for (auto &mc : b->classes) {
+    if (!fan_out(b, s)) return PPPM_ECUDA;
+    for (size_t i = 0; i < b->classes.size(); ++i) {
+        auto &mc = b->classes[i];
+        if (cufftSetStream(mc.c2r, b->lanes[i % nl]) != CUFFT_SUCCESS) return PPPM_ECUFFT;
         const int ncomp = b->ik ? 3 : 1;
         for (int a = 0; a < ncomp; ++a) {
             char *in = (char *)mc.spec + 2 * rs * mc.Mhalf * a;
@@ -351,7 +387,10 @@ int batch_enqueue(pppm_batch *b, const R *x, const R *q, R *f, double *ev) {
             if (r != CUFFT_SUCCESS) return PPPM_ECUFFT;
         }
     }
-    for (int P = 2; P <= MAXP; ++P) launch_batch_fieldforce<R>(sys, b->ff_list[P], P, b->ik, f, (R)b->C, s);
+    if (!fan_in(b, s) || !fan_out(b, s)) return PPPM_ECUDA;
+    for (int P = 2; P <= MAXP; ++P)
+        launch_batch_fieldforce<R>(sys, b->ff_list[P], P, b->ik, f, (R)b->C, b->lanes[P % nl]);
+    if (!fan_in(b, s)) return PPPM_ECUDA;
     if (cudaStreamWaitEvent(s, b->join, 0) != cudaSuccess) return PPPM_ECUDA;
     return cudaGetLastError() == cudaSuccess ? PPPM_OK : PPPM_ECUDA;
 }
@@ -400,8 +439,23 @@ int pppm_batch_setup(pppm_batch **out, int nsys, const double *box, const int64_
     int rc = PPPM_OK;
     if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fan, cudaEventDisableTiming) != cudaSuccess)
         rc = PPPM_ECUDA;
+    for (int i = 0; i < pppm_batch::kLanes && !rc; ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            rc = PPPM_ECUDA;
+            break;
+        }
+        b->lanes.push_back(st);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            rc = PPPM_ECUDA;
+            break;
+        }
+        b->lane_done.push_back(e);
+    }
     if (!rc) rc = bmalloc(b, (void **)&b->err, 16);
     if (!rc && cudaMemset(b->err, 0, 16) != cudaSuccess) rc = PPPM_ECUDA;
     for (int P = 2; P <= MAXP && !rc; ++P) {
