@@ -230,7 +230,7 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * function with the energy/virial sums, inverse FFT(s); Sec. 2.1 step 2) runs
  * as three hand-written kernels instead of cuFFT plus two kernels; allowed
  * for PPPM_FP32 / PPPM_FP32C plans whose three mesh edges are each 16, 32, 64
- * or 128 (PPPM_EINVAL otherwise).  Results agree with the cuFFT path to FP32
+ * or 128, or cubic meshes of edge 48 or 96 (PPPM_EINVAL otherwise).  Results agree with the cuFFT path to FP32
  * rounding.  Bit 4: mesh tiles of 4 points per edge instead of 8 (eight
  * times the tiles and CTAs of the sort, make_rho and the tile-staged
  * fieldforce, a larger halo share); not with bit 1.  Default: bit 4 when the

@@ -1,7 +1,7 @@
 // The Poisson solve of Sec. 2.1 step 2 / Sec. 3.2 -- forward 3-D FFT of the
 // mesh charge, multiply by the influence function, one (ad) or three (ik)
 // inverse 3-D FFTs -- as three kernels for FP32 plans whose mesh edges are
-// powers of two from 16 to 128:
+// powers of two from 16 to 128, or cubic meshes of edge 48 or 96:
 //   plane forward   CTA per x-plane: z real-to-complex of every row (two
 //                   rows packed in one complex transform), then the y
 //                   transform of every kz column         rho -> A[x][ky][kz]
@@ -17,7 +17,8 @@
 // the potential: one value per point).  cuFFT serves other meshes and FP64.
 //
 // One 1-D transform of length N = E L runs on a group of L lanes holding E
-// points each (E = 8, or 16 for N = 128), as the four-step factorisation
+// points each (E = 8; 16 for N = 128, 12 for 48, 24 for 96), as the
+// four-step factorisation
 // with n = j + L a and k = b + E c (j: lane in the group):
 //   X[b + E c] = sum_j W_L^(j c) W_N^(j b) sum_a W_E^(a b) x[j + L a]
 // i.e. an E-point DFT in registers, the twiddle W_N^(j b), a transpose
@@ -38,8 +39,8 @@ constexpr int FFT_WARPS = FFT_THREADS / 32;
 
 template <int N>
 struct Fft {
-    static_assert(N == 16 || N == 32 || N == 64 || N == 128, "power-of-two length 16..128");
-    static constexpr int E = (N == 128) ? 16 : 8;  // points per lane
+    static_assert(N == 16 || N == 32 || N == 64 || N == 128 || N == 48 || N == 96, "supported lengths");
+    static constexpr int E = (N == 128) ? 16 : (N == 96) ? 24 : (N == 48) ? 12 : 8;  // points per lane
     static constexpr int L = N / E;                 // lanes per line
     static constexpr int LINES = E / L;             // b-lines per lane in the out layout
     static constexpr int G = 32 / L;                // lines per warp
@@ -64,6 +65,44 @@ __device__ __forceinline__ constexpr float s16(int q) {
 // i with its low `bits` (<= 4) bits reversed
 __host__ __device__ constexpr int brev_bits(int i, int bits) {
     return (((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3)) >> (4 - bits);
+}
+
+// cos and sin of 2 pi q / m at compile time (Taylor series of the reduced
+// angle, double precision) for the twiddles of the mixed-radix stages
+__host__ __device__ constexpr double cx_angle(int q, int m) {
+    const int r = ((q % m) + m) % m;                       // [0, m)
+    const double a = 6.283185307179586476925 * r / m;      // [0, 2 pi)
+    return a > 3.141592653589793238463 ? a - 6.283185307179586476925 : a;  // (-pi, pi]
+}
+__host__ __device__ constexpr double cx_sin(double x) {
+    double term = x, sum = x;
+    for (int n = 1; n < 24; ++n) {
+        term *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double cx_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int n = 1; n < 24; ++n) {
+        term *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+        sum += term;
+    }
+    return sum;
+}
+template <int Q, int M>
+struct Twiddle {
+    static constexpr float c = (float)cx_cos(cx_angle(Q, M));
+    static constexpr float s = (float)cx_sin(cx_angle(Q, M));
+};
+
+// f(std::integral_constant<int, I>) for I = B .. E-1, in order
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
 }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -96,31 +135,79 @@ __device__ __forceinline__ void dit_stage(float2 (&t)[M]) {
     }
 }
 
-// In-register DFT of M = 2, 4, 8, 16 points at v[OFF .. OFF + M), natural
-// order in and out (radix 2, the bit reversal is a renaming of registers).
+// a * W_M^Q, W = exp(-2 pi i / M) (forward) or its conjugate (INV); compile-time twiddle
+template <bool INV, int Q, int M>
+__device__ __forceinline__ float2 mul_tw(float2 a) {
+    if constexpr (Q % M == 0) {
+        return a;
+    } else {
+        constexpr float c = Twiddle<Q, M>::c, sn = Twiddle<Q, M>::s;
+        const float s = INV ? sn : -sn;
+        return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+    }
+}
+
 template <int M, bool INV, int OFF = 0, int K>
+__device__ __forceinline__ void dft_reg(float2 (&v)[K]);
+
+// M = 3 m: three m-point DFTs of the stride-3 subsequences, the twiddles
+// W_M^(n1 k2), and a 3-point DFT for every k2 (decimation in time).
+template <int M, bool INV, int OFF, int K>
+__device__ __forceinline__ void dft_radix3(float2 (&v)[K]) {
+    constexpr int m = M / 3;
+    float2 s0[m], s1[m], s2[m];
+#pragma unroll
+    for (int n = 0; n < m; ++n) {
+        s0[n] = v[OFF + 3 * n];
+        s1[n] = v[OFF + 3 * n + 1];
+        s2[n] = v[OFF + 3 * n + 2];
+    }
+    dft_reg<m, INV>(s0);
+    dft_reg<m, INV>(s1);
+    dft_reg<m, INV>(s2);
+    constexpr float h3 = 0.866025403784438646764f;  // sqrt(3) / 2
+    static_for<0, m>([&](auto ic) {
+        constexpr int k = decltype(ic)::value;
+        const float2 a = s0[k];
+        const float2 b = mul_tw<INV, k, M>(s1[k]);
+        const float2 c = mul_tw<INV, 2 * k, M>(s2[k]);
+        const float2 t1 = cadd(b, c);
+        const float2 t2 = make_float2(a.x - 0.5f * t1.x, a.y - 0.5f * t1.y);
+        const float2 d = csub(b, c);
+        // -i sqrt(3)/2 (b - c) forward, +i sqrt(3)/2 (b - c) inverse
+        const float2 t3 = INV ? make_float2(-h3 * d.y, h3 * d.x) : make_float2(h3 * d.y, -h3 * d.x);
+        v[OFF + k] = cadd(a, t1);
+        v[OFF + k + m] = cadd(t2, t3);
+        v[OFF + k + 2 * m] = csub(t2, t3);
+    });
+}
+
+// In-register DFT of M points at v[OFF .. OFF + M), natural order in and
+// out: M = 2, 4, 8, 16 radix 2 (the bit reversal is a renaming of
+// registers), M = 3 * 2^k by one radix-3 split over those.
+template <int M, bool INV, int OFF, int K>
 __device__ __forceinline__ void dft_reg(float2 (&v)[K]) {
-    constexpr int LOGM = M == 2 ? 1 : M == 4 ? 2 : M == 8 ? 3 : 4;
+    if constexpr (M % 3 == 0) {
+        dft_radix3<M, INV, OFF>(v);
+        return;
+    } else {
+    constexpr int LOGM = M == 1 ? 0 : M == 2 ? 1 : M == 4 ? 2 : M == 8 ? 3 : 4;
     float2 t[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) t[i] = v[OFF + brev_bits(i, LOGM)];
-    dit_stage<M, 1, INV>(t);
+    if constexpr (M >= 2) dit_stage<M, 1, INV>(t);
     if constexpr (M >= 4) dit_stage<M, 2, INV>(t);
     if constexpr (M >= 8) dit_stage<M, 4, INV>(t);
     if constexpr (M >= 16) dit_stage<M, 8, INV>(t);
 #pragma unroll
     for (int i = 0; i < M; ++i) v[OFF + i] = t[i];
+    }
 }
 
 // dft_reg<L> on each of the LINES consecutive L-register lines of v
 template <int L, int LINES, bool INV, int K>
 __device__ __forceinline__ void line_dfts(float2 (&v)[K]) {
-    dft_reg<L, INV, 0>(v);
-    if constexpr (LINES > 1) dft_reg<L, INV, L>(v);
-    if constexpr (LINES > 2) {
-        dft_reg<L, INV, 2 * L>(v);
-        dft_reg<L, INV, 3 * L>(v);
-    }
+    static_for<0, LINES>([&](auto ic) { dft_reg<L, INV, decltype(ic)::value * L>(v); });
 }
 
 // index held by register r of lane j in the out layout
@@ -290,7 +377,7 @@ __global__ void __launch_bounds__(32 * plane_warps<NY, NZ>()) k_fft_plane_fwd(co
             for (int t = 0; t < T; ++t) {
                 const int k = j + FZ::L * t;
                 if (k < MZH) {
-                    const float2 zk = scr[k], zm = scr[(NZ - k) & (NZ - 1)];
+                    const float2 zk = scr[k], zm = scr[k == 0 ? 0 : NZ - k];  // Z[-k]
                     x1[t] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
                     x2[t] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
                 }
@@ -341,6 +428,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_green(int My, int nlb, co
     using F = Fft<NX>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float2 tw[NX];
+    __shared__ float kvx[NX], kdx[NX];
     __shared__ double sh[7][FFT_WARPS];
     fill_twiddles<NX>(tw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -355,23 +443,21 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_green(int My, int nlb, co
     const float *__restrict__ kd = reinterpret_cast<const float *>(b.kdiff);
     const int64_t total = (int64_t)NX * My * MZH;
     // plan constants (nothing in the step writes them), loaded before the
-    // wait: G / M and the kx wavenumbers (energy) or derivative factors of
-    // this lane's out-layout points
-    float Gk[F::E], kx[F::E];
+    // wait: G / M of this lane's out-layout points, the x wavenumbers and
+    // derivative factors (shared), this line's y and z ones
+    float Gk[F::E];
 #pragma unroll
     for (int r = 0; r < F::E; ++r) {
         const int k = out_index<NX>(j, r);
         Gk[r] = ok ? __ldg(Gs + ((int64_t)k * My + ky) * MZH + kz) : 0.0f;
-        kx[r] = (a == 0) ? __ldg(kv + k) : 0.0f;
+    }
+    for (int t = threadIdx.x; t < NX; t += FFT_THREADS) {
+        kvx[t] = __ldg(kv + t);
+        kdx[t] = __ldg(kd + t);
     }
     const float kyv = __ldg(kv + NX + ky), kzv = __ldg(kv + NX + My + kz);
     const float dky = __ldg(kd + NX + ky), dkz = __ldg(kd + NX + My + kz);
-    float dkx[F::E];
-    if (IK && a == 0) {
-#pragma unroll
-        for (int r = 0; r < F::E; ++r) dkx[r] = __ldg(kd + out_index<NX>(j, r));
-    }
-    __syncthreads();  // twiddles
+    __syncthreads();  // twiddles and wavenumber tables
     pdl_wait();
     pdl_trigger();
     float2 v[F::E];
@@ -389,7 +475,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_green(int My, int nlb, co
 #pragma unroll
         for (int r = 0; r < F::E; ++r) {
             const float s = w * Gk[r] * (v[r].x * v[r].x + v[r].y * v[r].y);
-            const float kxv = kx[r];
+            const float kxv = kvx[out_index<NX>(j, r)];
             const float k2 = kxv * kxv + kyv * kyv + kzv * kzv;
             const float fac = (k2 > 0.0f) ? 2.0f * (1.0f + k2 * i4g2) / k2 : 0.0f;
             const float sf = s * fac;
@@ -419,7 +505,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_green(int My, int nlb, co
         const float pr = Gk[r] * v[r].x, pi = Gk[r] * v[r].y;
         if (IK) {
             // E_a = -i k_a G rho_hat / M  ->  (k_a pi, -k_a pr), Nyquist zeroed
-            const float dk = (a == 0) ? dkx[r] : ((a == 1) ? dky : dkz);
+            const float dk = (a == 0) ? kdx[out_index<NX>(j, r)] : ((a == 1) ? dky : dkz);
             v[r] = make_float2(dk * pi, -dk * pr);
         } else {
             v[r] = make_float2(pr, pi);
@@ -527,7 +613,12 @@ __global__ void __launch_bounds__(32 * plane_warps<NY, NZ>()) k_fft_plane_inv(co
 // ---------------------------------------------------------------------------
 // host side: dispatch over the mesh edges
 // ---------------------------------------------------------------------------
+// Cubic meshes of these edges use the mixed-radix lengths (one instantiation
+// per edge rather than one per combination of edges).
+bool cubic_mixed(const int M[3]) { return M[0] == M[1] && M[1] == M[2] && (M[0] == 48 || M[0] == 96); }
+
 bool custom_fft_supported(const int M[3]) {
+    if (cubic_mixed(M)) return true;
     for (int d = 0; d < 3; ++d)
         if (M[d] != 16 && M[d] != 32 && M[d] != 64 && M[d] != 128) return false;
     return true;
@@ -563,8 +654,33 @@ int x_line_blocks(int My, int mzh) {
 
 }  // namespace
 
+template <int N>
+cudaError_t prepare_cubic() {
+    constexpr int MZH = N / 2 + 1;
+    cudaError_t e = cudaFuncSetAttribute(k_fft_plane_fwd<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)plane_fwd_smem<N, N>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_plane_inv<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)plane_inv_smem<N, N>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_x_green<N, MZH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)x_green_smem<N>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_x_green<N, MZH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)x_green_smem<N>());
+    return e;
+}
+
+// fn(std::integral_constant<int, N>) for the cubic mixed-radix edge of M
+template <typename F>
+void cubic_dispatch(const int M[3], F &&fn) {
+    if (M[0] == 48) fn(std::integral_constant<int, 48>{});
+    else fn(std::integral_constant<int, 96>{});
+}
+
 cudaError_t prepare_custom_fft(const int M[3]) {
     if (!custom_fft_supported(M)) return cudaErrorInvalidValue;
+    if (cubic_mixed(M)) return M[0] == 48 ? prepare_cubic<48>() : prepare_cubic<96>();
     cudaError_t e = cudaSuccess;
     pow2_dispatch(M[1], [&](auto ny) {
         pow2_dispatch(M[2], [&](auto nz) {
@@ -600,6 +716,27 @@ int launch_custom_fft(int step, const Geom<float> &g, bool ik_spec, const float 
     const int ncomp = ik_spec ? 3 : 1;
     const int64_t total = (int64_t)Mx * My * (g.M[2] / 2 + 1);
     int nparts = 0;
+    if (cubic_mixed(g.M)) {
+        cubic_dispatch(g.M, [&](auto nn) {
+            constexpr int N = decltype(nn)::value, MZH = N / 2 + 1;
+            if (step == 0) {
+                launch_k(k_fft_plane_fwd<N, N>, pdl, Mx, 32 * plane_warps<N, N>(), plane_fwd_smem<N, N>(), s, rho, A);
+            } else if (step == 1) {
+                const int nlb = x_line_blocks<N>(My, MZH);
+                if (ik_spec)
+                    launch_k(k_fft_x_green<N, MZH, true>, pdl, nlb * ncomp, FFT_THREADS, x_green_smem<N>(), s, My, nlb,
+                             (const float2 *)A, S, b, ec);
+                else
+                    launch_k(k_fft_x_green<N, MZH, false>, pdl, nlb * ncomp, FFT_THREADS, x_green_smem<N>(), s, My,
+                             nlb, (const float2 *)A, S, b, ec);
+                nparts = nlb;
+            } else {
+                launch_k(k_fft_plane_inv<N, N>, pdl, Mx * ncomp, 32 * plane_warps<N, N>(), plane_inv_smem<N, N>(), s,
+                         (const float2 *)S, field, Mx, total, ncomp == 3 ? 4 : 1);
+            }
+        });
+        return nparts;
+    }
     if (step == 0) {
         pow2_dispatch(My, [&](auto ny) {
             pow2_dispatch(g.M[2], [&](auto nz) {

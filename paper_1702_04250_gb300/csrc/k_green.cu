@@ -274,8 +274,10 @@ int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec, con
                  const EnergyConsts &ec, cudaStream_t s) {
     const int rows = g.M[0] * g.M[1];
     const int per_cta = GREEN_THREADS / 32;
-    // one z-row per warp while that fits in 152 x 8 CTAs (the partials buffer)
-    int nb = (rows + per_cta - 1) / per_cta;
+    // eight z rows per warp before the CTA's energy/virial reduction, but at
+    // least two CTAs per SM while there are rows for them, and at most
+    // 152 x 8 CTAs (the partials buffer)
+    int nb = std::max((rows + 8 * per_cta - 1) / (8 * per_cta), std::min(2 * 152, (rows + per_cta - 1) / per_cta));
     nb = std::min(std::max(nb, 1), 152 * 8);
     const auto *rh = reinterpret_cast<const complex_t<R> *>(rho_hat);
     auto *sp = reinterpret_cast<complex_t<R> *>(spec);

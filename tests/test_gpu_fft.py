@@ -1,5 +1,5 @@
 """The hand-written Poisson solve (variant bit 3: FP32 plans, power-of-two
-mesh edges 16..128) vs the oracle's FP64 Poisson solve on the GPU's own mesh
+mesh edges 16..128 or cubic 48^3 / 96^3) vs the oracle's FP64 Poisson solve on the GPU's own mesh
 charge, vs the cuFFT path of the same plan, and end to end vs the oracle.
 
 Mesh-level bar: the field (ik) or potential (ad) within 2e-6 of its largest
@@ -55,6 +55,8 @@ MESHES = [
     ((64, 64, 64), (40.0, 40.0, 40.0)),
     ((128, 32, 16), (70.0, 19.0, 9.0)),
     ((16, 128, 128), (9.0, 66.0, 70.0)),
+    ((48, 48, 48), (30.0, 30.0, 30.0)),   # mixed radix: 12 points per lane
+    ((96, 96, 96), (60.0, 60.0, 60.0)),   # mixed radix: 24 points per lane
 ]
 
 
@@ -183,7 +185,8 @@ def test_variant_bit_refused_where_unsupported(torch):
     from paper_1702_04250_gb300 import pppm
 
     box = (20.0, 20.0, 20.0)
-    for mesh, prec in (((24, 32, 32), "fp32c"), ((32, 32, 256), "fp32"), ((32, 32, 32), "fp64")):
+    for mesh, prec in (((24, 32, 32), "fp32c"), ((32, 32, 256), "fp32"), ((32, 32, 32), "fp64"),
+                       ((96, 96, 48), "fp32c")):
         plan = pppm.PPPM(box, 10, 5, mesh, 0.9, "ik", prec, 1.0)
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(OWN_FFT)
