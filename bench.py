@@ -17,8 +17,10 @@ More is measured on rank 0 (key "extra", skipped with --no-extra): the
 2,048,001-charge water-like system (256^3, P=7, ad, FP32C; the HBM-sized
 case: per-stage times and the make_rho / fieldforce roofline fractions), the
 batch of 256 independent systems (one call, one graph; against the FP64 batch
-and against 256 single-system plans), and the real-space erfc sum of the
-bench workload (r_C = 10 A), the other half of the Ewald split.
+and against 256 single-system plans), the real-space erfc sum of the bench
+workload (r_C = 10 A), the other half of the Ewald split, the mesh chosen for
+a target accuracy with step times by mesh edge, and the differentiable energy
+of the 99,999-charge system (96^3): force step and energy with gradients.
 
 --impl reference times the FP64 CPU oracle on the same workload instead.
 Multi-GPU: the path does not shard (one system); N ranks run N independent
@@ -460,6 +462,50 @@ def real_leg(torch, flush, steps=30):
             "timing": f"{steps} calls, L2 flushed before each"}
 
 
+def autograd_leg(torch, flush, steps=30):
+    """The differentiable energy on 99,999 water-like charges (100 A cube,
+    96^3, P=5, ik): the force step and the energy with its hand-written
+    gradients (dE/dx, dE/dq: one pppm_energy_grad call, what the autograd
+    Function runs), FP32C and FP64, one graph per force step."""
+    from paper_1702_04250_gb300 import pppm
+    from paper_1702_04250_gb300.workloads import config
+
+    w = config("c5")
+    g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
+    out = {}
+    for prec in ("fp32c", "fp64"):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        x = torch.tensor(w.x, dtype=dt, device="cuda")
+        q = torch.tensor(w.q, dtype=dt, device="cuda")
+        plan = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode="ik", precision=prec, qqrd2e=w.qqrd2e, graph=True)
+        variant = plan.autotune(x, q)
+        f = torch.empty((w.n, 3), dtype=dt, device="cuda")
+        ev = torch.zeros(8, dtype=torch.float64, device="cuda")
+        t_force, _ = time_steps(torch, plan, x, q, f, ev, steps, 3, flush, sync_ranks=False)
+        s = plan.stream
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            plan.energy_grad(x, q)
+        plan.sync()
+        tot = 0.0
+        for _ in range(steps):
+            with torch.cuda.stream(s):
+                flush.zero_()
+            e0.record(s)
+            plan.energy_grad(x, q)
+            e1.record(s)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        plan.sync()
+        out[prec] = {"force_step_us": round(t_force / steps * 1e3, 1),
+                     "energy_and_gradients_us": round(tot / steps * 1e3, 1),
+                     "poisson_solve": "hand-written FFT" if variant & 8 else "cuFFT"}
+        plan.close()
+    return {"workload": "water-like 33,333 molecules (99,999 charges), 100 A cube, mesh 96^3, order 5, ik",
+            **out, "timing": f"{steps} calls each, L2 flushed before each"}
+
+
 def mesh_leg(torch, flush, steps=40):
     """Mesh choice for a target accuracy on the water-like 32,001 charges
     (r_C = 10 A, 1e-4; the error estimate runs as one FP64 kernel per mesh
@@ -655,7 +701,8 @@ def main():
 
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         line["extra"] = {"large": large_leg(torch, flush), "batch": batch_leg(torch, flush),
-                         "real_space": real_leg(torch, flush), "mesh_choice": mesh_leg(torch, flush)}
+                         "real_space": real_leg(torch, flush), "mesh_choice": mesh_leg(torch, flush),
+                         "autograd_c5": autograd_leg(torch, flush)}
     if rank == 0:
         if not args.no_cpu_baseline:
             rate, n, dt = oracle_rate(workload())
