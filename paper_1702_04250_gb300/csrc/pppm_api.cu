@@ -52,7 +52,7 @@ struct pppm_plan {
     double *G64 = nullptr;
     void *Gs = nullptr, *kvec = nullptr, *kdiff = nullptr;
     double *green_part = nullptr;
-    unsigned int *counters = nullptr;  // [0] map, [1] green
+    unsigned int *counters = nullptr;  // [0] the sort's last-block ticket
     double *ev = nullptr;              // [8]
     double *d_sf = nullptr;            // [6] setup sums
     double sf[6] = {0, 0, 0, 0, 0, 0};
@@ -783,7 +783,6 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     p->gb.kvec = p->kvec;
     p->gb.kdiff = p->kdiff;
     p->gb.part = p->green_part;
-    p->gb.counter = p->counters + 1;
     p->gb.qsum = p->sb.qsum;
     p->gb.map_part = p->sb.blk;
     p->gb.ev = p->ev;

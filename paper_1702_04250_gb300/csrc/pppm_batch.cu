@@ -248,7 +248,6 @@ int batch_build(pppm_batch *b, const double *box, const int64_t *n, const int *o
         if ((rc = bmalloc(b, &p, sizeof(double) * (7 * S.green_nb + 8)))) return rc;
         S.gb.part = (double *)p;
         S.gb.ev = (double *)p + 7 * S.green_nb;
-        S.gb.counter = S.sb.counter;
         S.gb.qsum = S.sb.qsum;
         S.gb.map_part = S.sb.blk;
         S.ec.epref = 0.5 * b->C * (h[0] * h[1] * h[2]) * (h[0] * h[1] * h[2]) / V * (double)mc.Mtot;

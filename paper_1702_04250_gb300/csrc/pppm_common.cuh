@@ -243,7 +243,6 @@ struct GreenBufs {
     const void *kvec;      // [Mx + My + Mzh] wavenumbers (step type), Nyquist negative
     const void *kdiff;     // same with the Nyquist entries zeroed (ik differentiation)
     double *part;          // [7 * nblk] per-block partial energy/virial
-    unsigned int *counter; // [1] unused
     double *qsum;          // [2] sum q, sum q^2 (written by k_energy_final)
     const double *map_part;// [2 * map_nblk] per-block sum q, sum q^2 of k_particle_map
     double *ev;            // [8] energy + virial
