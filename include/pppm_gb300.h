@@ -233,9 +233,11 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * or 128, or cubic meshes of edge 48 or 96 (PPPM_EINVAL otherwise).  Results agree with the cuFFT path to FP32
  * rounding.  Bit 4: mesh tiles of 4 points per edge instead of 8 (eight
  * times the tiles and CTAs of the sort, make_rho and the tile-staged
- * fieldforce, a larger halo share); not with bit 1.  Default: bit 4 when the
- * mesh has fewer than 304 tiles of 8^3 (two per SM), bit 0 for ik plans whose
- * n_max is at least 16 per tile, bit 3 where it is allowed.
+ * fieldforce, a larger halo share); not with bit 1.  Bit 5: make_rho's brick
+ * laid out with the strides of the largest tile (compile-time offsets); not
+ * with bit 2.  Default: bit 4 when the mesh has fewer than 304 tiles of 8^3
+ * (two per SM), bit 0 for ik plans whose n_max is at least 16 per tile, bit 3
+ * where it is allowed, bit 5.
  * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a
  * combination the plan does not allow).
  * pppm_autotune times every variant on the caller's inputs (one warm-up and

@@ -91,7 +91,10 @@ __device__ __forceinline__ void fixed_scale(const R *__restrict__ recp, int star
     ifs = ldexpf(1.0f, -e);
 }
 
-template <typename R, int P, int ACC>
+// CS: the brick's strides are those of the largest tile (TILE_B + P - 1 per
+// edge, compile-time), so every stencil point's offset is an immediate;
+// otherwise they are this tile's own extents.
+template <typename R, int P, int ACC, bool CS = false>
 __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &b, R *__restrict__ rho,
                                               int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -105,7 +108,10 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     const int Ex = tile_origin(tx + 1, g.T[0], g.M[0]) - ox + P - 1;
     const int Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - oy + P - 1;
     const int Ez = tile_origin(tz + 1, g.T[2], g.M[2]) - oz + P - 1;
-    const int vol = Ex * Ey * Ez;
+    constexpr int EB = TILE_B + P - 1;          // widest brick edge
+    const int SZ = CS ? EB : Ez;                // brick row (z) stride
+    const int SY = CS ? EB * EB : Ey * Ez;      // brick plane stride
+    const int vol = CS ? EB * EB * EB : Ex * Ey * Ez;
 
     pdl_wait();  // the sort's outputs (and its reads of the histogram) are complete
     const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
@@ -178,14 +184,14 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
                 wyk[t] = __shfl_sync(0xffffffffu, wy, (gbase + t) & 31);
             }
             if (live) {
-                const int row = (ax * Ey + ay) * Ez + az + k;
+                const int row = ax * SY + ay * SZ + az + k;
 #pragma unroll
                 for (int a = 0; a < P; ++a) {
                     const R wa = wxq[a] * wz;
 #pragma unroll
                     for (int c = 0; c < P; ++c) {
                         const R v = wa * wyk[c];
-                        const int e = row + (a * Ey + c) * Ez;
+                        const int e = row + a * SY + c * SZ;
                         if (ACC == ACC_FIXED) {
                             // t = v s = hi + lo / 2^16 with full-rate float ops:
                             // adding 1.5 * 2^23 rounds |t| < 2^22 to an integer
@@ -230,7 +236,7 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
                 int gy = oy - g.rlo + ey;
                 gy += (gy < 0) ? g.M[1] : 0;
                 gy -= (gy >= g.M[1]) ? g.M[1] : 0;
-                const int e = (ex * Ey + ey) * Ez + lz;
+                const int e = ex * SY + ey * SZ + lz;
                 R v;
                 if (ACC == ACC_FIXED) {
                     // normalise in integers (exact), then one FP32 rounding
@@ -693,16 +699,16 @@ __global__ void __launch_bounds__(RHO_THREADS) k_batch_make_rho_w(const BatchSys
     make_rho_w_body<P>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);
 }
 
-template <typename R, int P, int ACC>
+template <typename R, int P, int ACC, bool CS = false>
 __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b, R *__restrict__ rho) {
-    make_rho_body<R, P, ACC>(g, b, rho, blockIdx.x);
+    make_rho_body<R, P, ACC, CS>(g, b, rho, blockIdx.x);
 }
 
 template <typename R, int P, int ACC>
 __global__ void __launch_bounds__(RHO_THREADS) k_batch_make_rho(const BatchSys<R> *__restrict__ sys, BatchList bl) {
     const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
     const BatchSys<R> &S = sys[bl.ids[e]];
-    make_rho_body<R, P, ACC>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);
+    make_rho_body<R, P, ACC, true>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);  // compile-time brick strides
 }
 
 template <typename R, int P>
@@ -730,15 +736,19 @@ static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, int acc, cudaS
         }
     }
     if constexpr (std::is_same<R, float>::value) {
-        if (acc == ACC_FIXED && g.rho_copies) {
+        if (acc == ACC_FIXED && g.rho_copies == 1) {
             launch_one(k_make_rho_fixed<P>, pdl, dim3(g.ntiles), GBrick<P>::BYTES, s, g, b, rho, GBrick<P>::NT);
             return;
         }
     }
-    if (acc == ACC_FIXED)
-        launch_one(k_make_rho<R, P, ACC_FIXED>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
-    else
-        launch_one(k_make_rho<R, P, ACC_NATIVE>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
+    const bool cs = g.rho_copies == 2;  // one brick with compile-time strides
+    if (acc == ACC_FIXED) {
+        if (cs) launch_one(k_make_rho<R, P, ACC_FIXED, true>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
+        else launch_one(k_make_rho<R, P, ACC_FIXED>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
+    } else {
+        if (cs) launch_one(k_make_rho<R, P, ACC_NATIVE, true>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
+        else launch_one(k_make_rho<R, P, ACC_NATIVE>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
+    }
 }
 
 template <typename R, int P>

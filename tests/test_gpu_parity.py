@@ -196,7 +196,7 @@ def test_orders_on_ragged_mesh(torch, P, mode, prec):
     xo, qo = oracle_inputs(x, q, prec)
     ref = OraclePPPM(box, mesh, P, g, mode, 2.0).compute(xo, qo)
     check_all(f, ev, ref, prec, f"P={P} {mode}")
-    plan.set_variant(0)  # 8^3 tiles (uneven: 7/7/6, 6/6/5, 6/6)
+    plan.set_variant(32 if prec == "fp32c" else 0)  # 8^3 tiles (uneven: 7/7/6, 6/6/5, 6/6)
     dt = torch.float64 if prec == "fp64" else torch.float32
     f0, ev0 = plan.compute(torch.tensor(x, dtype=dt, device="cuda"), torch.tensor(q, dtype=dt, device="cuda"))
     plan.sync()
@@ -344,17 +344,17 @@ def test_fieldforce_variants_and_autotune(torch, c2_refs, mode):
     plan = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode, "fp32c", w.qqrd2e)
     # fieldforce per particle / tile-staged x make_rho one / four brick copies
     # x cuFFT / hand-written Poisson solve x 8^3 / 4^3 tiles
-    for v in (0, 1, 4, 5, 8, 9, 12, 13, 16, 17, 20, 25, 29):
+    for v in (0, 1, 4, 5, 8, 9, 12, 13, 16, 17, 20, 25, 29, 32, 41, 57):
         plan.set_variant(v)
         f, ev = plan.compute(x, q)
         plan.sync()
         check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"variant {v} {mode}")
     choice = plan.autotune(x, q)
-    assert choice & ~0x1D == 0  # bits 0, 2, 3, 4
+    assert choice & ~0x3D == 0 and not (choice & 4 and choice & 32)  # bits 0, 2, 3, 4, 5
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"autotuned {choice}")
-    for bad in (2, 3, 6, 7, 10, 18, 32):  # long tiles are reserved; unknown bits
+    for bad in (2, 3, 6, 7, 10, 18, 36, 64):  # long tiles are reserved; exclusive pairs; unknown bits
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(bad)
     p64 = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode, "fp64", w.qqrd2e)
@@ -378,7 +378,7 @@ def test_order7_variants(torch, mode):
     q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
     plan = pppm.PPPM(w.box, w.n, 7, w.mesh, g, mode, "fp32c", w.qqrd2e)
     assert plan.info()["tile"] == 8 and plan.info()["ntiles"] == 512
-    for v in (0, 1, 4, 5, 8, 13, 16, 29):
+    for v in (0, 1, 4, 5, 8, 13, 16, 29, 32, 41):
         plan.set_variant(v)
         f, ev = plan.compute(x, q)
         plan.sync()
@@ -387,7 +387,7 @@ def test_order7_variants(torch, mode):
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(bad)
     choice = plan.autotune(x, q)
-    assert choice & ~0x1D == 0
+    assert choice & ~0x3D == 0
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, "fp32c", f"P=7 autotuned {choice}")
