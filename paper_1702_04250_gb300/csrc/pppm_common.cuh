@@ -54,7 +54,8 @@ struct Geom {
     R coef[MAXP][MAXP];   // coef[k][l]: weight of stencil point k, power l of delta
     R dcoef[MAXP][MAXP];  // d/ddelta of the same polynomials
     int ff_tiled;         // fieldforce variant: 0 per-particle through L1, 1 tile-staged brick
-    int rho_copies;       // FP32C make_rho variant: 0 one shared brick, 1 four interleaved copies
+    int rho_copies;       // make_rho brick: 0 one, tile strides; 1 four interleaved copies (FP32C);
+                          // 2 one, strides of the largest tile
     int lut_bins;         // coefficient table entries (0: exact polynomials), see pppm_set_lut
     int launch_flags;     // host side: LF_* launch options of this step
     int planar_stride;    // ik field layout: 0 interleaved (Ex,Ey,Ez,pad); > 0 three planes this far apart
