@@ -509,9 +509,10 @@ def autograd_leg(torch, flush, steps=30):
 def mesh_leg(torch, flush, steps=40):
     """Mesh choice for a target accuracy on the water-like 32,001 charges
     (r_C = 10 A, 1e-4; the error estimate runs as one FP64 kernel per mesh
-    tried), and why FFT-friendly sizes matter: the same FP32C ik step on
-    mesh edges 64 (a power of two), 67 and 71 (primes), 70 (2 5 7) and 72
-    (2^3 3^2), with g held fixed."""
+    tried), why FFT-friendly sizes matter (the same FP32C ik step on mesh
+    edges 64 (a power of two), 67 and 71 (primes), 70 (2 5 7) and 72
+    (2^3 3^2), with g held fixed), and which order meets the target fastest
+    (orders 3-7, each with its chosen mesh)."""
     from paper_1702_04250_gb300 import pppm
     from paper_1702_04250_gb300.workloads import config
 
@@ -537,8 +538,20 @@ def mesh_leg(torch, flush, steps=40):
         sizes[str(m)] = {"us_per_step": round(tot / steps * 1e3, 1),
                          "est_rms_force_err": float(f"{pppm.kspace_error(w.box, (m,) * 3, w.order, g, w.n, q2):.4g}")}
         plan.close()
+    # the order that meets the target fastest (a larger stencil allows a coarser mesh)
+    orders = []
+    for order in (3, 4, 5, 6, 7):
+        for name, kind in (("primes_le_7", pppm.FFT_SMOOTH), ("powers_of_two", pppm.FFT_POW2)):
+            mesh, go, err = pppm.choose_mesh(w.box, w.n, q2, order, w.r_cut, w.rel_acc, kind)
+            plan = pppm.PPPM(w.box, w.n, order, mesh, go, mode="ik", precision="fp32c", qqrd2e=w.qqrd2e,
+                             graph=True)
+            plan.autotune(x, q)
+            tot, _ = time_steps(torch, plan, x, q, f, ev, steps, 3, flush, sync_ranks=False)
+            orders.append({"order": order, "sizes": name, "mesh": list(mesh), "est_rms_force_err": float(f"{err:.4g}"),
+                           "us_per_step": round(tot / steps * 1e3, 1)})
+            plan.close()
     return {"workload": "water-like 32,001 charges, 68 A cube, P=5, ik, r_C = 10 A, target 1e-4",
-            "choice": choice, "step_by_mesh_edge_fp32c": sizes,
+            "choice": choice, "step_by_mesh_edge_fp32c": sizes, "order_sweep_fp32c": orders,
             "timing": f"{steps} graph steps per mesh, L2 flushed before each"}
 
 
