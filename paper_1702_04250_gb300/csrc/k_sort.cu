@@ -89,17 +89,31 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
     __shared__ bool last;
     if (rho_zero) clear_mesh<R>(rho_zero, mtot, lb, nlb);
     const int i = lb * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     R qs = R(0), qq = R(0);
+    int tile = -1 - lane;  // a key no other lane or tile has
+    uint32_t packed = 0;
     if (i < n) {
         R xi[3], qi;
         if (!load_particle<R>(x, q, i, xi, qi)) atomicOr(b.err, ERR_NONFINITE);
         int a[3];
         R d[3];
         anchors<R>(g, xi, a, d);
-        b.rank[i] = atomicAdd(&b.tile_count[tile_index<R>(g, a)], 1);
-        b.anchor[i] = pack_anchor(a[0], a[1], a[2]);
+        tile = tile_index<R>(g, a);
+        packed = pack_anchor(a[0], a[1], a[2]);
         qs = qi;
         qq = qi * qi;
+    }
+    // ranks within the tile: one atomic per distinct tile of the warp (the
+    // atoms of a molecule usually share one), handed out in lane order
+    const unsigned int peers = __match_any_sync(0xffffffffu, tile);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (i < n && lane == leader) base = atomicAdd(&b.tile_count[tile], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (i < n) {
+        b.rank[i] = base + __popc(peers & ((1u << lane) - 1u));
+        b.anchor[i] = packed;
     }
     // per-block sums of q and q^2, reduced later off the critical path
     double s1, s2;
@@ -138,7 +152,7 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
     } else {
         for (int k = lo; k < hi; ++k) local += __ldcg(&b.tile_count[k]);
     }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5;
     int incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
