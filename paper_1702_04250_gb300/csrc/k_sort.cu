@@ -239,6 +239,8 @@ __device__ __forceinline__ void scatter_body(const Geom<R> &g, int n, const R *_
         anchors<R>(g, xi, a, d);
     }
     pdl_wait();
+    // this particle's rank from particle_map, requested before the scan
+    const int rank = (i < n) ? b.rank[i] : 0;
     const int *starts = b.tile_start;
     if (!big) {
         scan_tiles_smem(b.tile_count, g.ntiles, sh_start, sh_warp);
@@ -259,10 +261,9 @@ __device__ __forceinline__ void scatter_body(const Geom<R> &g, int n, const R *_
             d[k] = lo + (bin + R(0.5)) / K;
         }
     }
-    const uint32_t packed = b.anchor[i];  // same computation as k_particle_map
-    int s[3];
-    unpack_anchor(packed, s[0], s[1], s[2]);
-    const int dest = starts[tile_index<R>(g, s)] + b.rank[i];
+    // the anchor is particle_map's: the same function of the same inputs
+    const uint32_t packed = pack_anchor(a[0], a[1], a[2]);
+    const int dest = starts[tile_index<R>(g, a)] + rank;
     if ((unsigned int)dest >= (unsigned int)n) {  // a stale histogram: skip, report
         atomicOr(b.err, ERR_INTERNAL);
         return;
