@@ -113,6 +113,14 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     const int SY = CS ? EB * EB : Ey * Ez;      // brick plane stride
     const int vol = CS ? EB * EB * EB : Ex * Ey * Ez;
 
+    // the brick is this CTA's own shared memory: cleared while the sort may
+    // still be finishing (ordered before the atomics by the barrier below)
+    {
+        const int words = (ACC == ACC_FIXED ? 2 * vol : vol * (int)(sizeof(R) / 4));
+        int *w = reinterpret_cast<int *>(smem_raw);
+        for (int e = threadIdx.x; e < words; e += blockDim.x) w[e] = 0;
+    }
+
     pdl_wait();  // the sort's outputs (and its reads of the histogram) are complete
     const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
     if (threadIdx.x == 0) b.tile_count[tile] = 0;  // histogram is clean for the next step
@@ -128,13 +136,7 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     // |sum v s| < 2^30 (so the hi word cannot overflow)
     float fs = 1.0f, ifs = 1.0f;
     if (ACC == ACC_FIXED) fixed_scale<R>(recp, start, end, (float)g.ivcell, fs, ifs);
-
-    {
-        const int words = (ACC == ACC_FIXED ? 2 * vol : vol * (int)(sizeof(R) / 4));
-        int *w = reinterpret_cast<int *>(smem_raw);
-        for (int e = threadIdx.x; e < words; e += blockDim.x) w[e] = 0;
-    }
-    __syncthreads();
+    else __syncthreads();  // (fixed_scale ends with one)
 
     // GS lanes serve one particle (32 / GS particles per warp; the lanes past
     // the last whole group idle).  GS = P, except 8 at P = 7: the warp holds
