@@ -37,6 +37,7 @@ constexpr int RHO_THREADS = 256;
 constexpr int GROUP = 8;
 constexpr int ACC_NATIVE = 0, ACC_FIXED = 1;
 constexpr int LO_CHUNK = 32768;
+constexpr int ORDER_CHUNK = RHO_THREADS;  // particles per bank-ordered sub-chunk (one per thread)
 constexpr float MAGIC = 12582912.0f;      // 1.5 * 2^23
 constexpr int MAGIC_BITS = 0x4B400000;    // its bit pattern
 
@@ -113,12 +114,21 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     const int SY = CS ? EB * EB : Ey * Ez;      // brick plane stride
     const int vol = CS ? EB * EB * EB : Ex * Ey * Ez;
 
+    // bank-ordering scratch: particles of a sub-chunk counted by the shared
+    // bank of their first stencil point, then listed in that order
+    __shared__ int s_bins[32], s_off[32];
+    __shared__ int s_list[ORDER_CHUNK];
+
     // the brick is this CTA's own shared memory: cleared while the sort may
     // still be finishing (ordered before the atomics by the barrier below)
     {
         const int words = (ACC == ACC_FIXED ? 2 * vol : vol * (int)(sizeof(R) / 4));
+        int4 *w4 = reinterpret_cast<int4 *>(smem_raw);
+        const int n4 = words >> 2;
+        for (int e = threadIdx.x; e < n4; e += blockDim.x) w4[e] = make_int4(0, 0, 0, 0);
         int *w = reinterpret_cast<int *>(smem_raw);
-        for (int e = threadIdx.x; e < words; e += blockDim.x) w[e] = 0;
+        for (int e = 4 * n4 + (int)threadIdx.x; e < words; e += blockDim.x) w[e] = 0;
+        if (threadIdx.x < 32) s_bins[threadIdx.x] = 0;
     }
 
     pdl_wait();  // the sort's outputs (and its reads of the histogram) are complete
@@ -148,8 +158,9 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     const int k = lane % GS;                     // z stencil offset of this lane
     const int gbase = lane - k;
     const bool lane_on = lane < NG * GS && k < P;
-    const int grp = (threadIdx.x >> 5) * NG + lane / GS;  // particle slot in the CTA
-    const int ngrp = (blockDim.x >> 5) * NG;
+    const int q = lane / GS;                     // this group's place in its warp
+    const int warp = threadIdx.x >> 5;
+    const int ngrp = (blockDim.x >> 5) * NG;     // particle slots per pass of the CTA
     const R qscale = (ACC == ACC_FIXED) ? (R)(g.ivcell * (R)fs) : g.ivcell;
     // this lane's polynomial (stencil offset k), held in registers for the CTA
     R ck[P];
@@ -158,98 +169,141 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
 
     for (int chunk = start; chunk < end; chunk += LO_CHUNK) {
         const int cend = min(end, chunk + LO_CHUNK);
-        // warp-uniform trip count: all 32 lanes take part in the shuffles
-        for (int base = chunk; base < cend; base += ngrp) {
-            const int j = base + grp;
-            const bool live = lane_on && j < cend;
-            R dx = R(0), dy = R(0), dz = R(0), qv = R(0);
-            int ax = 0, ay = 0, az = 0;
-            if (live) {
-                const vec4_t<R> r = reinterpret_cast<const vec4_t<R> *>(recp)[j];
-                dx = r.x; dy = r.y; dz = r.z; qv = r.w * qscale;
-                unpack_anchor(b.cell[j], ax, ay, az);
-                ax -= ox; ay -= oy; az -= oz;        // local anchor in [0, tile size)
-                if ((unsigned)ax > (unsigned)(Ex - P) || (unsigned)ay > (unsigned)(Ey - P) ||
-                    (unsigned)az > (unsigned)(Ez - P)) {  // not this tile's particle: skip, report
-                    if (k == 0) atomicOr(b.err, ERR_INTERNAL);
-                    ax = ay = az = 0;
-                    qv = R(0);
+        for (int sub = chunk; sub < cend; sub += ORDER_CHUNK) {
+            const int nch = min(ORDER_CHUNK, cend - sub);
+            // Bank order: a group's z run starts at brick word row0 = anchor
+            // index, so its atomics hit banks row0 + k + (a, c offset) mod 32
+            // and two groups of one warp collide iff their row0 are closer
+            // than P mod 32, whatever (a, c).  Counting-sort the sub-chunk by
+            // row0 mod 32 and hand the warp's groups particles a quarter (an
+            // NG-th) of the sorted list apart: their runs then start about
+            // 32 / NG >= P banks apart.  The accumulation is exact integer
+            // arithmetic (ACC_FIXED), so the order changes no result bit.
+            {
+                int key = 0, rank = 0;
+                if ((int)threadIdx.x < nch) {
+                    int ax, ay, az;
+                    unpack_anchor(b.cell[sub + threadIdx.x], ax, ay, az);
+                    key = ((ax - ox) * SY + (ay - oy) * SZ + (az - oz)) & 31;
+                    rank = atomicAdd(&s_bins[key], 1);
                 }
+                __syncthreads();
+                if (threadIdx.x < 32) {
+                    const int v = s_bins[threadIdx.x];
+                    int incl = v;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                        if ((int)threadIdx.x >= o) incl += u;
+                    }
+                    s_off[threadIdx.x] = incl - v;
+                    s_bins[threadIdx.x] = 0;  // clean for the next sub-chunk
+                }
+                __syncthreads();
+                if ((int)threadIdx.x < nch) s_list[s_off[key] + rank] = threadIdx.x;
+                __syncthreads();
             }
-            // lane k evaluates the three weights of stencil offset k (an idle
-            // lane's shuffle source wraps within the warp; it is not used)
-            const R wx = horner<R, P>(ck, dx), wy = horner<R, P>(ck, dy), wz = horner<R, P>(ck, dz);
-            R wxq[P], wyk[P];
+            const int Q = (nch + NG - 1) / NG;   // sorted positions per group place
+            // warp-uniform trip count: all 32 lanes take part in the shuffles
+            for (int base = 0; base < NG * Q; base += ngrp) {
+                const int col = base / NG + warp;   // slot (base + warp NG + q) -> position q Q + col
+                const int pos = q * Q + col;
+                const bool live = lane_on && col < Q && pos < nch;
+                R dx = R(0), dy = R(0), dz = R(0), qv = R(0);
+                int ax = 0, ay = 0, az = 0;
+                if (live) {
+                    const int j = sub + s_list[pos];
+                    const vec4_t<R> r = reinterpret_cast<const vec4_t<R> *>(recp)[j];
+                    dx = r.x; dy = r.y; dz = r.z; qv = r.w * qscale;
+                    unpack_anchor(b.cell[j], ax, ay, az);
+                    ax -= ox; ay -= oy; az -= oz;        // local anchor in [0, tile size)
+                    if ((unsigned)ax > (unsigned)(Ex - P) || (unsigned)ay > (unsigned)(Ey - P) ||
+                        (unsigned)az > (unsigned)(Ez - P)) {  // not this tile's particle: skip, report
+                        if (k == 0) atomicOr(b.err, ERR_INTERNAL);
+                        ax = ay = az = 0;
+                        qv = R(0);
+                    }
+                }
+                // lane k evaluates the three weights of stencil offset k (an idle
+                // lane's shuffle source wraps within the warp; it is not used)
+                const R wx = horner<R, P>(ck, dx), wy = horner<R, P>(ck, dy), wz = horner<R, P>(ck, dz);
+                R wxq[P], wyk[P];
 #pragma unroll
-            for (int t = 0; t < P; ++t) {
-                wxq[t] = __shfl_sync(0xffffffffu, wx, (gbase + t) & 31) * qv;
-                wyk[t] = __shfl_sync(0xffffffffu, wy, (gbase + t) & 31);
-            }
-            if (live) {
-                const int row = ax * SY + ay * SZ + az + k;
+                for (int t = 0; t < P; ++t) {
+                    wxq[t] = __shfl_sync(0xffffffffu, wx, (gbase + t) & 31) * qv;
+                    wyk[t] = __shfl_sync(0xffffffffu, wy, (gbase + t) & 31);
+                }
+                if (live) {
+                    const int row = ax * SY + ay * SZ + az + k;
 #pragma unroll
-                for (int a = 0; a < P; ++a) {
-                    const R wa = wxq[a] * wz;
+                    for (int a = 0; a < P; ++a) {
+                        const R wa = wxq[a] * wz;
 #pragma unroll
-                    for (int c = 0; c < P; ++c) {
-                        const R v = wa * wyk[c];
-                        const int e = row + a * SY + c * SZ;
-                        if (ACC == ACC_FIXED) {
-                            // t = v s = hi + lo / 2^16 with full-rate float ops:
-                            // adding 1.5 * 2^23 rounds |t| < 2^22 to an integer
-                            // held in the mantissa bits
-                            const float t = (float)v;
-                            const float r1 = __fadd_rn(t, MAGIC);
-                            const float fr = __fadd_rn(t, -__fadd_rn(r1, -MAGIC));  // exact
-                            const float r2 = __fmaf_rn(fr, 65536.0f, MAGIC);
-                            atomicAdd(&acch[e], __float_as_int(r1) - MAGIC_BITS);
-                            atomicAdd(&accl[e], (unsigned int)(__float_as_int(r2) - MAGIC_BITS));
-                        } else {
-                            atomicAdd(&accr[e], v);
+                        for (int c = 0; c < P; ++c) {
+                            const int e = row + a * SY + c * SZ;
+                            if (ACC == ACC_FIXED) {
+                                // t = wa wy s = hi + lo / 2^16, the product never
+                                // rounded on its own: adding 1.5 * 2^23 inside the
+                                // FMA rounds |t| < 2^22 to an integer held in the
+                                // mantissa bits, and the second FMA takes the exact
+                                // remainder (|.| <= 1/2) before its one rounding
+                                const float fa = (float)wa, fy = (float)wyk[c];
+                                const float r1 = __fmaf_rn(fa, fy, MAGIC);
+                                const float hi = __fadd_rn(r1, -MAGIC);  // exact
+                                const float fr = __fmaf_rn(fa, fy, -hi);
+                                const float r2 = __fmaf_rn(fr, 65536.0f, MAGIC);
+                                atomicAdd(&acch[e], __float_as_int(r1) - MAGIC_BITS);
+                                atomicAdd(&accl[e], (unsigned int)(__float_as_int(r2) - MAGIC_BITS));
+                            } else {
+                                atomicAdd(&accr[e], wa * wyk[c]);
+                            }
                         }
                     }
                 }
             }
+            __syncthreads();  // the list is rewritten by the next sub-chunk
         }
         if (ACC == ACC_FIXED && cend < end) {  // fold lo into hi before it can overflow
-            __syncthreads();
             for (int e = threadIdx.x; e < vol; e += blockDim.x) {
                 const int l = (int)accl[e];  // signed sum of fractions in [-2^15, 2^15] each
                 acch[e] += l >> 16;          // floor division by 2^16
                 accl[e] = (unsigned int)(l & 0xffff);
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
 
-    // flush the brick (tile + halo) into the global mesh: 16 lanes per z row
-    // (Ez <= 14), 16 rows per pass; every wrap is a single conditional since
+    // flush the brick (tile + halo) into the global mesh: thread (ry, lz) owns
+    // brick column (y = ry, z = lz) -- edges are at most TILE_B + P - 1 <= 16
+    // points -- and walks it along x; every wrap is a single conditional since
     // the brick is never wider than the mesh plus one period.
+    static_assert(TILE_B + 7 - 1 <= 16 && RHO_THREADS == 256, "one brick column per thread");
     const int lz = threadIdx.x & 15, ry = threadIdx.x >> 4;
-    if (lz < Ez) {
+    if (lz < Ez && ry < Ey) {
         int gz = oz - g.rlo + lz;
         gz += (gz < 0) ? g.M[2] : 0;
         gz -= (gz >= g.M[2]) ? g.M[2] : 0;
+        int gy = oy - g.rlo + ry;
+        gy += (gy < 0) ? g.M[1] : 0;
+        gy -= (gy >= g.M[1]) ? g.M[1] : 0;
+        R *__restrict__ col = rho + gy * g.M[2] + gz;
+        const int plane = g.M[1] * g.M[2];
+        const int e0 = ry * SZ + lz;
+        int gx = ox - g.rlo;
+        gx += (gx < 0) ? g.M[0] : 0;
         for (int ex = 0; ex < Ex; ++ex) {
-            int gx = ox - g.rlo + ex;
-            gx += (gx < 0) ? g.M[0] : 0;
-            gx -= (gx >= g.M[0]) ? g.M[0] : 0;
-            for (int ey = ry; ey < Ey; ey += RHO_THREADS / 16) {
-                int gy = oy - g.rlo + ey;
-                gy += (gy < 0) ? g.M[1] : 0;
-                gy -= (gy >= g.M[1]) ? g.M[1] : 0;
-                const int e = ex * SY + ey * SZ + lz;
-                R v;
-                if (ACC == ACC_FIXED) {
-                    // normalise in integers (exact), then one FP32 rounding
-                    const int l = (int)accl[e];
-                    const int h = acch[e] + (l >> 16);
-                    v = (R)(fmaf((float)(l & 0xffff), 1.0f / 65536.0f, (float)h) * ifs);
-                } else {
-                    v = accr[e];
-                }
-                if (v != R(0)) atomicAdd(&rho[(gx * g.M[1] + gy) * g.M[2] + gz], v);
+            const int e = e0 + ex * SY;
+            R v;
+            if (ACC == ACC_FIXED) {
+                // normalise in integers (exact), then one FP32 rounding
+                const int l = (int)accl[e];
+                const int h = acch[e] + (l >> 16);
+                v = (R)(fmaf((float)(l & 0xffff), 1.0f / 65536.0f, (float)h) * ifs);
+            } else {
+                v = accr[e];
             }
+            if (v != R(0)) atomicAdd(col + gx * plane, v);
+            gx = (gx + 1 == g.M[0]) ? 0 : gx + 1;
         }
     }
 }
