@@ -20,6 +20,7 @@ namespace pppm {
 
 constexpr int MAP_THREADS = 256;
 constexpr int SMALL_TILES = 4096;  // histogram scanned per scatter block up to this many tiles
+constexpr int SCAN_BATCH = 4;      // histogram loads in flight per thread in the last-block scan (keeps 32 registers)
 
 template <typename R>
 __device__ __forceinline__ bool load_particle(const R *__restrict__ x, const R *__restrict__ q,
@@ -138,19 +139,32 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
 
     // ---- last block: exclusive scan of the tile histogram ---------------
     const int nt = g.ntiles;
-    // chunks of a multiple of 4 tiles: whole chunks load as int4 (the
-    // histogram comes from cudaMalloc, 16-byte aligned)
+    // each thread owns a chunk of a multiple of 4 tiles (whole chunks load as
+    // int4; the histogram comes from cudaMalloc, 16-byte aligned) and keeps
+    // SCAN_BATCH loads in flight: this block alone runs while the rest of the
+    // step waits, so its time is L2 round trips, not bandwidth
     const int chunk = ((nt + blockDim.x - 1) / blockDim.x + 3) & ~3;
     const int lo = min(nt, (int)threadIdx.x * chunk), hi = min(nt, lo + chunk);
+    const bool whole = (hi - lo == chunk);
+    const int4 *c4 = reinterpret_cast<const int4 *>(b.tile_count + lo);
+    const int n4 = chunk / 4;
     int local = 0;
-    if (hi - lo == chunk) {
-        const int4 *c4 = reinterpret_cast<const int4 *>(b.tile_count + lo);
-        for (int k = 0; k < chunk / 4; ++k) {
-            const int4 v = __ldcg(c4 + k);
-            local += v.x + v.y + v.z + v.w;
+    if (whole) {
+        for (int k0 = 0; k0 < n4; k0 += SCAN_BATCH) {
+            int4 v[SCAN_BATCH];
+#pragma unroll
+            for (int u = 0; u < SCAN_BATCH; ++u) v[u] = (k0 + u < n4) ? __ldcg(c4 + k0 + u) : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < SCAN_BATCH; ++u) local += v[u].x + v[u].y + v[u].z + v[u].w;
         }
     } else {
-        for (int k = lo; k < hi; ++k) local += __ldcg(&b.tile_count[k]);
+        for (int k0 = lo; k0 < hi; k0 += SCAN_BATCH) {
+            int v[SCAN_BATCH];
+#pragma unroll
+            for (int u = 0; u < SCAN_BATCH; ++u) v[u] = (k0 + u < hi) ? __ldcg(&b.tile_count[k0 + u]) : 0;
+#pragma unroll
+            for (int u = 0; u < SCAN_BATCH; ++u) local += v[u];
+        }
     }
     const int w = threadIdx.x >> 5;
     int incl = local;
@@ -171,10 +185,36 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
     }
     __syncthreads();
     int run = sh_scan[w] + incl - local;
-    for (int k = lo; k < hi; ++k) {
-        const int c = __ldcg(&b.tile_count[k]);
-        b.tile_start[k] = run;
-        run += c;
+    if (whole) {
+        for (int k0 = 0; k0 < n4; k0 += SCAN_BATCH) {
+            int4 v[SCAN_BATCH];
+#pragma unroll
+            for (int u = 0; u < SCAN_BATCH; ++u) v[u] = (k0 + u < n4) ? __ldcg(c4 + k0 + u) : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < SCAN_BATCH; ++u) {
+                if (k0 + u < n4) {
+                    int *t = b.tile_start + lo + 4 * (k0 + u);
+                    t[0] = run;
+                    t[1] = run + v[u].x;
+                    t[2] = run + v[u].x + v[u].y;
+                    t[3] = run + v[u].x + v[u].y + v[u].z;
+                    run += v[u].x + v[u].y + v[u].z + v[u].w;
+                }
+            }
+        }
+    } else {
+        for (int k0 = lo; k0 < hi; k0 += SCAN_BATCH) {
+            int v[SCAN_BATCH];
+#pragma unroll
+            for (int u = 0; u < SCAN_BATCH; ++u) v[u] = (k0 + u < hi) ? __ldcg(&b.tile_count[k0 + u]) : 0;
+#pragma unroll
+            for (int u = 0; u < SCAN_BATCH; ++u) {
+                if (k0 + u < hi) {
+                    b.tile_start[k0 + u] = run;
+                    run += v[u];
+                }
+            }
+        }
     }
     if (hi == nt && lo < hi) b.tile_start[nt] = run;
     if (threadIdx.x == 0) *b.counter = 0u;

@@ -103,6 +103,33 @@ def test_anchor_and_sort(c1_fp64_ik):
     np.testing.assert_array_equal(sorted_tiles, owner)
 
 
+def test_sort_many_tiles_ragged_scan(torch):
+    """More tiles than the per-block shared-memory scan holds (17 x 17 x 18 =
+    5,202 tiles of a 136 x 136 x 144 mesh): the last particle_map block scans
+    the histogram, 217 threads with chunks of 24 tiles and one partial chunk
+    of 18.  Exact anchors (FP64), a permutation, tile offsets equal to the
+    exclusive scan of the brute-force tile counts, every particle in its tile."""
+    box, mesh, P = (40.0, 40.0, 42.0), (136, 136, 144), 5
+    x, q = uniform_alternating(60_001, box, seed=29)
+    plan, *_ = run(torch, box, mesh, P, 0.6, "ik", "fp64", x, q)
+    h = np.array(box) / np.array(mesh)
+    u = wrap_positions(x, box) / h
+    ref = np.stack([stencil(u[:, d], P, mesh[d])[0][:, (P - 1) // 2] for d in range(3)], axis=1)
+    np.testing.assert_array_equal(plan.get_array("anchor"), ref)
+    perm = plan.get_array("perm")
+    assert np.array_equal(np.sort(perm), np.arange(len(q)))
+    inf = plan.info()
+    T = [(m + inf["tile"] - 1) // inf["tile"] for m in mesh]
+    assert T[0] * T[1] * T[2] == 5202
+    tile = lambda a, d: ((a + 1) * T[d] - 1) // mesh[d]
+    tid = (tile(ref[:, 0], 0) * T[1] + tile(ref[:, 1], 1)) * T[2] + tile(ref[:, 2], 2)
+    counts = np.bincount(tid, minlength=T[0] * T[1] * T[2])
+    ts = plan.get_array("tilestart")
+    np.testing.assert_array_equal(ts, np.concatenate([[0], np.cumsum(counts)]))
+    np.testing.assert_array_equal(tid[perm], np.repeat(np.arange(len(counts)), counts))
+    plan.close()
+
+
 def test_rho_green_field(c1_fp64_ik):
     w, g, plan, f, ev, o, ref = c1_fp64_ik
     rho = plan.get_array("rho")
