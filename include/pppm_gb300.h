@@ -240,10 +240,11 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * where it is allowed, bit 5.
  * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a
  * combination the plan does not allow).
- * pppm_autotune times every variant on the caller's inputs (one warm-up and
- * five timed pppm_compute steps each, synchronous, graph mode off while it
- * runs), keeps the fastest, writes its bitmask to choice_out (nullable), and
- * leaves f holding a valid result.  Both drop any captured graph. */
+ * pppm_autotune times every variant on the caller's inputs (two warm-up and
+ * ten timed pppm_compute steps each, synchronous, as CUDA graphs when the
+ * plan's graph mode is on; a variant scores its fastest step), keeps the
+ * fastest, writes its bitmask to choice_out (nullable), and leaves f holding
+ * a valid result.  Both drop any captured graph. */
 int pppm_set_variant(pppm_plan *p, int variants);
 
 /* Lookup-table stencil coefficients (Sec. 3.1 "precompute", Table 1's LUT-500

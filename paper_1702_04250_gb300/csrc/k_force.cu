@@ -412,7 +412,10 @@ static void launch_ff(const Geom<R> &g, int64_t n, const SortBufs &b, const R *f
     SelfCoef sc;
     for (int i = 0; i < 6; ++i) sc.c[i] = c[i];
     const bool pdl = (g.launch_flags & LF_PDL_FF) != 0;
-    if (g.ff_tiled) {
+    // the energy gradient (MODE 2) gathers a scalar potential, which reads
+    // best through L1 on every measured workload; the plan's tuned variant
+    // is chosen on force steps and applies to MODE 0 / 1 only
+    if (g.ff_tiled && MODE != 2) {
         if (pdl)
             launch_pdl(k_fieldforce_tiled<R, P, MODE>, dim3(g.ntiles), dim3(FF_THREADS), ff_brick_bytes<R, P, MODE>(),
                        s, g, b, field, f, dq, qC, sc, gs, gb);
