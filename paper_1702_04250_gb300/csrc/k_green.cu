@@ -24,6 +24,7 @@
 namespace pppm {
 
 constexpr int GREEN_THREADS = 256;
+constexpr int GREEN_ZU = 4;  // spectrum elements a lane keeps in flight along a z-row
 
 // ---------------------------------------------------------------------------
 // Setup (FP64): G on the half spectrum and the ad self-force sums
@@ -190,44 +191,63 @@ __device__ __forceinline__ void green_body(const Geom<R> &g, const complex_t<R> 
     const int lane = threadIdx.x & 31;
     const int wrow = threadIdx.x >> 5;
     R acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    // one thread per spectrum element in z-rows: row = (kx, ky), lanes along kz
-    const int zlanes = (Mzh >= 32) ? 32 : Mzh;
+    // one warp per z-row: row = (kx, ky), lanes along kz
     const int rows_per_cta = GREEN_THREADS / 32;
     for (int row = lb * rows_per_cta + wrow; row < rows; row += nlb * rows_per_cta) {
         const int ix = row / My, iy = row - ix * My;
         const R kx = kv[ix], ky = kv[Mx + iy];
         const R dkx = kd[ix], dky = kd[Mx + iy];
         const R kxy2 = kx * kx + ky * ky;
-        for (int iz = lane; iz < Mzh && lane < zlanes; iz += 32) {
-            const int e = row * Mzh + iz;
-            const complex_t<R> r = rhat[e];
-            const R G = Gs[e];
-            const R pr = G * r.x, pi = G * r.y;
-            if (IK) {
-                // E_a = -i k_a G rho_hat / M  ->  (k_a pi, -k_a pr)
-                const R dkz = kd[Mx + My + iz];
-                complex_t<R> o;
-                o.x = dkx * pi; o.y = -dkx * pr; spec[e] = o;
-                o.x = dky * pi; o.y = -dky * pr; spec[total + e] = o;
-                o.x = dkz * pi; o.y = -dkz * pr; spec[2 * total + e] = o;
-            } else {
-                complex_t<R> o;
-                o.x = pr; o.y = pi;
-                spec[e] = o;
+        // GREEN_ZU elements a lane, every load issued before any is used (the
+        // kernel streams rho_hat and G once: its time is bytes in flight)
+        for (int iz0 = lane; iz0 < Mzh; iz0 += GREEN_ZU * 32) {
+            complex_t<R> rv[GREEN_ZU];
+            R Gv[GREEN_ZU];
+#pragma unroll
+            for (int u = 0; u < GREEN_ZU; ++u) {
+                const int iz = iz0 + 32 * u;
+                if (iz < Mzh) {
+                    rv[u] = rhat[row * Mzh + iz];
+                    Gv[u] = Gs[row * Mzh + iz];
+                } else {
+                    rv[u].x = rv[u].y = R(0);
+                    Gv[u] = R(0);
+                }
             }
-            const R w = (iz == 0 || (evenz && iz == Mzh - 1)) ? R(1) : R(2);
-            const R s = w * G * (r.x * r.x + r.y * r.y);
-            const R kz = kv[Mx + My + iz];
-            const R k2 = kxy2 + kz * kz;
-            const R fac = (k2 > R(0)) ? R(2) * (R(1) + k2 * i4g2) / k2 : R(0);
-            const R sf = s * fac;
-            acc[0] += s;
-            acc[1] += s - sf * kx * kx;
-            acc[2] += s - sf * ky * ky;
-            acc[3] += s - sf * kz * kz;
-            acc[4] -= sf * kx * ky;
-            acc[5] -= sf * kx * kz;
-            acc[6] -= sf * ky * kz;
+#pragma unroll
+            for (int u = 0; u < GREEN_ZU; ++u) {
+                const int iz = iz0 + 32 * u;
+                if (iz >= Mzh) continue;
+                const int e = row * Mzh + iz;
+                const complex_t<R> r = rv[u];
+                const R G = Gv[u];
+                const R pr = G * r.x, pi = G * r.y;
+                if (IK) {
+                    // E_a = -i k_a G rho_hat / M  ->  (k_a pi, -k_a pr)
+                    const R dkz = kd[Mx + My + iz];
+                    complex_t<R> o;
+                    o.x = dkx * pi; o.y = -dkx * pr; spec[e] = o;
+                    o.x = dky * pi; o.y = -dky * pr; spec[total + e] = o;
+                    o.x = dkz * pi; o.y = -dkz * pr; spec[2 * total + e] = o;
+                } else {
+                    complex_t<R> o;
+                    o.x = pr; o.y = pi;
+                    spec[e] = o;
+                }
+                const R w = (iz == 0 || (evenz && iz == Mzh - 1)) ? R(1) : R(2);
+                const R s = w * G * (r.x * r.x + r.y * r.y);
+                const R kz = kv[Mx + My + iz];
+                const R k2 = kxy2 + kz * kz;
+                const R fac = (k2 > R(0)) ? R(2) * (R(1) + k2 * i4g2) / k2 : R(0);
+                const R sf = s * fac;
+                acc[0] += s;
+                acc[1] += s - sf * kx * kx;
+                acc[2] += s - sf * ky * ky;
+                acc[3] += s - sf * kz * kz;
+                acc[4] -= sf * kx * ky;
+                acc[5] -= sf * kx * kz;
+                acc[6] -= sf * ky * kz;
+            }
         }
     }
     for (int c = 0; c < 7; ++c) {
