@@ -186,6 +186,22 @@ def onchip_make_rho(n, P, ms, sm_mhz):
             "peak_source": f"microbenchmark, {SHARED_ATOMIC_OPS_PER_CLK_SM} ops/clk/SM x {N_SM} SMs at {mhz:.0f} MHz"}
 
 
+def mesh_stage_gbs(mesh, stage_ms, ik=False):
+    """Achieved GB/s of the FP32 mesh stages at their minimum traffic: one read
+    and one write of each array a stage touches (a lower bound for cuFFT's
+    multi-pass transforms).  Forward: real mesh in, half spectrum out; green:
+    rho_hat and G in, one (ad) or three (ik) spectra out; inverse: the
+    spectra in, the potential or the interleaved field out."""
+    m = int(mesh[0]) * int(mesh[1]) * int(mesh[2])
+    mh = int(mesh[0]) * int(mesh[1]) * (int(mesh[2]) // 2 + 1)
+    nspec = 3 if ik else 1
+    nbytes = {"fft_fwd": 4 * m + 8 * mh,
+              "green": 8 * mh + 4 * mh + 8 * nspec * mh,
+              "fft_inv": 8 * nspec * mh + (16 if ik else 4) * m}
+    return {k: {"bytes": b, "gbs": round(b / (stage_ms[k] * 1e-3) / 1e9, 1)}
+            for k, b in nbytes.items() if stage_ms.get(k)}
+
+
 def make_plan(w, g, mode, prec, graph=True):
     from paper_1702_04250_gb300 import pppm
 
@@ -415,6 +431,7 @@ def large_leg(torch, flush, steps=30):
             "stage_ms": {k: round(v, 4) for k, v in stage.items()},
             "roofline": roof,
             "onchip_make_rho": onchip_make_rho(N, w.order, stage["make_rho"], None),
+            "mesh_stage_gbs": mesh_stage_gbs(w.mesh, stage),
             "timing": f"{steps} graph steps, L2 flushed before each; stage times from a second pass with stage events"}
 
 

@@ -61,3 +61,19 @@ def test_reference_arm_other_ranks_do_no_work():
 
     args = argparse.Namespace(steps=1, warmup=3)
     assert bench.reference_arm(args, rank=1, world=2) is None
+
+
+def test_mesh_stage_bytes():
+    """The mesh stages' minimum traffic: a 256^3 real mesh is 64 MiB, its half
+    spectrum 256 x 256 x 129 complex values; ik adds two spectra and writes
+    the four-component field."""
+    import bench
+
+    m, mh = 256 ** 3, 256 * 256 * 129
+    ad = bench.mesh_stage_gbs((256, 256, 256), {"fft_fwd": 1.0, "green": 0.5, "fft_inv": 2.0})
+    assert ad["fft_fwd"]["bytes"] == 4 * m + 8 * mh
+    assert ad["green"]["bytes"] == 20 * mh and ad["fft_inv"]["bytes"] == 8 * mh + 4 * m
+    assert ad["green"]["gbs"] == round(20 * mh / 0.5e-3 / 1e9, 1)
+    ik = bench.mesh_stage_gbs((64, 64, 64), {"fft_fwd": 0.01, "green": 0.01, "fft_inv": 0.01}, ik=True)
+    assert ik["green"]["bytes"] == 36 * 64 * 64 * 33 and ik["fft_inv"]["bytes"] == 24 * 64 * 64 * 33 + 16 * 64 ** 3
+    assert bench.mesh_stage_gbs((8, 8, 8), {"fft_fwd": 0.0}) == {}
