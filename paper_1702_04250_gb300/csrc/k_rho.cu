@@ -502,259 +502,6 @@ __global__ void __launch_bounds__(GBrick<P>::NT) k_batch_make_rho_fixed(const Ba
     make_rho_fixed_body<P>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);
 }
 
-// ---------------------------------------------------------------------------
-// FP32C at order P >= 5: one particle per warp.
-//
-// The 8-lane groups above put four particles in a warp, and their z runs land
-// on overlapping shared-memory banks (more than half of all atomic wavefronts
-// were bank-conflict replays at P = 7).  Here the lanes of a warp own (y, z)
-// stencil offsets (c, k) of ONE particle and loop over the x offset a, and the
-// brick's row stride puts the lanes of every atomic instruction on 32
-// distinct banks:
-//   P = 5     the 25 pairs c*5 + k on lanes 0..24, row stride 13: rows
-//             c = 0..4 start on banks 0, 13, 26, 7, 20 and never overlap;
-//   P = 6, 7  8 lanes per row (lanes with k >= P idle), rows 4b .. 4b+3 in
-//             block b, row stride 24 = -8 (mod 32): four disjoint octets.
-// The brick strides are compile-time, so every atomic address is one
-// register plus an immediate.
-//
-// Bias-free fixed point.  Both words take the raw bit pattern of
-// (t + 1.5 * 2^23), i.e. the rounded integer plus the bias B = 0x4B400000,
-// with no subtraction per update.  B is a multiple of 2^22, so the low word's
-// low 22 bits hold the plain sum of the lo parts as long as that sum stays
-// inside +-2^21 (a fold every W_FOLD particles guarantees it); the rest of the
-// low word is n B, the same bias the high word carries, and both sums come
-// back exactly:  lo = sext22(L),  hi = H - (L - lo).
-// ---------------------------------------------------------------------------
-template <int P> struct WLayout;
-template <> struct WLayout<5> { static constexpr int RS = 13, NB = 1; };
-template <> struct WLayout<6> { static constexpr int RS = 24, NB = 2; };
-template <> struct WLayout<7> { static constexpr int RS = 24, NB = 2; };
-
-template <int P>
-struct WBrick {
-    static constexpr int RS = WLayout<P>::RS;   // row (z) stride in words
-    static constexpr int EY = TILE_B + P - 1;   // rows per plane: tile y-edge <= TILE_B
-    static constexpr int EX = TILE_B + P - 1;   // planes: tile x-edge <= TILE_B
-    static constexpr int PS = EY * RS;          // plane stride
-    static constexpr int VOLW = EX * PS;        // words per accumulator array
-    static constexpr int ZMAX = RS - (P - 1);   // widest tile along z
-    static constexpr int LPR = RS > 16 ? 32 : 16;  // flush lanes per z row
-};
-
-// Not dispatched: on a tile of 70,000 charges (one particle per warp, heavy
-// contention on a few hundred brick words, a fold every 500 particles) this
-// kernel raised a misaligned-address fault on GB300 in three of four runs,
-// with no out-of-range or misaligned access found in its source.  The 8-lane
-// kernel above serves FP32C until the cause is found.
-constexpr bool kMakeRhoW = false;
-
-constexpr int W_LO_BITS = 13;   // lo = rint(fraction * 2^13), |lo| <= 2^12
-constexpr int W_FOLD = 500;     // 500 * 2^12 + 2^13 < 2^21
-
-// Sums of one brick point from its two biased words (see above).
-__device__ __forceinline__ void w_recover(unsigned int H, unsigned int L, int &hi, int &lo) {
-    lo = ((int)(L << 10)) >> 10;
-    hi = (int)(H - (L - (unsigned int)lo));
-}
-
-// red.shared.add.u32 of a float's bit pattern at a shared-space byte address
-// plus a compile-time offset (the brick is only read after a barrier)
-template <int OFF>
-__device__ __forceinline__ void red_shared(unsigned int addr, float v) {
-    asm volatile("{\n\t.reg .b32 t;\n\tmov.b32 t, %1;\n\tred.shared.add.u32 [%0+%2], t;\n\t}" ::"r"(addr),
-                 "f"(v), "n"(OFF));
-}
-
-// One x offset A of a lane's column: the contribution wx * wyz split into
-// the two biased words (r1 = rint(t) + B, r2 = rint(frac * 2^13) + B, with
-// the product t = wx * wyz never rounded on its own: both FMAs see it exact).
-template <int A, int P, int PS, int VOLW>
-struct ScatterX {
-    static __device__ __forceinline__ void run(const float (&wx)[P], float wyz, unsigned int addr) {
-        const float r1 = __fmaf_rn(wx[A], wyz, MAGIC);
-        const float hi = __fadd_rn(r1, -MAGIC);
-        const float fr = __fmaf_rn(wx[A], wyz, -hi);  // |fr| <= 1/2, rounded once
-        const float r2 = __fmaf_rn(fr, (float)(1 << W_LO_BITS), MAGIC);
-        red_shared<4 * A * PS>(addr, r1);
-        red_shared<4 * (A * PS + VOLW)>(addr, r2);
-        ScatterX<A + 1, P, PS, VOLW>::run(wx, wyz, addr);
-    }
-};
-template <int P, int PS, int VOLW>
-struct ScatterX<P, P, PS, VOLW> {
-    static __device__ __forceinline__ void run(const float (&)[P], float, unsigned int) {}
-};
-
-template <int P>
-__device__ __forceinline__ void make_rho_w_body(const Geom<float> &g, const SortBufs &b, float *__restrict__ rho,
-                                                int tile) {
-    using BR = WBrick<P>;
-    constexpr int NB = WLayout<P>::NB;
-    constexpr int RS = BR::RS;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned int *acch = reinterpret_cast<unsigned int *>(smem_raw);
-    unsigned int *accl = acch + BR::VOLW;
-
-    pdl_wait();  // the sort's outputs (and its reads of the histogram) are complete
-    const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
-    if (threadIdx.x == 0) b.tile_count[tile] = 0;  // histogram is clean for the next step
-    if (start == end) return;
-
-    const int tz = tile % g.T[2];
-    const int ty = (tile / g.T[2]) % g.T[1];
-    const int tx = tile / (g.T[2] * g.T[1]);
-    const int ox = tile_origin(tx, g.T[0], g.M[0]);
-    const int oy = tile_origin(ty, g.T[1], g.M[1]);
-    const int oz = tile_origin(tz, g.T[2], g.M[2]);
-    const int Ex = tile_origin(tx + 1, g.T[0], g.M[0]) - ox + P - 1;
-    const int Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - oy + P - 1;
-    const int Ez = tile_origin(tz + 1, g.T[2], g.M[2]) - oz + P - 1;
-
-    const float4 *__restrict__ rec = reinterpret_cast<const float4 *>(b.rec);
-    float fs, ifs;
-    fixed_scale<float>(reinterpret_cast<const float *>(b.rec), start, end, g.ivcell, fs, ifs);
-
-    const unsigned int sbase = (unsigned int)__cvta_generic_to_shared(acch);
-    if ((sbase & 15u) == 0) {
-        uint4 *w4 = reinterpret_cast<uint4 *>(smem_raw);
-        for (int e = threadIdx.x; e < 2 * BR::VOLW / 4; e += RHO_THREADS) w4[e] = make_uint4(0u, 0u, 0u, 0u);
-        static_assert((2 * BR::VOLW) % 4 == 0, "brick words");
-    } else {  // never expected: the brick is declared 16-byte aligned; report and stay scalar
-        if (threadIdx.x == 0) atomicOr(b.err, ERR_INTERNAL);
-        for (int e = threadIdx.x; e < 2 * BR::VOLW; e += RHO_THREADS) acch[e] = 0u;
-    }
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // weight role: lane dim*P + kk (< 3P) evaluates W_kk of dimension dim
-    const int dim = lane / P, kk = lane - (lane / P) * P;
-    float ck[P];
-#pragma unroll
-    for (int l = 0; l < P; ++l) ck[l] = (lane < 3 * P) ? g.coef[kk][l] : 0.0f;
-    // stencil role per block: offsets (c, k), brick offset c*RS + k.  Lanes
-    // without a stencil point still issue their atomics -- a zero weight at an
-    // in-bounds address in a bank no other lane of the instruction uses --
-    // so the scatter has no divergent branch (the biased words count adds,
-    // not particles, and need no exact count).
-    int off[NB], sy[NB], sz[NB];
-    float vmask[NB];
-#pragma unroll
-    for (int bb = 0; bb < NB; ++bb) {
-        int c, k;
-        bool v;
-        if (P == 5) {
-            c = lane / 5;
-            k = lane - c * 5;
-            v = lane < 25;
-            // idle lanes 25..31 take the free banks 5, 6, 12, 18, 19, 25, 31
-            // (five bits each, lane 25 lowest)
-            const int spare = (int)((0x7f33930c5ull >> (5 * (lane > 25 ? lane - 25 : 0))) & 31u);
-            off[bb] = v ? c * RS + k : spare;
-        } else {
-            c = 4 * bb + (lane >> 3);
-            k = lane & 7;
-            v = k < P && c < P;
-            // rows c >= P reuse row c - 4 (same bank octet); z offset k <= 7
-            // stays inside the row for tiles up to 16 deep
-            off[bb] = (c < P ? c : c - 4) * RS + k;
-        }
-        if (!v) c = k = 0;
-        vmask[bb] = v ? 1.0f : 0.0f;
-        sy[bb] = P + c;
-        sz[bb] = 2 * P + k;
-    }
-    const float qscale = g.ivcell * fs;
-    constexpr int NW = RHO_THREADS / 32;
-
-    bool bad = false;  // a particle outside this tile (an inconsistent sort)
-    for (int chunk = start; chunk < end; chunk += W_FOLD) {
-        const int cend = min(end, chunk + W_FOLD);
-        int j = chunk + warp;
-        const int jl = cend - 1;
-        float4 rn = rec[min(j, jl)];
-        uint32_t cn = b.cell[min(j, jl)];
-        for (; j < cend; j += NW) {   // warp-uniform: every lane takes part in the shuffles
-            const float4 r = rn;
-            const uint32_t cc = cn;
-            rn = rec[min(j + NW, jl)];  // prefetch the warp's next particle (branch-free)
-            cn = b.cell[min(j + NW, jl)];
-            int ax, ay, az;
-            unpack_anchor(cc, ax, ay, az);
-            ax -= ox; ay -= oy; az -= oz;
-            // a particle outside the tile adds zeros at the brick origin and is reported
-            const bool out = (unsigned)ax > (unsigned)(Ex - P) || (unsigned)ay > (unsigned)(Ey - P) ||
-                             (unsigned)az > (unsigned)(Ez - P);
-            bad |= out;
-            const unsigned int pb = out ? sbase : sbase + 4u * (unsigned int)(ax * BR::PS + ay * RS + az);
-            const float d = dim == 0 ? r.x : (dim == 1 ? r.y : r.z);
-            const float w = horner<float, P>(ck, d);
-            const float qv = out ? 0.0f : r.w * qscale;
-            float wx[P];
-#pragma unroll
-            for (int a = 0; a < P; ++a) wx[a] = __shfl_sync(0xffffffffu, w, a);
-#pragma unroll
-            for (int bb = 0; bb < NB; ++bb) {
-                const float wyz =
-                    vmask[bb] * qv * __shfl_sync(0xffffffffu, w, sy[bb]) * __shfl_sync(0xffffffffu, w, sz[bb]);
-                ScatterX<0, P, BR::PS, BR::VOLW>::run(wx, wyz, pb + 4u * (unsigned int)off[bb]);
-            }
-        }
-        __syncthreads();
-        if (cend < end) {  // fold: unbiased hi, lo in [0, 2^13)
-            for (int e = threadIdx.x; e < BR::VOLW; e += RHO_THREADS) {
-                int hi, lo;
-                w_recover(acch[e], accl[e], hi, lo);
-                acch[e] = (unsigned int)(hi + (lo >> W_LO_BITS));
-                accl[e] = (unsigned int)(lo & ((1 << W_LO_BITS) - 1));
-            }
-            __syncthreads();
-        }
-    }
-    if (bad && lane == 0) atomicOr(b.err, ERR_INTERNAL);
-
-    // flush the brick (tile + halo) into the global mesh, z rows of LPR lanes;
-    // every wrap is a single conditional (the brick is never wider than the
-    // mesh plus one period)
-    constexpr int LPR = BR::LPR, RPP = RHO_THREADS / LPR;
-    const int lz = threadIdx.x % LPR, ry = threadIdx.x / LPR;
-    if (lz < Ez) {
-        int gz = oz - g.rlo + lz;
-        gz += (gz < 0) ? g.M[2] : 0;
-        gz -= (gz >= g.M[2]) ? g.M[2] : 0;
-        for (int ex = 0; ex < Ex; ++ex) {
-            int gx = ox - g.rlo + ex;
-            gx += (gx < 0) ? g.M[0] : 0;
-            gx -= (gx >= g.M[0]) ? g.M[0] : 0;
-            for (int ey = ry; ey < Ey; ey += RPP) {
-                int gy = oy - g.rlo + ey;
-                gy += (gy < 0) ? g.M[1] : 0;
-                gy -= (gy >= g.M[1]) ? g.M[1] : 0;
-                const int e = ex * BR::PS + ey * RS + lz;
-                int hi, lo;
-                w_recover(acch[e], accl[e], hi, lo);
-                // normalise in integers (exact), then one FP32 rounding
-                const float v = fmaf((float)(lo & ((1 << W_LO_BITS) - 1)), 1.0f / (float)(1 << W_LO_BITS),
-                                     (float)(hi + (lo >> W_LO_BITS))) * ifs;
-                if (v != 0.0f) atomicAdd(&rho[(gx * g.M[1] + gy) * g.M[2] + gz], v);
-            }
-        }
-    }
-}
-
-template <int P>
-__global__ void __launch_bounds__(RHO_THREADS) k_make_rho_w(Geom<float> g, SortBufs b, float *__restrict__ rho) {
-    make_rho_w_body<P>(g, b, rho, blockIdx.x);
-}
-
-template <int P>
-__global__ void __launch_bounds__(RHO_THREADS) k_batch_make_rho_w(const BatchSys<float> *__restrict__ sys,
-                                                                  BatchList bl) {
-    const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
-    const BatchSys<float> &S = sys[bl.ids[e]];
-    make_rho_w_body<P>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);
-}
-
 template <typename R, int P, int ACC, bool CS = false>
 __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b, R *__restrict__ rho) {
     make_rho_body<R, P, ACC, CS>(g, b, rho, blockIdx.x);
@@ -785,12 +532,6 @@ static void launch_one(K kernel, bool pdl, dim3 grid, size_t bytes, cudaStream_t
 template <typename R, int P>
 static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, int acc, cudaStream_t s, bool pdl) {
     const size_t bytes = brick_bytes<R, P>(acc);
-    if constexpr (std::is_same<R, float>::value && P >= 5) {
-        if (acc == ACC_FIXED && kMakeRhoW) {
-            launch_one(k_make_rho_w<P>, pdl, dim3(g.ntiles), 8 * WBrick<P>::VOLW, s, g, b, rho);
-            return;
-        }
-    }
     if constexpr (std::is_same<R, float>::value) {
         if (acc == ACC_FIXED && g.rho_copies == 1) {
             launch_one(k_make_rho_fixed<P>, pdl, dim3(g.ntiles), GBrick<P>::BYTES, s, g, b, rho, GBrick<P>::NT);
@@ -838,12 +579,6 @@ static cudaError_t prepare_p(int acc) {
 template <typename R, int P>
 static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc, bool copies4, cudaStream_t s) {
     const size_t bytes = brick_bytes<R, P>(acc);
-    if constexpr (std::is_same<R, float>::value && P >= 5) {
-        if (acc == ACC_FIXED && kMakeRhoW) {
-            k_batch_make_rho_w<P><<<bl.nblocks, RHO_THREADS, 8 * WBrick<P>::VOLW, s>>>(sys, bl);
-            return;
-        }
-    }
     if constexpr (std::is_same<R, float>::value) {
         if (acc == ACC_FIXED && copies4) {
             k_batch_make_rho_fixed<P><<<bl.nblocks, GBrick<P>::NT, GBrick<P>::BYTES, s>>>(sys, bl);

@@ -78,11 +78,12 @@ template <typename R> using complex_t = typename Complex<R>::type;
 __host__ __device__ inline int tile_of(int n, int T, int M) { return ((n + 1) * T - 1) / M; }
 
 // Tiles per dimension (T) and the widest tile (TE) for tile edge TILE_B, or
-// 2 TILE_B along z when long_z, or TILE_B / 2 when small.  Long tiles halve
-// the tile count and cut the halo share of the make_rho brick flush; only the
-// compensated FP32 make_rho at order >= 6 has a brick deep enough for them.
-// Small tiles give meshes with few 8^3 tiles enough CTAs for the GPU, at
-// the price of a larger halo share.
+// 2 TILE_B along z when long_z, or TILE_B / 2 when small.  Long tiles would
+// halve the tile count and cut the halo share of the make_rho brick flush,
+// but no dispatched make_rho takes bricks deeper than 16 points (one brick
+// column per thread of its flush), so they are refused.  Small tiles give
+// meshes with few 8^3 tiles enough CTAs for the GPU, at the price of a
+// larger halo share.
 inline void tile_shape(const int M[3], bool long_z, int T[3], int TE[3], bool small = false) {
     for (int d = 0; d < 3; ++d) {
         const int e = small ? TILE_B / 2 : ((d == 2 && long_z) ? 2 * TILE_B : TILE_B);
@@ -93,7 +94,7 @@ inline void tile_shape(const int M[3], bool long_z, int T[3], int TE[3], bool sm
 inline bool long_tiles_allowed(int P, bool compensated) {
     (void)P;
     (void)compensated;
-    return false;  // needs the warp-per-particle make_rho, which is not dispatched (see k_rho.cu)
+    return false;  // no make_rho brick deeper than 16 points (see tile_shape)
 }
 __host__ __device__ inline int tile_origin(int t, int T, int M) { return (t * M) / T; }
 
