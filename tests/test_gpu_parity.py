@@ -270,6 +270,27 @@ def test_dense_tile(torch, prec, P):
     check_all(f, ev, ref, prec, "dense tile")
 
 
+@pytest.mark.parametrize("prec,P,n,spread", [("fp32c", 5, 256, 1.5), ("fp32c", 7, 257, 1.5),
+                                             ("fp32c", 5, 513, 0.2), ("fp64", 7, 257, 0.2)])
+def test_subchunk_boundaries(torch, prec, P, n, spread):
+    """make_rho orders each tile's particles in sub-chunks of 256 by the shared
+    bank their stencil runs start on: one tile holding exactly 256, 257 or 513
+    charges (a full sub-chunk, one plus a single particle, two plus one), and
+    with spread 0.2 every charge on the same anchor (all in one bank bin)."""
+    r = np.random.default_rng(37 + n)
+    box, mesh, g = (20.0, 20.0, 20.0), (20, 20, 20), 0.5
+    x = 3.3 + r.uniform(0.0, spread, (n, 3))
+    q = r.normal(size=n)
+    plan, f, ev = run(torch, box, mesh, P, g, "ik", prec, x, q)
+    xo, qo = oracle_inputs(x, q, prec)
+    ref = OraclePPPM(box, mesh, P, g, "ik", 1.0).compute(xo, qo, keep=True)
+    rho = plan.get_array("rho").astype(np.float64)
+    rerr = np.sqrt(np.mean((rho - ref["rho"]) ** 2)) / np.sqrt(np.mean(ref["rho"] ** 2))
+    assert rerr < (1e-12 if prec == "fp64" else 1e-5), rerr
+    check_all(f, ev, ref, prec, f"sub-chunk n={n}")
+    plan.close()
+
+
 def test_empty_input(torch):
     from paper_1702_04250_gb300 import pppm
 
