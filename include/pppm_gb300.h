@@ -221,7 +221,9 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
 /* Kernel variants of a plan (Sec. 3.1's mapping functions have one result
  * and several implementations; the paper picks them by measurement, and so
  * does this).  Bit 0: fieldforce stages the tile's field brick in shared
- * memory (1) or reads the field through L1 per particle (0).  Bit 1
+ * memory (1) or reads the field through L1 per particle (0); it applies to
+ * force steps -- pppm_energy_grad and pppm_potential always gather the
+ * potential through L1.  Bit 1
  * (mesh tiles 16 points long along z) is reserved: refused with PPPM_EINVAL
  * by every plan of this build.  Bit 2: PPPM_FP32C make_rho accumulates in
  * four interleaved copies of the tile brick (no shared-memory bank
