@@ -686,6 +686,12 @@ def cpu_cores_used():
     return 1
 
 
+def cpu_baseline_obj(rate, sample):
+    """The oracle's timing: the threads it used and the host's core count."""
+    return {"value": round(rate, 4), "unit": "steps/s", "cores": cpu_cores_used(),
+            "host_cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return None
@@ -697,8 +703,7 @@ def reference_arm(args, rank, world):
             "n_gpus": world, "steps": n, "warmup": 1, "ms_per_step": round(1000.0 / rate, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(w, {"precision": "fp64 (oracle)"}),
-            "cpu_baseline": {"value": round(rate, 4), "unit": "steps/s", "cores": cpu_cores_used(),
-                             "kind": "oracle", "sample": f"{n} full oracle steps of the workload ({dt:.1f} s)"},
+            "cpu_baseline": cpu_baseline_obj(rate, f"{n} full oracle steps of the workload ({dt:.1f} s)"),
             "e2e": {"value": round(rate, 4), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -736,9 +741,7 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline:
             rate, n, dt = oracle_rate(workload())
-            line["cpu_baseline"] = {"value": round(rate, 4), "unit": "steps/s", "cores": cpu_cores_used(),
-                                    "kind": "oracle",
-                                    "sample": f"{n} full FP64 oracle steps of the same workload ({dt:.1f} s)"}
+            line["cpu_baseline"] = cpu_baseline_obj(rate, f"{n} full FP64 oracle steps of the same workload ({dt:.1f} s)")
         print(json.dumps(line))
     if world > 1:
         import torch

@@ -77,3 +77,11 @@ def test_mesh_stage_bytes():
     ik = bench.mesh_stage_gbs((64, 64, 64), {"fft_fwd": 0.01, "green": 0.01, "fft_inv": 0.01}, ik=True)
     assert ik["green"]["bytes"] == 36 * 64 * 64 * 33 and ik["fft_inv"]["bytes"] == 24 * 64 * 64 * 33 + 16 * 64 ** 3
     assert bench.mesh_stage_gbs((8, 8, 8), {"fft_fwd": 0.0}) == {}
+
+
+def test_cpu_baseline_object():
+    import bench
+
+    o = bench.cpu_baseline_obj(5.12345, "50 steps")
+    assert o == {"value": 5.1235, "unit": "steps/s", "cores": 1, "host_cores": os.cpu_count(),
+                 "kind": "oracle", "sample": "50 steps"}
