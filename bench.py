@@ -1,26 +1,26 @@
 """Benchmark of the PPPM k-space path on GB300.
 
 One step = one full pass of the k-space path (particle_map + sort, make_rho,
-forward FFT, influence-function multiply with energy/virial, inverse FFTs,
-fieldforce) over the water-like workload: 10,667 rigid 3-site molecules
-(32,001 charges) in a 68 A periodic cube, mesh 64^3, order 5, ik
-differentiation, FP32 spreading/FFT/interpolation with compensated mesh
-accumulation.  Inputs are resident in HBM; the L2 is flushed (256 MiB write)
-before every timed step and each step is timed with CUDA events on the plan's
-stream.  The step runs as one captured CUDA graph.
+forward FFT, influence-function multiply with energy/virial, inverse FFT,
+fieldforce with the ad self-force epilogue) over the largest single-GPU
+workload: 682,667 rigid 3-site water-like molecules (2,048,001 charges) in a
+272 A periodic cube, mesh 256^3, order 7, ad differentiation, FP32 spreading /
+FFT / interpolation with compensated mesh accumulation and FP64 setup and
+reductions.  Inputs are resident in HBM (and larger than L2; the L2 is also
+flushed with a 256 MiB write before every timed step); each step is one
+captured CUDA graph timed with CUDA events on the plan's stream.
 
-Also reported on the same line: Mparticles/s, the force error of this FP32C
-form against the FP64 form (same GPU, same inputs), the dominant kernel's
-roofline fraction, the end-to-end rate through the host-buffer C-ABI call,
-the FP64 oracle timed on the host cores, and the same metric for ad / FP64.
-More is measured on rank 0 (key "extra", skipped with --no-extra): the
-2,048,001-charge water-like system (256^3, P=7, ad, FP32C; the HBM-sized
-case: per-stage times and the make_rho / fieldforce roofline fractions), the
-batch of 256 independent systems (one call, one graph; against the FP64 batch
-and against 256 single-system plans), the real-space erfc sum of the bench
-workload (r_C = 10 A), the other half of the Ewald split, the mesh chosen for
-a target accuracy with step times by mesh edge, and the differentiable energy
-of the 99,999-charge system (96^3): force step and energy with gradients.
+Reported on the same line: Mparticles/s; the error of every result (forces,
+energy, virial) against the FP64 form on the same GPU and against the FP64
+CPU oracle (forces on a 1 % subsample); the roofline of make_rho and
+fieldforce (event-timed inside the timed region, algorithmic bytes over the
+measured HBM copy peak); the end-to-end rate through the host-buffer C-ABI
+call; the FP64 oracle timed on the host cores (one core, and independent
+replicas on all cores).  More on rank 0 under "extra" (skipped with
+--no-extra): the 32,001-charge water-like system (64^3, P=5; ik and ad,
+FP32C and FP64), the batch of 256 independent systems, the real-space erfc
+sum, the mesh chosen for a target accuracy, and the differentiable energy of
+the 99,999-charge system.
 
 --impl reference times the FP64 CPU oracle on the same workload instead.
 Multi-GPU: the path does not shard (one system); N ranks run N independent
@@ -43,52 +43,103 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 256 << 20
-PROFILE_EVERY = 10  # timed steps per step that carries the dominant kernel's events
-WORKLOAD = "c2"
+WORKLOAD = "c3"
+HEADLINE_MODE = "ad"
+SUBSAMPLE = 100  # forces compared with the oracle (and oracle forces timed) on every 100th charge
 
 
-def workload():
+def workload(name=WORKLOAD):
     from paper_1702_04250_gb300.workloads import config
 
-    return config(WORKLOAD)
+    return config(name)
 
 
 def metric_name():
-    return "PPPM k-space steps/sec at 1e-4 rel force error vs FP64 form (water-like 32,001 charges, 64^3, P=5, ik, FP32C)"
+    return ("PPPM k-space steps/sec at 1e-4 rel force error vs FP64 form (water-like 2,048,001 charges, "
+            "272 A cube, 256^3, P=7, ad, FP32C)")
 
 
 def config_dict(w, extra=None):
-    d = {"workload": "c2 water-like: 10,667 rigid 3-site molecules (32,001 charges), 68 A cube, mesh 64^3, "
-                     "order 5, ik, g_ewald for 1e-4 at r_C = 10 A",
-         "n_charges": int(w.n), "mesh": list(w.mesh), "order": int(w.order), "diff": "ik", "precision": "fp32c",
-         "l2": "flushed (256 MiB write) before every timed step", "graph": True}
+    d = {"workload": "c3 water-like: 682,667 rigid 3-site molecules (2,048,001 charges), 272 A cube, mesh 256^3, "
+                     "order 7, ad, FP32C, g_ewald for 1e-4 at r_C = 10 A",
+         "n_charges": int(w.n), "mesh": list(w.mesh), "order": int(w.order), "diff": HEADLINE_MODE,
+         "precision": "fp32c",
+         "l2": "inputs larger than L2 (mesh 64 MiB + particles 80 MiB); also flushed (256 MiB write) before "
+               "every timed step", "graph": True}
     if extra:
         d.update(extra)
     return d
 
 
 # ---------------------------------------------------------------------------
-# clocks
+# clocks (read-only nvidia-smi queries of the GPU this process runs on)
 # ---------------------------------------------------------------------------
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0):
-        self.index = index
+    def __init__(self, dev=0):
+        self.dev = dev
         self.samples = []
         self.proc = None
+        self.error = None
+        self.gpu_id = None
 
-    def start(self):
+    def _candidates(self):
+        """nvidia-smi --id values naming this process's GPU: its UUID, its PCI
+        bus id, the CUDA_VISIBLE_DEVICES entry, and the ordinal last (nvidia-smi
+        reads an ordinal as a physical index)."""
+        import torch
+
+        out = []
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+            p = torch.cuda.get_device_properties(self.dev)
+            u = str(p.uuid)
+            out.append(u if u.startswith("GPU-") else "GPU-" + u)
+            out.append(f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0")
+        except Exception as e:  # older torch: no uuid / pci fields
+            self.error = f"device properties: {e}"
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            items = [s.strip() for s in vis.split(",") if s.strip()]
+            if self.dev < len(items):
+                out.append(items[self.dev])
+        out.append(str(self.dev))
+        return out
+
+    def _resolve(self):
+        errs = []
+        for c in self._candidates():
+            try:
+                r = subprocess.run(["nvidia-smi", f"--id={c}", "--query-gpu=index,clocks.sm",
+                                    "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+            except Exception as e:
+                errs.append(f"{c}: {e}")
+                continue
+            if r.returncode == 0 and r.stdout.strip():
+                return c
+            errs.append(f"{c}: rc {r.returncode} {r.stderr.strip()[:120]}")
+        self.error = "; ".join(errs)[:400]
+        return None
+
+    def start(self, wait_first_s=5.0):
+        self.gpu_id = self._resolve()
+        if self.gpu_id is None:
+            return
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                         stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
-        except Exception:
+        except Exception as e:
+            self.error = f"nvidia-smi: {e}"
             self.proc = None
+            return
+        t0 = time.time()
+        while not self.samples and time.time() - t0 < wait_first_s and self.proc.poll() is None:
+            time.sleep(0.02)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -101,10 +152,23 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+            if not self.samples:
+                try:
+                    self.error = (self.error or "") + " stderr: " + self.proc.stderr.read()[:300]
+                except Exception:
+                    pass
         if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "error": self.error,
+                    "gpu_id": self.gpu_id}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(s[1]) for s in self.samples if len(s) > 2 and num(s[1]) is not None]
+        mx = [num(s[2]) for s in self.samples if len(s) > 2 and num(s[2]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
         for s in self.samples:
@@ -112,7 +176,7 @@ class ClockSampler:
                 if len(s) > 5 + k and s[5 + k].lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.samples)}
+                "reasons": sorted(reasons), "samples": len(self.samples), "gpu_id": self.gpu_id}
 
 
 # ---------------------------------------------------------------------------
@@ -141,12 +205,18 @@ def known_traffic(stage, workload_name, source):
     for ln in lines:
         if ln.startswith("#") or not ln.strip():
             continue
-        st, wl, src, sha, nbytes = ln.split()
+        parts = ln.split()
+        if len(parts) < 5:
+            continue
+        st, wl, src, sha, nbytes = parts[:5]
+        variant = parts[5] if len(parts) > 5 else None
         if st == stage and wl == workload_name and src == source:
             m = hashlib.sha1()
             for f in (src, "paper_1702_04250_gb300/csrc/pppm_common.cuh"):
                 m.update(open(os.path.join(ROOT, f), "rb").read())
-            return int(nbytes) if m.hexdigest()[:16] == sha else None
+            if m.hexdigest()[:16] != sha:
+                return None
+            return {"bytes": int(nbytes), "variant": variant}
     return None
 
 
@@ -183,23 +253,34 @@ def onchip_make_rho(n, P, ms, sm_mhz):
     ach = ops / (ms * 1e-3) / 1e9
     return {"resource": "shared-memory int32 atomics", "ops_per_launch": int(ops),
             "achieved_gops": round(ach, 1), "peak_gops": round(peak, 1), "frac": round(ach / peak, 4),
-            "peak_source": f"microbenchmark, {SHARED_ATOMIC_OPS_PER_CLK_SM} ops/clk/SM x {N_SM} SMs at {mhz:.0f} MHz"}
+            "floor_ms": round(ops / (peak * 1e9) * 1e3, 4), "clock_mhz": mhz,
+            "clock_source": "sampled median" if sm_mhz else "assumed maximum (no clock samples)",
+            "peak_source": f"microbenchmark, {SHARED_ATOMIC_OPS_PER_CLK_SM} ops/clk/SM x {N_SM} SMs"}
+
+
+def alg_bytes(stage, n, mesh, ik):
+    """Algorithmic (minimum) bytes per launch of a stage, FP32 step type, as
+    the hot-path scope table counts them: particles once, mesh once.
+      sort       16N read + 16N write + 8N (cell key, permutation)
+      make_rho   16N (x, q) + 8M (compensated hi + lo mesh write)
+      green      4M (rho_hat, M/2 complex) + 2M (G, real half spectrum) + 4M per output spectrum
+      fieldforce ik: 16M (float4 field) + 32N (x, q in; F out); ad: 4M + 32N"""
+    M = int(mesh[0]) * int(mesh[1]) * int(mesh[2])
+    mh = int(mesh[0]) * int(mesh[1]) * (int(mesh[2]) // 2 + 1)
+    return {"sort": 40 * n,
+            "make_rho": 16 * n + 8 * M,
+            "green": 8 * mh + 4 * mh + 8 * mh * (3 if ik else 1),
+            "fieldforce": (16 * M if ik else 4 * M) + 32 * n,
+            "fft_fwd": 4 * M + 8 * mh,
+            "fft_inv": 8 * mh * (3 if ik else 1) + (16 if ik else 4) * M}[stage]
 
 
 def mesh_stage_gbs(mesh, stage_ms, ik=False):
     """Achieved GB/s of the FP32 mesh stages at their minimum traffic: one read
     and one write of each array a stage touches (a lower bound for cuFFT's
-    multi-pass transforms).  Forward: real mesh in, half spectrum out; green:
-    rho_hat and G in, one (ad) or three (ik) spectra out; inverse: the
-    spectra in, the potential or the interleaved field out."""
-    m = int(mesh[0]) * int(mesh[1]) * int(mesh[2])
-    mh = int(mesh[0]) * int(mesh[1]) * (int(mesh[2]) // 2 + 1)
-    nspec = 3 if ik else 1
-    nbytes = {"fft_fwd": 4 * m + 8 * mh,
-              "green": 8 * mh + 4 * mh + 8 * nspec * mh,
-              "fft_inv": 8 * nspec * mh + (16 if ik else 4) * m}
-    return {k: {"bytes": b, "gbs": round(b / (stage_ms[k] * 1e-3) / 1e9, 1)}
-            for k, b in nbytes.items() if stage_ms.get(k)}
+    multi-pass transforms)."""
+    return {k: {"bytes": alg_bytes(k, 0, mesh, ik), "gbs": round(alg_bytes(k, 0, mesh, ik) / (stage_ms[k] * 1e-3) / 1e9, 1)}
+            for k in ("fft_fwd", "green", "fft_inv") if stage_ms.get(k)}
 
 
 def make_plan(w, g, mode, prec, graph=True):
@@ -219,7 +300,8 @@ def time_steps(torch, plan, x, q, f, ev, steps, warmup, flush, profile=False, sy
     n_prof = 0
     for i in range(warmup):
         plan.set_profiling(profile if (profile and i % every == 0) else False)
-        flush.zero_()
+        with torch.cuda.stream(s):
+            flush.zero_()
         plan.compute(x, q, f, ev)
     torch.cuda.synchronize()
     if sync_ranks and torch.distributed.is_available() and torch.distributed.is_initialized():
@@ -250,6 +332,33 @@ def time_steps(torch, plan, x, q, f, ev, steps, warmup, flush, profile=False, sy
     return total, {k: v / max(n_prof, 1) for k, v in stage_sum.items()}
 
 
+def rel_rms(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(math.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+def result_errors(f, ev, f_ref, ev_ref):
+    """Per-result error metrics: forces relative RMS, energy relative,
+    virial norm-relative."""
+    ev = np.asarray(ev, dtype=np.float64)
+    ev_ref = np.asarray(ev_ref, dtype=np.float64)
+    return {"force_rel_rms": rel_rms(f, f_ref),
+            "energy_rel": float(abs(ev[0] - ev_ref[0]) / abs(ev_ref[0])),
+            "virial_rel": float(np.linalg.norm(ev[1:7] - ev_ref[1:7]) / np.linalg.norm(ev_ref[1:7]))}
+
+
+def kernel_roofline(stage, w, ms, ik, peak, peak_kind, traffic_src, variant_ok):
+    nbytes = alg_bytes(stage, w.n, w.mesh, ik)
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    tr = known_traffic(stage, w.name, traffic_src) if variant_ok else None
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": tr["bytes"] if tr else None,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+            "alg_bytes_per_launch": int(nbytes), "avg_launch_ms": round(ms, 5),
+            "roof_ms": round(nbytes / (peak * 1e9) * 1e3, 4)}
+
+
 def gpu_arm(args, rank, world):
     import torch
 
@@ -263,39 +372,43 @@ def gpu_arm(args, rank, world):
     g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, q2, w.box)
     x32 = torch.tensor(w.x, dtype=torch.float32, device="cuda")
     q32 = torch.tensor(w.q, dtype=torch.float32, device="cuda")
-    x64 = torch.tensor(w.x, dtype=torch.float64, device="cuda")
-    q64 = torch.tensor(w.q, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ik = HEADLINE_MODE == "ik"
 
-    plan = make_plan(w, g, "ik", "fp32c")
+    plan = make_plan(w, g, HEADLINE_MODE, "fp32c")
     f = torch.empty((w.n, 3), dtype=torch.float32, device="cuda")
     ev = torch.zeros(8, dtype=torch.float64, device="cuda")
     variant = plan.autotune(x32, q32)  # what a user of the plan does once
     plan.compute(x32, q32, f, ev)
     plan.sync()
+    f_fp32c = f.double().cpu().numpy()
+    ev_fp32c = ev[:7].cpu().numpy()
 
     # accuracy of this form against the FP64 form on the same GPU and inputs
-    p64 = make_plan(w, g, "ik", "fp64", graph=False)
+    p64 = make_plan(w, g, HEADLINE_MODE, "fp64", graph=False)
     f64, ev64 = p64.compute(x32.double(), q32.double())
     p64.sync()
-    f64n = f64.cpu().numpy()
-    rel_err = math.sqrt(float(np.sum((f.double().cpu().numpy() - f64n) ** 2) / np.sum(f64n ** 2)))
-    e_err = abs(ev[0].item() - ev64[0].item()) / abs(ev64[0].item())
+    err_fp64 = result_errors(f_fp32c, ev_fp32c, f64.cpu().numpy(), ev64.cpu().numpy())
+    del f64
+    p64.close()
+    torch.cuda.empty_cache()
 
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(dev)
     clocks.start()
-    # which of our kernels dominates (all stage events on, short untimed pass)
-    _, disc = time_steps(torch, plan, x32, q32, f, ev, 20, 3, flush, profile=True)
+    # per-stage times (all stage events on, short untimed pass)
+    _, disc = time_steps(torch, plan, x32, q32, f, ev, 10, 3, flush, profile=True)
     own_fft = bool(variant & 8)  # the hand-written Poisson solve (else cuFFT + k_green)
     own = {k: disc[k] for k in ("sort", "make_rho", "green", "fieldforce") + (("fft_fwd", "fft_inv") if own_fft else ())}
     dom = max(own, key=own.get)
+    kern = ["make_rho", "fieldforce"]
 
-    # the timed region: K steps; every 10th carries events around the dominant kernel
-    t_ms, stages = time_steps(torch, plan, x32, q32, f, ev, args.steps, args.warmup, flush, profile=[dom],
-                              every=PROFILE_EVERY)
+    # the timed region: K steps; every 2nd carries events around make_rho and fieldforce
+    every = 2
+    t_ms, stages = time_steps(torch, plan, x32, q32, f, ev, args.steps, args.warmup, flush, profile=kern,
+                              every=every)
     clocks_rep = clocks.stop()
     torch.cuda.synchronize()
     if world > 1:
@@ -305,34 +418,26 @@ def gpu_arm(args, rank, world):
     steps_per_s = throughput(1, t_ms, args.steps, world)
 
     # the same steps without any stage event (graph of kernels only)
-    t_plain, _ = time_steps(torch, plan, x32, q32, f, ev, max(20, args.steps // 2), 3, flush, profile=False)
-    ms_plain = t_plain / max(20, args.steps // 2)
+    n_plain = max(20, args.steps // 2)
+    t_plain, _ = time_steps(torch, plan, x32, q32, f, ev, n_plain, 3, flush, profile=False)
+    ms_plain = t_plain / n_plain
 
-    # roofline of the dominant hand-written kernel
-    stage_ms = dict(disc)        # all stages, discovery pass (events inflate each)
-    stage_ms[dom] = stages[dom]  # the dominant kernel, timed region (every 10th step)
-    N, M = w.n, int(np.prod(w.mesh))
-    MH = (M // w.mesh[2]) * (w.mesh[2] // 2 + 1)  # half spectrum
-    alg_bytes = {
-        "sort": (12 + 4) * N * 2 + (16 + 4 + 4 + 4 + 4) * N,   # x,q read twice; record, anchor, perm, rank writes
-        "make_rho": (16 + 4) * N + 4 * M,                        # sorted records + anchors in, mesh out once
-        "green": 8 * MH * (1 + 3) + 4 * MH,                      # rho_hat in, three spectra out, G in
-        "fft_fwd": 4 * M + 8 * MH,                               # mesh in, rho_hat out
-        "fft_inv": 8 * MH * 3 + 12 * M,                          # three spectra in, three field components out
-        "fieldforce": 16 * M + (16 + 4 + 4 + 12) * N,            # float4 field once, records, anchors, perm, forces
-    }[dom]
-    source = {"sort": "k_sort.cu", "make_rho": "k_rho.cu", "fieldforce": "k_force.cu", "fft_fwd": "k_fft.cu",
-              "fft_inv": "k_fft.cu", "green": "k_fft.cu" if own_fft else "k_green.cu"}[dom]
-    # the committed c2 captures are of variant 9 (one-brick make_rho, tile-staged fieldforce)
-    traffic_ok = not ((dom == "fieldforce" and not variant & 1) or (dom == "make_rho" and variant & 4))
     peak, peak_kind = measured_peak()
-    achieved = alg_bytes / (stage_ms[dom] * 1e-3) / 1e9
-    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": known_traffic(dom, WORKLOAD, "paper_1702_04250_gb300/csrc/" + source) if traffic_ok else None,
-            "peak_source": peak_kind,
-            "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(stage_ms[dom], 5),
-            "launches_timed": f"every {PROFILE_EVERY}th timed step carries events around this kernel",
-            "stage_ms": {k: round(v, 5) for k, v in stage_ms.items()}}
+    src = "paper_1702_04250_gb300/csrc/"
+    # the committed c3 captures: the per-particle L1 fieldforce (variant bit 0 clear), the one-brick make_rho
+    kernels = {
+        "make_rho": kernel_roofline("make_rho", w, stages["make_rho"], ik, peak, peak_kind, src + "k_rho.cu",
+                                    not variant & 4),
+        "fieldforce": kernel_roofline("fieldforce", w, stages["fieldforce"], ik, peak, peak_kind,
+                                      src + "k_force.cu", not variant & 1),
+    }
+    top = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
+    roof = dict(kernels[top])
+    roof["kernel"] = top
+    roof["launches_timed"] = f"every {every}nd timed step carries events around make_rho and fieldforce"
+    roof["kernels"] = kernels
+    roof["stage_ms_all_events"] = {k: round(v, 5) for k, v in disc.items()}
+    roof["dominant_own_stage"] = dom
 
     # end to end through the host-buffer C-ABI call (pinned host memory)
     xh = torch.tensor(w.x, dtype=torch.float32).pin_memory()
@@ -341,107 +446,120 @@ def gpu_arm(args, rank, world):
     evh = torch.empty(8, dtype=torch.float64).pin_memory()
     for _ in range(3):
         plan.compute_host_into(w.n, xh.data_ptr(), qh.data_ptr(), fh.data_ptr(), evh.data_ptr())
-    ne = max(20, args.steps // 2)
+    ne = max(10, args.steps // 2)
     t0 = time.perf_counter()
     for _ in range(ne):
         plan.compute_host_into(w.n, xh.data_ptr(), qh.data_ptr(), fh.data_ptr(), evh.data_ptr())
     e2e_s = (time.perf_counter() - t0) / ne
-
-    # the other forms of the same metric, shorter runs
-    variants = {}
-    for mode, prec, xx, qq in (("ad", "fp32c", x32, q32), ("ik", "fp64", x64, q64), ("ad", "fp64", x64, q64)):
-        pv = make_plan(w, g, mode, prec)
-        fv = torch.empty((w.n, 3), dtype=xx.dtype, device="cuda")
-        tv, _ = time_steps(torch, pv, xx, qq, fv, ev, max(20, args.steps // 4), 3, flush)
-        variants[f"{mode}_{prec}"] = {"steps_per_s": round(1000.0 / (tv / max(20, args.steps // 4)), 1)}
-        pv.close()
+    e2e_err = rel_rms(fh.double().numpy(), f_fp32c)
+    plan.close()
 
     # particle_map, scatter, make_rho, energy_final, fieldforce, and either green (the 3-D
     # transforms in cuFFT, not ours) or the three hand-written Poisson-solve kernels
     launches_per_step = 8 if own_fft else 6
     line = {
-        "metric": metric_name(), "value": round(steps_per_s, 2), "unit": "steps/s", "n_gpus": world,
+        "metric": metric_name(), "value": round(steps_per_s, 3), "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32c", "data": "synthetic",
         "config": config_dict(w, {"parallelism": "replicas" if world > 1 else "single",
                                   "fieldforce_variant": "tile-staged" if variant & 1 else "per-particle L1",
-                                  "poisson_solve": "hand-written FFT" if own_fft else "cuFFT"}),
-        "mparticles_per_s": round(world * N / (ms_per_step * 1e-3) / 1e6, 2),
-        "rel_force_err_vs_fp64": rel_err, "rel_energy_err_vs_fp64": e_err,
+                                  "poisson_solve": "hand-written FFT" if own_fft else "cuFFT",
+                                  "variant_mask": int(variant), "g_ewald": round(g, 8)}),
+        "mparticles_per_s": round(world * w.n / (ms_per_step * 1e-3) / 1e6, 2),
+        "error_vs_fp64_form": err_fp64,
+        "meets_1e-4_force": err_fp64["force_rel_rms"] <= 1e-4,
         "ms_per_step_without_kernel_events": round(ms_plain, 5),
-        "steps_per_s_without_kernel_events": round(world * 1000.0 / ms_plain, 2),
+        "steps_per_s_without_kernel_events": round(world * 1000.0 / ms_plain, 3),
         "roofline": roof,
-        "onchip": onchip_make_rho(N, w.order, stage_ms["make_rho"], clocks_rep.get("sm_mhz")),
-        "e2e": {"value": round(world / e2e_s, 2), "unit": "steps/s", "h2d_bytes_per_step": int(16 * N),
-                "d2h_bytes_per_step": int(12 * N + 56)},
+        "onchip": onchip_make_rho(w.n, w.order, stages["make_rho"], clocks_rep.get("sm_mhz")),
+        "e2e": {"value": round(world / e2e_s, 3), "unit": "steps/s", "h2d_bytes_per_step": int(16 * w.n),
+                "d2h_bytes_per_step": int(12 * w.n + 56), "call": "pppm_compute_host, pinned host buffers",
+                "force_rel_rms_vs_device_call": e2e_err},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks_rep,
-        "variants": variants,
     }
-    return line
+    return line, (f_fp32c, ev_fp32c, g)
 
 
 # ---------------------------------------------------------------------------
 # extra workloads (rank 0)
 # ---------------------------------------------------------------------------
-def large_leg(torch, flush, steps=30):
-    """2,048,001 water-like charges, 256^3, P=7, ad, FP32C, one graph per step."""
+def c2_leg(torch, flush, steps=400):
+    """The 32,001-charge water-like system (68 A cube, 64^3, P=5): ik FP32C
+    (autotuned; the hand-written Poisson solve), with its own roofline, the
+    host-buffer call, and the ad / FP64 forms."""
     from paper_1702_04250_gb300 import pppm
-    from paper_1702_04250_gb300.workloads import config
 
-    w = config("c3")
+    w = workload("c2")
     g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
-    x = torch.tensor(w.x, dtype=torch.float32, device="cuda")
-    q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
-    plan = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode="ad", precision="fp32c", qqrd2e=w.qqrd2e, graph=True)
-    variant = plan.autotune(x, q)
+    x32 = torch.tensor(w.x, dtype=torch.float32, device="cuda")
+    q32 = torch.tensor(w.q, dtype=torch.float32, device="cuda")
+    x64, q64 = x32.double(), q32.double()
+    plan = make_plan(w, g, "ik", "fp32c")
     f = torch.empty((w.n, 3), dtype=torch.float32, device="cuda")
     ev = torch.zeros(8, dtype=torch.float64, device="cuda")
-    t_plain, _ = time_steps(torch, plan, x, q, f, ev, steps, 3, flush, profile=False, sync_ranks=False)
-    _, stage = time_steps(torch, plan, x, q, f, ev, steps, 3, flush, profile=True, sync_ranks=False)
-    ms = t_plain / steps
-    # error of this form against the FP64 form on a 1 % subsample (every 100th charge)
-    p64 = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode="ad", precision="fp64", qqrd2e=w.qqrd2e)
-    f64, ev64 = p64.compute(x.double(), q.double())
+    variant = plan.autotune(x32, q32)
+    plan.compute(x32, q32, f, ev)
+    plan.sync()
+    p64 = make_plan(w, g, "ik", "fp64", graph=False)
+    f64, ev64 = p64.compute(x64, q64)
     p64.sync()
-    sub = slice(0, w.n, 100)
-    a = f[sub].double().cpu().numpy()
-    b = f64[sub].cpu().numpy()
-    err = math.sqrt(float(np.sum((a - b) ** 2) / np.sum(b ** 2)))
-    e_err = abs(ev[0].item() - ev64[0].item()) / abs(ev64[0].item())
+    err = result_errors(f.double().cpu().numpy(), ev[:7].cpu().numpy(), f64.cpu().numpy(), ev64.cpu().numpy())
     p64.close()
-    N, M = w.n, int(np.prod(w.mesh))
+    _, disc = time_steps(torch, plan, x32, q32, f, ev, 20, 3, flush, profile=True, sync_ranks=False)
+    t_ms, stages = time_steps(torch, plan, x32, q32, f, ev, steps, 10, flush, profile=["make_rho", "fieldforce"],
+                              sync_ranks=False, every=10)
+    t_plain, _ = time_steps(torch, plan, x32, q32, f, ev, steps, 3, flush, sync_ranks=False)
     peak, kind = measured_peak()
-    alg = {"make_rho": 20 * N + 4 * M, "fieldforce": 4 * M + 36 * N}
-    roof = {}
-    for k, nbytes in alg.items():
-        achieved = nbytes / (stage[k] * 1e-3) / 1e9
-        src = "paper_1702_04250_gb300/csrc/" + ("k_rho.cu" if k == "make_rho" else "k_force.cu")
-        # the committed capture is of the per-particle fieldforce (the ad default)
-        tr = known_traffic(k, "c3", src) if (k == "make_rho" or not variant & 1) else None
-        roof[k] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                   "frac": round(achieved / peak, 4), "traffic": tr, "alg_bytes_per_launch": int(nbytes),
-                   "avg_launch_ms": round(stage[k], 4), "peak_source": kind}
+    src = "paper_1702_04250_gb300/csrc/"
+    roof = {"make_rho": kernel_roofline("make_rho", w, stages["make_rho"], True, peak, kind, src + "k_rho.cu",
+                                        not variant & 4),
+            "fieldforce": kernel_roofline("fieldforce", w, stages["fieldforce"], True, peak, kind,
+                                          src + "k_force.cu", bool(variant & 1))}
+    xh = torch.tensor(w.x, dtype=torch.float32).pin_memory()
+    qh = torch.tensor(w.q, dtype=torch.float32).pin_memory()
+    fh = torch.empty((w.n, 3), dtype=torch.float32).pin_memory()
+    evh = torch.empty(8, dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        plan.compute_host_into(w.n, xh.data_ptr(), qh.data_ptr(), fh.data_ptr(), evh.data_ptr())
+    ne = max(20, steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        plan.compute_host_into(w.n, xh.data_ptr(), qh.data_ptr(), fh.data_ptr(), evh.data_ptr())
+    e2e_s = (time.perf_counter() - t0) / ne
     plan.close()
-    return {"workload": "water-like 682,667 molecules (2,048,001 charges), 272 A cube, mesh 256^3, order 7, ad, FP32C",
-            "steps_per_s": round(1000.0 / ms, 2), "ms_per_step": round(ms, 4),
-            "mparticles_per_s": round(N / (ms * 1e-3) / 1e6, 1),
-            "rel_force_err_vs_fp64_1pct_subsample": err, "rel_energy_err_vs_fp64": e_err,
+    variants = {}
+    ev2 = torch.zeros(8, dtype=torch.float64, device="cuda")
+    for mode, prec, xx, qq in (("ad", "fp32c", x32, q32), ("ik", "fp64", x64, q64), ("ad", "fp64", x64, q64)):
+        pv = make_plan(w, g, mode, prec)
+        fv = torch.empty((w.n, 3), dtype=xx.dtype, device="cuda")
+        nv = max(20, steps // 4)
+        tv, _ = time_steps(torch, pv, xx, qq, fv, ev2, nv, 3, flush, sync_ranks=False)
+        variants[f"{mode}_{prec}"] = {"steps_per_s": round(1000.0 / (tv / nv), 1)}
+        pv.close()
+    ms = t_ms / steps
+    return {"workload": "water-like 10,667 molecules (32,001 charges), 68 A cube, mesh 64^3, order 5, ik, FP32C",
+            "steps_per_s": round(1000.0 / ms, 1), "ms_per_step": round(ms, 5),
+            "steps_per_s_without_kernel_events": round(1000.0 * steps / t_plain, 1),
+            "mparticles_per_s": round(w.n / (ms * 1e-3) / 1e6, 1),
+            "error_vs_fp64_form": err, "variant_mask": int(variant),
             "fieldforce_variant": "tile-staged" if variant & 1 else "per-particle L1",
-            "stage_ms": {k: round(v, 4) for k, v in stage.items()},
-            "roofline": roof,
-            "onchip_make_rho": onchip_make_rho(N, w.order, stage["make_rho"], None),
-            "mesh_stage_gbs": mesh_stage_gbs(w.mesh, stage),
-            "timing": f"{steps} graph steps, L2 flushed before each; stage times from a second pass with stage events"}
+            "poisson_solve": "hand-written FFT" if variant & 8 else "cuFFT",
+            "roofline": roof, "stage_ms_all_events": {k: round(v, 5) for k, v in disc.items()},
+            "onchip_make_rho": onchip_make_rho(w.n, w.order, stages["make_rho"], None),
+            "e2e_steps_per_s": round(1.0 / e2e_s, 1), "variants": variants,
+            "hbm_fraction_note": "1 MB mesh: every kernel is latency-bound, one partial wave; the HBM fraction is "
+                                 "not meaningful at this size",
+            "timing": f"{steps} graph steps, L2 flushed before each; every 10th with events around make_rho and "
+                      f"fieldforce"}
 
 
 def real_leg(torch, flush, steps=30):
     """Real-space part of the Ewald split on the water-like 32,001 charges,
     r_C = 10 A, FP32, against the FP64 form."""
     from paper_1702_04250_gb300 import pppm
-    from paper_1702_04250_gb300.workloads import config
 
-    w = config("c2")
+    w = workload("c2")
     g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
     out = {}
     for prec in ("fp32", "fp64"):
@@ -469,13 +587,12 @@ def real_leg(torch, flush, steps=30):
         rs.close()
     ms, f32, cells = out["fp32"]
     f64 = out["fp64"][1]
-    err = math.sqrt(float(np.sum((f32 - f64) ** 2) / np.sum(f64 ** 2)))
     V = float(np.prod(w.box))
     pairs = w.n * (w.n / V) * 4.0 / 3.0 * math.pi * w.r_cut ** 3  # ordered pairs within r_C
     return {"workload": "water-like 32,001 charges, 68 A cube, r_C = 10 A, erfc real-space sum, FP32",
             "cells": list(cells), "ms_per_call": round(ms, 4), "calls_per_s": round(1000.0 / ms, 1),
             "pairs_within_cutoff_per_s": float(f"{pairs / (ms * 1e-3):.4g}"),
-            "fp64_ms_per_call": round(out["fp64"][0], 4), "rel_force_err_fp32_vs_fp64": err,
+            "fp64_ms_per_call": round(out["fp64"][0], 4), "rel_force_err_fp32_vs_fp64": rel_rms(f32, f64),
             "timing": f"{steps} calls, L2 flushed before each"}
 
 
@@ -485,9 +602,8 @@ def autograd_leg(torch, flush, steps=30):
     gradients (dE/dx, dE/dq: one pppm_energy_grad call, what the autograd
     Function runs), FP32C and FP64, one graph per force step."""
     from paper_1702_04250_gb300 import pppm
-    from paper_1702_04250_gb300.workloads import config
 
-    w = config("c5")
+    w = workload("c5")
     g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
     out = {}
     for prec in ("fp32c", "fp64"):
@@ -531,16 +647,17 @@ def mesh_leg(torch, flush, steps=40):
     (2^3 3^2), with g held fixed), and which order meets the target fastest
     (orders 3-7, each with its chosen mesh)."""
     from paper_1702_04250_gb300 import pppm
-    from paper_1702_04250_gb300.workloads import config
 
-    w = config("c2")
+    w = workload("c2")
     q2 = float(np.sum(w.q ** 2))
     choice = {}
-    for name, kind in (("primes_le_7", pppm.FFT_SMOOTH), ("powers_of_two", pppm.FFT_POW2)):
-        t0 = time.perf_counter()
-        mesh, g, err = pppm.choose_mesh(w.box, w.n, q2, w.order, w.r_cut, w.rel_acc, kind)
-        choice[name] = {"mesh": list(mesh), "g_ewald": round(g, 6), "est_rms_force_err": float(f"{err:.4g}"),
-                        "choose_ms": round((time.perf_counter() - t0) * 1e3, 1)}
+    for mode in ("ik",):
+        for name, kind in (("primes_le_7", pppm.FFT_SMOOTH), ("powers_of_two", pppm.FFT_POW2)):
+            t0 = time.perf_counter()
+            mesh, g, err = pppm.choose_mesh(w.box, w.n, q2, w.order, w.r_cut, w.rel_acc, kind, mode=mode)
+            choice[f"{mode}_{name}"] = {"mesh": list(mesh), "g_ewald": round(g, 6),
+                                        "est_rms_force_err": float(f"{err:.4g}"),
+                                        "choose_ms": round((time.perf_counter() - t0) * 1e3, 1)}
     g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, q2, w.box)
     x = torch.tensor(w.x, dtype=torch.float32, device="cuda")
     q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
@@ -555,7 +672,6 @@ def mesh_leg(torch, flush, steps=40):
         sizes[str(m)] = {"us_per_step": round(tot / steps * 1e3, 1),
                          "est_rms_force_err": float(f"{pppm.kspace_error(w.box, (m,) * 3, w.order, g, w.n, q2):.4g}")}
         plan.close()
-    # the order that meets the target fastest (a larger stencil allows a coarser mesh)
     orders = []
     for order in (3, 4, 5, 6, 7):
         for name, kind in (("primes_le_7", pppm.FFT_SMOOTH), ("powers_of_two", pppm.FFT_POW2)):
@@ -567,8 +683,8 @@ def mesh_leg(torch, flush, steps=40):
             orders.append({"order": order, "sizes": name, "mesh": list(mesh), "est_rms_force_err": float(f"{err:.4g}"),
                            "us_per_step": round(tot / steps * 1e3, 1)})
             plan.close()
-    return {"workload": "water-like 32,001 charges, 68 A cube, P=5, ik, r_C = 10 A, target 1e-4",
-            "choice": choice, "step_by_mesh_edge_fp32c": sizes, "order_sweep_fp32c": orders,
+    return {"workload": "water-like 32,001 charges, 68 A cube, P=5, r_C = 10 A, target 1e-4",
+            "choice": choice, "step_by_mesh_edge_fp32c": sizes, "order_sweep_fp32c_ik": orders,
             "timing": f"{steps} graph steps per mesh, L2 flushed before each"}
 
 
@@ -593,7 +709,7 @@ def batch_leg(torch, flush, steps=20):
         b = pppm.PPPMBatch(systems, mode="ik", precision=prec, qqrd2e=C, graph=True)
         x = torch.tensor(xs, dtype=dt, device="cuda")
         q = torch.tensor(qs, dtype=dt, device="cuda")
-        b.autotune(x, q)
+        choice = b.autotune(x, q)
         f = torch.empty((ntot, 3), dtype=dt, device="cuda")
         for _ in range(3):
             b.compute(x, q, f)
@@ -613,13 +729,11 @@ def batch_leg(torch, flush, steps=20):
         out = f.double().cpu().numpy()
         info = b.info()
         b.close()
-        return tot / steps, out, info
+        return tot / steps, out, info, choice
 
-    ms32, f32, info = time_batch("fp32c")
-    ms64, f64, _ = time_batch("fp64")
-    err = math.sqrt(float(np.sum((f32 - f64) ** 2) / np.sum(f64 ** 2)))
+    ms32, f32, info, choice = time_batch("fp32c")
+    ms64, f64, _, _ = time_batch("fp64")
 
-    # the same 256 systems as 256 single-system plans, one graph each, back to back
     plans, xt, qt, ft = [], [], [], []
     stream = torch.cuda.Stream()
     for sd in systems:
@@ -652,10 +766,10 @@ def batch_leg(torch, flush, steps=20):
                         f"meshes 16^3-64^3 ({info['mesh_classes']} mesh classes), orders 3/5/7, ik",
             "fp32c": {"calls_per_s": round(1000.0 / ms32, 2), "ms_per_call": round(ms32, 4),
                       "systems_per_s": round(len(systems) * 1000.0 / ms32, 1),
-                      "mparticles_per_s": round(ntot / (ms32 * 1e-3) / 1e6, 1)},
+                      "mparticles_per_s": round(ntot / (ms32 * 1e-3) / 1e6, 1), "autotuned_mask": int(choice)},
             "fp64": {"calls_per_s": round(1000.0 / ms64, 2), "ms_per_call": round(ms64, 4)},
             "fp32c_over_fp64": round(ms64 / ms32, 3),
-            "rel_force_err_fp32c_vs_fp64": err,
+            "rel_force_err_fp32c_vs_fp64": rel_rms(f32, f64),
             "single_plans_fp32c": {"ms_for_all_systems": round(ms_single, 4),
                                    "batch_speedup": round(ms_single / ms32, 2)},
             "timing": f"{steps} graph calls, L2 flushed before each"}
@@ -664,85 +778,210 @@ def batch_leg(torch, flush, steps=20):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_rate(w, budget_s=12.0, max_steps=50):
+def oracle_setup(w, mode=HEADLINE_MODE):
+    """g, G and (ad) the self-force coefficients of the oracle for w (untimed setup)."""
     from oracle import OraclePPPM, estimate_g_ewald
 
     g = estimate_g_ewald(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
-    o = OraclePPPM(w.box, w.mesh, w.order, g, "ik", w.qqrd2e)
+    return OraclePPPM(w.box, w.mesh, w.order, g, mode, w.qqrd2e)
+
+
+def oracle_sampled_step(o, x, q, stride):
+    """One oracle step of the workload, its stages called in the oracle's own
+    order, with the per-particle interpolation (fieldforce) run on every
+    stride-th charge only and its time scaled by stride: every charge's force
+    is an independent stencil sum, so the full step's fieldforce takes
+    stride times as long.  make_rho, the Poisson solve and the energy/virial
+    run on the whole workload.  Returns (estimated full-step seconds, the
+    sample's CPU seconds, outputs)."""
+    from oracle import pppm_oracle as po
+
+    t = {}
+    t0 = time.perf_counter()
+    rho = po.make_rho(x, q, o.box, o.mesh, o.P, o.lut)
+    t["make_rho"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    if o.mode == "ik":
+        rho_hat, fields = po.poisson_ik(rho, o.G, o.box)
+    else:
+        rho_hat, phi = po.poisson_ad(rho, o.G)
+    t["poisson"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    E_mesh, vir = po.energy_virial_mesh(rho_hat, o.G, o.box, o.mesh, o.g, o.C)
+    energy = E_mesh + po.self_energy(q, o.g, o.C) + po.background_energy(q, o.g, o.C, o.box)
+    t["energy_virial"] = time.perf_counter() - t0
+    sub = slice(0, x.shape[0], stride)
+    t0 = time.perf_counter()
+    if o.mode == "ik":
+        f = po.fieldforce_ik(x[sub], q[sub], fields, o.box, o.mesh, o.P, o.C, o.lut)
+    else:
+        f = po.fieldforce_ad(x[sub], q[sub], phi, o.box, o.mesh, o.P, o.C, o.sf, o.lut)
+    t["fieldforce_sample"] = time.perf_counter() - t0
+    sample_s = sum(t.values())
+    est = t["make_rho"] + t["poisson"] + t["energy_virial"] + stride * t["fieldforce_sample"]
+    ev = np.concatenate([[energy], vir])
+    return est, sample_s, {"f_sub": f, "ev": ev, "stage_s": {k: round(v, 3) for k, v in t.items()}}
+
+
+def _replica_worker(args):
+    """One oracle replica in its own (spawned) process: regenerate the
+    workload, wait at the barrier, run one sampled step with the parent's
+    oracle setup."""
+    name, o, stride, barrier = args
+    w = workload(name)
     x = w.x.astype(np.float32).astype(np.float64)
     q = w.q.astype(np.float32).astype(np.float64)
-    o.compute(x, q)
-    n = 0
+    barrier.wait()
     t0 = time.perf_counter()
-    while n < max_steps and time.perf_counter() - t0 < budget_s:
-        o.compute(x, q)
-        n += 1
-    dt = time.perf_counter() - t0
-    return n / dt, n, dt
+    est, sample_s, _ = oracle_sampled_step(o, x, q, stride)
+    return est, sample_s, time.perf_counter() - t0
 
 
-def cpu_cores_used():
-    # numpy's FFT and bincount run on one thread
-    return 1
+def host_memory_budget():
+    """Bytes the oracle replicas may use: 40 % of the smaller of the host's
+    available memory and this process group's cgroup allowance."""
+    avail = 0
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                avail = int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    try:
+        lim = open("/sys/fs/cgroup/memory.max").read().strip()
+        cur = int(open("/sys/fs/cgroup/memory.current").read().strip())
+        if lim != "max":
+            avail = min(avail, int(lim) - cur)
+    except (OSError, ValueError):
+        pass
+    return int(0.4 * max(avail, 0))
 
 
-def cpu_baseline_obj(rate, sample):
-    """The oracle's timing: the threads it used and the host's core count."""
-    return {"value": round(rate, 4), "unit": "steps/s", "cores": cpu_cores_used(),
-            "host_cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+# peak resident memory of one sampled oracle step of the 2M-charge workload
+# (measured 11.6 GB: the B-spline recursion keeps ~30 [N, P] float64 arrays), with margin
+ORACLE_REPLICA_BYTES = 14 << 30
+
+
+def oracle_all_cores(w, o, stride, max_replicas=None):
+    """Independent oracle replicas, one per host core (bounded by free
+    memory), each running one sampled step at the same time: the host's
+    throughput on this workload with every core busy.  Returns a dict or
+    None when only one replica fits."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    r = min(cores, max(1, host_memory_budget() // ORACLE_REPLICA_BYTES))
+    if max_replicas:
+        r = min(r, max_replicas)
+    if r < 2:
+        return None
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        barrier = mgr.Barrier(r)
+        with ctx.Pool(r) as pool:
+            t0 = time.perf_counter()
+            res = pool.map(_replica_worker, [(w.name, o, stride, barrier)] * r)
+            wall = time.perf_counter() - t0
+    rate = sum(1.0 / est for est, _, _ in res)
+    return {"value": rate, "replicas": r, "per_replica_est_s": [round(e, 2) for e, _, _ in res],
+            "per_replica_sample_s": [round(s, 2) for _, s, _ in res], "wall_s": round(wall, 1)}
+
+
+def cpu_baseline_leg(w, gpu_out=None, all_cores=True):
+    """The FP64 oracle on the host cores: one core, then (all_cores) one
+    replica per core.  With gpu_out = (FP32C forces, energy/virial), also the
+    error of the GPU results against the oracle (forces on the subsample)."""
+    o = oracle_setup(w)
+    x = w.x.astype(np.float32).astype(np.float64)  # the GPU's float32 inputs, exactly (reading R15)
+    q = w.q.astype(np.float32).astype(np.float64)
+    est, sample_s, out = oracle_sampled_step(o, x, q, SUBSAMPLE)
+    one = {"value": round(1.0 / est, 5), "unit": "steps/s", "cores": 1, "kind": "oracle",
+           "est_full_step_s": round(est, 2), "stage_s": out["stage_s"],
+           "sample": f"one step of the same workload: make_rho, Poisson solve and energy/virial on all "
+                     f"{w.n:,} charges, fieldforce on every {SUBSAMPLE}th charge with its time x{SUBSAMPLE} "
+                     f"({sample_s:.1f} s of CPU work)"}
+    res = {"one_core": one}
+    if all_cores:
+        ac = oracle_all_cores(w, o, SUBSAMPLE)
+        if ac:
+            res["all_cores"] = {"value": round(ac["value"], 5), "unit": "steps/s", "cores": ac["replicas"],
+                                "kind": "oracle", "wall_s": ac["wall_s"],
+                                "per_replica_est_s": ac["per_replica_est_s"],
+                                "sample": f"{ac['replicas']} independent replicas (spawned processes, one per "
+                                          f"core up to 40 % of free memory at 14 GiB each), each one sampled "
+                                          f"step as above, run at the same time; value = sum of their rates"}
+    if gpu_out is not None:
+        f32c, ev32c = gpu_out[0], gpu_out[1]
+        res["gpu_error_vs_oracle"] = dict(result_errors(f32c[::SUBSAMPLE], ev32c, out["f_sub"], out["ev"]),
+                                          forces_on=f"every {SUBSAMPLE}th charge ({out['f_sub'].shape[0]:,})")
+    return res
+
+
+def cpu_baseline_obj(res):
+    best = res.get("all_cores") or res["one_core"]
+    obj = {k: best[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    obj["host_cores"] = os.cpu_count()
+    obj["one_core"] = res["one_core"]
+    if "all_cores" in res:
+        obj["all_cores"] = res["all_cores"]
+    return obj
 
 
 def reference_arm(args, rank, world):
     if rank != 0:
         return None
     w = workload()
-    steps = max(1, args.steps)
-    budget = 60.0
-    rate, n, dt = oracle_rate(w, budget_s=budget, max_steps=steps)
-    return {"impl": "reference", "metric": metric_name(), "value": round(rate, 4), "unit": "steps/s",
-            "n_gpus": world, "steps": n, "warmup": 1, "ms_per_step": round(1000.0 / rate, 3),
+    res = cpu_baseline_leg(w, None, all_cores=True)
+    obj = cpu_baseline_obj(res)
+    rate = obj["value"]
+    n_steps = obj.get("all_cores", {}).get("cores", 1)
+    return {"impl": "reference", "metric": metric_name(), "value": rate, "unit": "steps/s",
+            "n_gpus": world, "steps": n_steps, "warmup": 0, "ms_per_step": round(1000.0 / rate, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(w, {"precision": "fp64 (oracle)"}),
-            "cpu_baseline": cpu_baseline_obj(rate, f"{n} full oracle steps of the workload ({dt:.1f} s)"),
-            "e2e": {"value": round(rate, 4), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": obj,
+            "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the 2M-charge and batched workloads")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return  # rank 0 alone times the oracle
+        line = reference_arm(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
     if world > 1:
         import torch
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        torch.distributed.init_process_group("nccl" if args.impl == "ours" else "gloo")
-    if args.impl == "reference":
-        line = reference_arm(args, rank, world)
-        if line is not None:
-            print(json.dumps(line))
-        return
-    line = gpu_arm(args, rank, world)
+        torch.distributed.init_process_group("nccl")
+    line, gpu_out = gpu_arm(args, rank, world)
     if rank == 0 and not args.no_extra:
         import torch
 
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-        line["extra"] = {"large": large_leg(torch, flush), "batch": batch_leg(torch, flush),
+        line["extra"] = {"c2": c2_leg(torch, flush), "batch": batch_leg(torch, flush),
                          "real_space": real_leg(torch, flush), "mesh_choice": mesh_leg(torch, flush),
                          "autograd_c5": autograd_leg(torch, flush)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = cpu_baseline_leg(workload(), gpu_out, all_cores=True)
+        line["cpu_baseline"] = cpu_baseline_obj(res)
+        line["error_vs_oracle"] = res["gpu_error_vs_oracle"]
     if rank == 0:
-        if not args.no_cpu_baseline:
-            rate, n, dt = oracle_rate(workload())
-            line["cpu_baseline"] = cpu_baseline_obj(rate, f"{n} full FP64 oracle steps of the same workload ({dt:.1f} s)")
-        print(json.dumps(line))
+        print(json.dumps(line), flush=True)
     if world > 1:
         import torch
 

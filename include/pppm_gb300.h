@@ -267,9 +267,11 @@ int pppm_plan_info(const pppm_plan *p, int64_t info[10]);
  * make_rho as in pppm_compute, FP32 arithmetic).  The paper has no
  * counterpart: this serves callers that cannot call cudaMalloc where they
  * need the mesh -- a host engine that owns all device memory through its own
- * pool, code running under stream capture, or a step loop that must not pay
- * the device-wide synchronisation of cudaMalloc/cudaFree.
- *   box[3], mesh[3], order   as for pppm_setup (order 2..7, mesh >= order)
+ * pool and budget, or a step loop that must not pay the device-wide
+ * synchronisation of cudaMalloc/cudaFree.
+ *   box[3], mesh[3], order   as for pppm_setup (order 2..7, mesh >= order;
+ *                            box edges finite, and L, 1/L and M/L finite
+ *                            normal floats)
  *   precision               PPPM_FP32 or PPPM_FP32C
  *   n                       0 <= n <= 65536
  *   x, q                    device, float [n][3] and [n]
@@ -282,11 +284,21 @@ int pppm_plan_info(const pppm_plan *p, int64_t info[10]);
  * by all calls: it keeps the previous call's contents (the call clears what
  * must start at zero), and calls that overlap on the GPU race -- serialise
  * them.  The first call on a device looks the array's address up and sets
- * the kernels' shared-memory limits; make it before any stream capture.
- * Allocates nothing.  Asynchronous. */
+ * the kernels' shared-memory limits, and both are cached for the process:
+ * make that first call before any stream capture, and do not reset the
+ * device (cudaDeviceReset) between calls.  Allocates nothing.  Asynchronous:
+ * device-side findings (a non-finite position or charge, which is counted as
+ * zero; a failed consistency check, whose work is skipped) are only visible
+ * through pppm_make_rho_noalloc_status. */
 int pppm_make_rho_noalloc(const double box[3], const int mesh[3], int order, int precision,
                           int64_t n, const float *x, const float *q, float *rho,
                           void *cuda_stream);
+/* Status of the last pppm_make_rho_noalloc on this device: synchronises
+ * cuda_stream (the stream that call used), then returns PPPM_ENONFINITE if it
+ * met a non-finite input, PPPM_EINTERNAL if a device consistency check failed,
+ * else PPPM_OK (PPPM_ECUDA on a CUDA error).  Call it after the call and
+ * before the next one, which clears the word.  Allocates nothing. */
+int pppm_make_rho_noalloc_status(void *cuda_stream);
 
 /* ---- Batched path: many independent systems per call -------------------
  * The same three PPPM steps (Sec. 2.1) for nsys unrelated periodic systems

@@ -2,10 +2,9 @@
 //
 // Some callers cannot allocate device memory at the point where they need a
 // charge mesh: a host MD engine that owns all GPU memory through its own pool
-// and budget, a code path that runs inside CUDA stream capture (where
-// cudaMalloc is not allowed), or a latency-critical step loop that must not
-// pay the implicit device-wide synchronisation of cudaMalloc/cudaFree.  For
-// them pppm_make_rho_noalloc builds the mesh without any allocation: the sort
+// and budget, or a latency-critical step loop that must not pay the implicit
+// device-wide synchronisation of cudaMalloc/cudaFree.  For them
+// pppm_make_rho_noalloc builds the mesh without any allocation: the sort
 // scratch that a plan would own lives in one file-scope device array of fixed
 // size, which every GPU that loads this library keeps until the process exits.
 // The caller still passes the inputs and the output mesh.
@@ -14,10 +13,16 @@
 //  - All calls share the same scratch array, so calls that may overlap on the
 //    GPU (different streams, or several host threads) race and corrupt each
 //    other's result.  Serialise them (one stream is enough).
-//  - The first call on each device looks up the array's device address; make
-//    that first call before any stream capture.
+//  - The first call on each device looks up the array's device address (and
+//    sets the kernels' shared-memory limits) and caches both for the life of
+//    the process; make that first call before any stream capture, and do not
+//    reset the device (cudaDeviceReset) between calls.
 //  - Sizes beyond the fixed limits are rejected with PPPM_EINVAL before any
 //    GPU work.
+//  - Non-finite inputs and failed consistency checks are flagged in an error
+//    word inside the array; pppm_make_rho_noalloc_status reads it back.  The
+//    next call clears it.
+#include <cmath>
 #include <mutex>
 
 #include "pppm_common.cuh"
@@ -78,8 +83,12 @@ extern "C" int pppm_make_rho_noalloc(const double box[3], const int mesh[3], int
     if (n < 0 || n > NA_MAX_N) return PPPM_EINVAL;
     if (n > 0 && (!x || !q)) return PPPM_EINVAL;
     int T[3], TE[3];
-    for (int d = 0; d < 3; ++d)
-        if (!(box[d] > 0) || mesh[d] < order || mesh[d] > MAX_MESH) return PPPM_EINVAL;
+    for (int d = 0; d < 3; ++d) {
+        if (!(box[d] > 0) || !std::isfinite(box[d]) || mesh[d] < order || mesh[d] > MAX_MESH) return PPPM_EINVAL;
+        // the kernels work with float copies of L, 1/L and M/L: each must be a finite normal float
+        const float fl = (float)box[d], fil = (float)(1.0 / box[d]), fih = (float)((double)mesh[d] / box[d]);
+        if (!std::isnormal(fl) || !std::isnormal(fil) || !std::isnormal(fih)) return PPPM_EINVAL;
+    }
     tile_shape(mesh, false, T, TE);
     const int ntiles = T[0] * T[1] * T[2];
     if (ntiles > NA_MAX_TILES) return PPPM_EINVAL;
@@ -138,4 +147,21 @@ extern "C" int pppm_make_rho_noalloc(const double box[3], const int mesh[3], int
     if (n > 0) launch_sort<float>(g, n, x, q, b, s);
     launch_make_rho<float>(g, n, b, rho, precision == PPPM_FP32C, s);
     return cudaGetLastError() == cudaSuccess ? PPPM_OK : PPPM_ECUDA;
+}
+
+extern "C" int pppm_make_rho_noalloc_status(void *cuda_stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PPPM_ECUDA;
+    unsigned char *base = nullptr;
+    const int rc = scratch_address(dev, &base);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int err = 0;  // host stack word: a pageable copy, complete once the stream is synchronised
+    if (cudaMemcpyFromSymbolAsync(&err, g_noalloc_scratch, sizeof(int), OFF_MISC, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return PPPM_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PPPM_ECUDA;
+    if (err & ERR_NONFINITE) return PPPM_ENONFINITE;
+    if (err & ERR_INTERNAL) return PPPM_EINTERNAL;
+    return PPPM_OK;
 }

@@ -80,8 +80,60 @@ def test_mesh_stage_bytes():
 
 
 def test_cpu_baseline_object():
+    """The reported baseline is the all-cores figure when replicas ran, with
+    the one-core figure beside it."""
     import bench
 
-    o = bench.cpu_baseline_obj(5.12345, "50 steps")
-    assert o == {"value": 5.1235, "unit": "steps/s", "cores": 1, "host_cores": os.cpu_count(),
-                 "kind": "oracle", "sample": "50 steps"}
+    one = {"value": 0.01, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": "s1"}
+    o = bench.cpu_baseline_obj({"one_core": one})
+    assert o["value"] == 0.01 and o["cores"] == 1 and o["host_cores"] == os.cpu_count()
+    allc = {"value": 0.1, "unit": "steps/s", "cores": 12, "kind": "oracle", "sample": "s12"}
+    o = bench.cpu_baseline_obj({"one_core": one, "all_cores": allc})
+    assert o["value"] == 0.1 and o["cores"] == 12 and o["one_core"] == one and o["sample"] == "s12"
+
+
+def test_algorithmic_bytes_follow_the_scope_table():
+    """Per-launch algorithmic bytes on the 2,048,001-charge 256^3 workload:
+    make_rho 16N + 8M, ad fieldforce 4M + 32N, ik fieldforce 16M + 32N,
+    sort 40N, ad green 4M + 2M + 4M (half spectrum)."""
+    import bench
+
+    n, mesh = 2048001, (256, 256, 256)
+    M, mh = 256 ** 3, 256 * 256 * 129
+    assert bench.alg_bytes("make_rho", n, mesh, False) == 16 * n + 8 * M
+    assert bench.alg_bytes("fieldforce", n, mesh, False) == 4 * M + 32 * n
+    assert bench.alg_bytes("fieldforce", n, mesh, True) == 16 * M + 32 * n
+    assert bench.alg_bytes("sort", n, mesh, False) == 40 * n
+    assert bench.alg_bytes("green", n, mesh, False) == 20 * mh
+    assert abs(bench.alg_bytes("make_rho", n, mesh, False) / 1e6 - 167.0) < 0.5  # 167 MB
+    assert abs(bench.alg_bytes("fieldforce", n, mesh, False) / 1e6 - 132.6) < 0.5
+
+
+def test_sampled_oracle_step_is_the_oracle_step():
+    """The timed CPU sample runs the oracle's own stages: its subsampled
+    forces, energy and virial equal OraclePPPM.compute on the same inputs,
+    and the estimate scales only the fieldforce time."""
+    import numpy as np
+
+    import bench
+    from paper_1702_04250_gb300.workloads import config
+
+    w = config("c1")
+    for mode in ("ik", "ad"):
+        o = bench.oracle_setup(w, mode)
+        est, sample_s, out = bench.oracle_sampled_step(o, w.x, w.q, 7)
+        ref = o.compute(w.x, w.q, subset=np.arange(0, w.n, 7))
+        assert np.allclose(out["f_sub"], ref["f"], rtol=0, atol=1e-12 * np.abs(ref["f"]).max())
+        assert abs(out["ev"][0] - ref["energy"]) <= 1e-12 * abs(ref["energy"])
+        assert np.allclose(out["ev"][1:], ref["virial"], rtol=1e-12, atol=0)
+        st = out["stage_s"]
+        assert est >= sample_s - 0.01
+        assert abs(est - (st["make_rho"] + st["poisson"] + st["energy_virial"] + 7 * st["fieldforce_sample"])) < 0.01
+
+
+def test_oracle_replicas_respect_the_memory_budget(monkeypatch):
+    """No replica run when two do not fit in the memory budget."""
+    import bench
+
+    monkeypatch.setattr(bench, "host_memory_budget", lambda: bench.ORACLE_REPLICA_BYTES + 1)
+    assert bench.oracle_all_cores(None, None, 100) is None
