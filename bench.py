@@ -838,7 +838,7 @@ def _replica_worker(args):
 
 
 def host_memory_budget():
-    """Bytes the oracle replicas may use: 40 % of the smaller of the host's
+    """Bytes the oracle replicas may use: half of the smaller of the host's
     available memory and this process group's cgroup allowance."""
     avail = 0
     try:
@@ -854,12 +854,12 @@ def host_memory_budget():
             avail = min(avail, int(lim) - cur)
     except (OSError, ValueError):
         pass
-    return int(0.4 * max(avail, 0))
+    return int(0.5 * max(avail, 0))
 
 
 # peak resident memory of one sampled oracle step of the 2M-charge workload
 # (measured 11.6 GB: the B-spline recursion keeps ~30 [N, P] float64 arrays), with margin
-ORACLE_REPLICA_BYTES = 14 << 30
+ORACLE_REPLICA_BYTES = 13 << 30
 
 
 def oracle_all_cores(w, o, stride, max_replicas=None):
@@ -908,7 +908,7 @@ def cpu_baseline_leg(w, gpu_out=None, all_cores=True):
                                 "kind": "oracle", "wall_s": ac["wall_s"],
                                 "per_replica_est_s": ac["per_replica_est_s"],
                                 "sample": f"{ac['replicas']} independent replicas (spawned processes, one per "
-                                          f"core up to 40 % of free memory at 14 GiB each), each one sampled "
+                                          f"core up to half the free memory at 13 GiB each), each one sampled "
                                           f"step as above, run at the same time; value = sum of their rates"}
     if gpu_out is not None:
         f32c, ev32c = gpu_out[0], gpu_out[1]

@@ -180,7 +180,8 @@ def test_noalloc_rejects_sizes_beyond_its_limits(torch, L):
     big_mesh = torch.zeros((1,), dtype=torch.float32, device="cuda")
     assert noalloc(L, (10.0,) * 3, (136,) * 3, 5, 1, x, q, big_mesh, stream) == pppm.PPPM_EINVAL
     assert noalloc(L, (10.0,) * 3, (16,) * 3, 5, 0, x, q, rho, stream) == pppm.PPPM_EINVAL  # FP64 not offered
-    # boxes the float kernels cannot represent
-    for bad in ((float("inf"), 10.0, 10.0), (10.0, float("nan"), 10.0), (1e-37, 10.0, 10.0),
+    # boxes the float kernels cannot represent: infinite, NaN, below the smallest normal float
+    # (and 16 / 1e-38 overflows), above the largest float
+    for bad in ((float("inf"), 10.0, 10.0), (10.0, float("nan"), 10.0), (1e-38, 10.0, 10.0),
                 (10.0, 10.0, 1e39)):
         assert noalloc(L, bad, (16,) * 3, 5, 1, x, q, rho, stream) == pppm.PPPM_EINVAL
