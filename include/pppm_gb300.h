@@ -237,7 +237,11 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * times the tiles and CTAs of the sort, make_rho and the tile-staged
  * fieldforce, a larger halo share); not with bit 1.  Bit 5: make_rho's brick
  * laid out with the strides of the largest tile (compile-time offsets); not
- * with bit 2.  Default: bit 4 when the mesh has fewer than 304 tiles of 8^3
+ * with bit 2.  Bit 6: fieldforce runs as a persistent kernel (a few CTAs per
+ * SM walk the tiles) whose CTAs stage the next tile's field brick and
+ * particle records into a second shared-memory buffer while they gather the
+ * current tile (PPPM_FP32 / PPPM_FP32C only; not with bit 0; force steps
+ * only, like bit 0).  Default: bit 4 when the mesh has fewer than 304 tiles of 8^3
  * (two per SM), bit 0 for ik plans whose n_max is at least 16 per tile, bit 3
  * where it is allowed, bit 5.
  * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a

@@ -26,6 +26,8 @@
 // ad self force (paper silent; reading of the Ballenegger-Cerda-Holm form):
 // F_a -= q^2 sum_{n=1,2} c_{a,n} sin(2 pi n u_a), with u_a = n_a - delta_a the
 // grid coordinate, so sin(2 pi n u_a) = -sin(2 pi n delta_a).
+#include <type_traits>
+
 #include "pppm_common.cuh"
 
 namespace pppm {
@@ -40,8 +42,18 @@ __device__ __forceinline__ double4_32a ld4(const double *p) {
     const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
     return make_double4_32a(a.x, a.y, b.x, b.y);
 }
-__device__ __forceinline__ float sin2pi(float x) { return sinpif(2.0f * x); }
-__device__ __forceinline__ double sin2pi(double x) { return sinpi(2.0 * x); }
+// sin(2 pi x) and cos(2 pi x) in one call
+__device__ __forceinline__ void sincos2pi(float x, float &s, float &c) { sincospif(2.0f * x, &s, &c); }
+__device__ __forceinline__ void sincos2pi(double x, double &s, double &c) { sincospi(2.0 * x, &s, &c); }
+
+// The ad self force along one axis, q^2 (c1 sin(2 pi d) + c2 sin(4 pi d)), with
+// sin(4 pi d) = 2 sin(2 pi d) cos(2 pi d) from one sin/cos evaluation.
+template <typename R>
+__device__ __forceinline__ R self_force_axis(R c1, R c2, R d) {
+    R sn, cs;
+    sincos2pi(d, sn, cs);
+    return sn * (c1 + R(2) * c2 * cs);
+}
 
 __device__ __forceinline__ int wrap1(int i, int M) { return i < 0 ? i + M : (i >= M ? i - M : i); }
 
@@ -214,9 +226,9 @@ __device__ __forceinline__ void finish_particle(const Geom<R> &g, const SortBufs
         F2 = s * e2 * g.ih[2];
         if (MODE == 1) {
             const R q2 = qv * qv;
-            F0 += q2 * ((R)c[0] * sin2pi(dx) + (R)c[1] * sin2pi(R(2) * dx));
-            F1 += q2 * ((R)c[2] * sin2pi(dy) + (R)c[3] * sin2pi(R(2) * dy));
-            F2 += q2 * ((R)c[4] * sin2pi(dz) + (R)c[5] * sin2pi(R(2) * dz));
+            F0 += q2 * self_force_axis<R>((R)c[0], (R)c[1], dx);
+            F1 += q2 * self_force_axis<R>((R)c[2], (R)c[3], dy);
+            F2 += q2 * self_force_axis<R>((R)c[4], (R)c[5], dz);
         } else {
             // gradient of the energy: dE/dx = -(uncorrected ad force)
             F0 = -F0; F1 = -F1; F2 = -F2;
@@ -399,10 +411,344 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, Sort
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, double-buffered tile-staged fieldforce (FP32 step types,
+// variant bit 6).  One CTA per SM slot walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; while it gathers tile t from one shared-memory
+// buffer, the copies of tile t + gridDim.x (field brick over the tile plus
+// its P-1 halo, and the tile's particle records, anchors and input indices)
+// are in flight into the other buffer with cp.async, so the HBM/L2 latency
+// of the staging hides behind the gather instead of preceding it.  Each
+// stencil read is then a shared-memory load at a compile-time offset from
+// the particle's run start (brick strides of the widest tile), and the
+// P^3 loads of a group need no address arithmetic.
+//
+// Brick layout: [x][y][z], E = TILE_B + P - 1 points per x and y.  The ik
+// field (MODE 0) keeps E float4 points per z row.  The scalar potential
+// (MODE 1) keeps 16 floats per z row starting at global z = oz - 4 (tile
+// origin oz): with Mz a multiple of 8 and every z tile 8 wide (oz a multiple
+// of 8) each row is four aligned 16-byte copies; other meshes copy the
+// row's E points one by one into the same positions.  Stencil point k of a
+// particle with local anchor az sits at brick z index az + k + ZOFF.
+//
+// Particles of one tile are handled in sub-chunks of CH (the first one
+// staged with the brick, any further one copied when reached).  For the
+// scalar brick each sub-chunk is counting-sorted by the shared-memory bank
+// of its z run start, and a warp's particle groups take particles an NG-th
+// of the sorted list apart, so their loads rarely share a bank.
+// ---------------------------------------------------------------------------
+template <int P, int MODE>
+struct PersistGeom {
+    static constexpr int NT = 256;
+    static constexpr int E = TILE_B + P - 1;                // brick edge (x, y) of the widest tile
+    static constexpr bool VEC = (MODE == 0);                // float4 field points
+    static constexpr int RZ = VEC ? E : 16;                 // z row length (elements)
+    static constexpr int ZOFF = VEC ? 0 : 4 - (P - 1) / 2;  // brick z of stencil point k = az + k + ZOFF
+    static constexpr int ELEM = VEC ? 16 : 4;               // bytes per element
+    static constexpr int BRICK_BYTES = E * E * RZ * ELEM;
+    static constexpr int CH = 256;                          // particles per sub-chunk
+    static constexpr int REC_OFF = BRICK_BYTES;             // float4 records [CH]
+    static constexpr int CELL_OFF = REC_OFF + 16 * CH;      // packed anchors [CH]
+    static constexpr int PERM_OFF = CELL_OFF + 4 * CH;      // input indices [CH]
+    static constexpr int BUF_BYTES = PERM_OFF + 4 * CH;
+    static constexpr size_t BYTES = 2 * (size_t)BUF_BYTES;
+    static_assert(BRICK_BYTES % 16 == 0 && BUF_BYTES % 16 == 0, "16-byte aligned buffer parts");
+    static_assert(VEC || (ZOFF >= 1 && ZOFF + 7 + (P - 1) < RZ), "the 16-float z rows cover every stencil run");
+};
+
+struct TileBox {
+    int ox, oy, oz, Ex, Ey, Ez;  // origin and brick extents (tile width + P - 1)
+};
+__device__ __forceinline__ TileBox tile_box(const Geom<float> &g, int tile) {
+    TileBox t;
+    const int tz = tile % g.T[2];
+    const int ty = (tile / g.T[2]) % g.T[1];
+    const int tx = tile / (g.T[2] * g.T[1]);
+    t.ox = tile_origin(tx, g.T[0], g.M[0]);
+    t.oy = tile_origin(ty, g.T[1], g.M[1]);
+    t.oz = tile_origin(tz, g.T[2], g.M[2]);
+    t.Ex = tile_origin(tx + 1, g.T[0], g.M[0]) - t.ox + g.P - 1;
+    t.Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - t.oy + g.P - 1;
+    t.Ez = tile_origin(tz + 1, g.T[2], g.M[2]) - t.oz + g.P - 1;
+    return t;
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Issue (do not await) the copies of tile `tile` into buffer `buf`: its field
+// brick and its first min(n, CH) particles [s0, s0 + n).
+template <int P, int MODE>
+__device__ __forceinline__ void persist_stage(const Geom<float> &g, const SortBufs &b, const float *__restrict__ field,
+                                              int tile, int s0, int n, unsigned char *buf, bool aligned) {
+    using PG = PersistGeom<P, MODE>;
+    if (n <= 0) return;  // an empty tile needs no brick
+    const TileBox tb = tile_box(g, tile);
+    float *brick = reinterpret_cast<float *>(buf);
+    const int tid = threadIdx.x;
+    const int My = g.M[1], Mz = g.M[2];
+    if (!PG::VEC && aligned) {
+        // rows (ex, ey) of four aligned 16-byte chunks from z = oz - 4 (wrapped; Mz % 4 == 0)
+        const int j = tid & 3;
+        int gz = tb.oz - 4 + 4 * j;
+        gz += (gz < 0) ? Mz : 0;
+        gz -= (gz >= Mz) ? Mz : 0;
+        const int rows = tb.Ex * tb.Ey;
+        const unsigned int inv = (65536u + (unsigned)tb.Ey - 1u) / (unsigned)tb.Ey;  // r / Ey = (r inv) >> 16, r < 256
+        for (int r = tid >> 2; r < rows; r += PG::NT / 4) {
+            const int ex = (int)(((unsigned)r * inv) >> 16), ey = r - ex * tb.Ey;
+            const int gx = wrap1(tb.ox - g.rlo + ex, g.M[0]);
+            const int gy = wrap1(tb.oy - g.rlo + ey, My);
+            cp_async<16>(brick + (ex * PG::E + ey) * PG::RZ + 4 * j, field + ((int64_t)gx * My + gy) * Mz + gz);
+        }
+    } else {
+        // one element per copy: 16 lanes along z (Ez <= 14), 16 rows per pass
+        const int lz = tid & 15, ry = tid >> 4;
+        if (lz < tb.Ez) {
+            const int gz = wrap1(tb.oz - g.rlo + lz, Mz);
+            for (int ex = 0; ex < tb.Ex; ++ex) {
+                const int gx = wrap1(tb.ox - g.rlo + ex, g.M[0]);
+                for (int ey = ry; ey < tb.Ey; ey += PG::NT / 16) {
+                    const int gy = wrap1(tb.oy - g.rlo + ey, My);
+                    const int64_t p = ((int64_t)gx * My + gy) * Mz + gz;
+                    const int e = (ex * PG::E + ey) * PG::RZ + lz + PG::ZOFF;
+                    if (PG::VEC) cp_async<16>(brick + 4 * e, field + 4 * p);
+                    else cp_async<4>(brick + e, field + p);
+                }
+            }
+        }
+    }
+    const int m = min(n, PG::CH);
+    for (int i = tid; i < m; i += PG::NT) {
+        cp_async<16>(buf + PG::REC_OFF + 16 * i, reinterpret_cast<const float4 *>(b.rec) + s0 + i);
+        cp_async<4>(buf + PG::CELL_OFF + 4 * i, b.cell + s0 + i);
+        cp_async<4>(buf + PG::PERM_OFF + 4 * i, b.perm + s0 + i);
+    }
+}
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(256, (MODE == 0) ? 1 : 4)
+    k_fieldforce_persist(Geom<float> g, SortBufs b, const float *__restrict__ field, float *__restrict__ f, float qC,
+                         SelfCoef sc, int aligned) {
+    using PG = PersistGeom<P, MODE>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_bins[32], s_off[32];
+    __shared__ int s_list[PG::CH];
+
+    constexpr int NG = 32 / P;  // particle groups per warp
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int k = lane % P;
+    const int gbase = lane - k;
+    const int q = lane / P;  // this group's place in its warp
+    const bool lane_on = lane < NG * P;
+    constexpr int NGRP = (PG::NT / 32) * NG;  // particle slots per pass
+    LaneCoef<float, P> lc;
+    lc.load(g, k);
+    if (tid < 32) s_bins[tid] = 0;
+
+    const int stride = gridDim.x;
+    int t = blockIdx.x;
+    pdl_wait();  // the field, the sorted records and the tile offsets are complete
+    if (t >= g.ntiles) return;
+    // tile ranges one and two tiles ahead are loaded an iteration early
+    int cs = __ldg(&b.tile_start[t]), ce = __ldg(&b.tile_start[t + 1]);
+    persist_stage<P, MODE>(g, b, field, t, cs, ce - cs, smem_raw, aligned);
+    cp_async_commit();
+    int ns = 0, ne = 0;
+    if (t + stride < g.ntiles) {
+        ns = __ldg(&b.tile_start[t + stride]);
+        ne = __ldg(&b.tile_start[t + stride + 1]);
+    }
+    for (int it = 0; t < g.ntiles; ++it, t += stride) {
+        unsigned char *cur = smem_raw + (it & 1) * PG::BUF_BYTES;
+        unsigned char *nxt = smem_raw + ((it + 1) & 1) * PG::BUF_BYTES;
+        const int tn = t + stride;
+        if (tn < g.ntiles) persist_stage<P, MODE>(g, b, field, tn, ns, ne - ns, nxt, aligned);
+        cp_async_commit();
+        int n2s = 0, n2e = 0;
+        if (tn + stride < g.ntiles) {
+            n2s = __ldg(&b.tile_start[tn + stride]);
+            n2e = __ldg(&b.tile_start[tn + stride + 1]);
+        }
+        cp_async_wait_prev();  // tile t's copies (the older group) have landed
+        __syncthreads();
+
+        const TileBox tb = tile_box(g, t);
+        const float *brick = reinterpret_cast<const float *>(cur);
+        const float4 *srec = reinterpret_cast<const float4 *>(cur + PG::REC_OFF);
+        const uint32_t *scell = reinterpret_cast<const uint32_t *>(cur + PG::CELL_OFF);
+        const int *sperm = reinterpret_cast<const int *>(cur + PG::PERM_OFF);
+        const int n = ce - cs;
+        for (int sub = 0; sub < n; sub += PG::CH) {
+            const int nch = min(PG::CH, n - sub);
+            if (sub > 0) {  // a tile with more than CH particles: copy the next sub-chunk
+                __syncthreads();
+                for (int i = tid; i < nch; i += PG::NT) {
+                    reinterpret_cast<float4 *>(cur + PG::REC_OFF)[i] = reinterpret_cast<const float4 *>(b.rec)[cs + sub + i];
+                    reinterpret_cast<uint32_t *>(cur + PG::CELL_OFF)[i] = b.cell[cs + sub + i];
+                    reinterpret_cast<int *>(cur + PG::PERM_OFF)[i] = b.perm[cs + sub + i];
+                }
+                __syncthreads();
+            }
+            int Q;
+            if (!PG::VEC) {
+                // bank order of the sub-chunk (the scalar brick's run start, mod 32)
+                int key = 0, rank = 0;
+                if (tid < nch) {
+                    int ax, ay, az;
+                    unpack_anchor(scell[tid], ax, ay, az);
+                    key = (((ax - tb.ox) * PG::E + (ay - tb.oy)) * PG::RZ + (az - tb.oz) + PG::ZOFF) & 31;
+                    rank = atomicAdd(&s_bins[key], 1);
+                }
+                __syncthreads();
+                if (tid < 32) {
+                    const int v = s_bins[tid];
+                    int incl = v;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (tid >= o) incl += u;
+                    }
+                    s_off[tid] = incl - v;
+                    s_bins[tid] = 0;  // clean for the next sub-chunk
+                }
+                __syncthreads();
+                if (tid < nch) s_list[s_off[key] + rank] = tid;
+                __syncthreads();
+                Q = (nch + NG - 1) / NG;  // sorted positions per group place
+            } else {
+                Q = (nch + NG - 1) / NG;
+            }
+            // warp-uniform trip count: all 32 lanes take part in the shuffles
+            for (int base = 0; base < NG * Q; base += NGRP) {
+                const int col = base / NG + warp;
+                const int pos = q * Q + col;
+                const bool live = lane_on && col < Q && pos < nch;
+                const int idx = live ? (PG::VEC ? pos : s_list[pos]) : 0;
+                const float4 r = srec[idx];
+                int ax, ay, az;
+                unpack_anchor(scell[idx], ax, ay, az);
+                ax -= tb.ox; ay -= tb.oy; az -= tb.oz;
+                const bool intile = (unsigned)ax <= (unsigned)(tb.Ex - P) && (unsigned)ay <= (unsigned)(tb.Ey - P) &&
+                                    (unsigned)az <= (unsigned)(tb.Ez - P);
+                if (live && !intile && k == 0) atomicOr(b.err, ERR_INTERNAL);  // skipped, reported
+                const bool use = live && intile;
+                GroupWeights<float, P, MODE> w;
+                w.build(lc, gbase, r.x, r.y, r.z);
+                float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+                if (use) {
+                    const int row0 = (ax * PG::E + ay) * PG::RZ + az + k + PG::ZOFF;
+                    gather_column<float, P, MODE>(w, [&](int a, int c) {
+                        const int e = row0 + (a * PG::E + c) * PG::RZ;
+                        if (MODE == 0) return reinterpret_cast<const float4 *>(brick)[e];
+                        return as_vec<float>(brick[e]);
+                    }, e0, e1, e2);
+                }
+                // the ad self force: lanes 0..2 of a group evaluate one axis each
+                // (P >= 3), lane 0 hands them over; at P = 2 lane 0 does all three
+                float sfk = 0.f, sf1 = 0.f, sf2 = 0.f;
+                if (MODE == 1) {
+                    const float q2 = r.w * r.w;
+                    if (P >= 3) {
+                        if (k < 3) {  // constant indices keep the coefficients out of local memory
+                            const float d = (k == 0) ? r.x : ((k == 1) ? r.y : r.z);
+                            const double c1 = (k == 0) ? sc.c[0] : ((k == 1) ? sc.c[2] : sc.c[4]);
+                            const double c2 = (k == 0) ? sc.c[1] : ((k == 1) ? sc.c[3] : sc.c[5]);
+                            sfk = q2 * self_force_axis<float>((float)c1, (float)c2, d);
+                        }
+                        sf1 = __shfl_down_sync(0xffffffffu, sfk, 1);
+                        sf2 = __shfl_down_sync(0xffffffffu, sfk, 2);
+                    } else if (k == 0) {
+                        sfk = q2 * self_force_axis<float>((float)sc.c[0], (float)sc.c[1], r.x);
+                        sf1 = q2 * self_force_axis<float>((float)sc.c[2], (float)sc.c[3], r.y);
+                        sf2 = q2 * self_force_axis<float>((float)sc.c[4], (float)sc.c[5], r.z);
+                    }
+                }
+                if (MODE == 0) {
+                    e0 *= w.wz; e1 *= w.wz; e2 *= w.wz;
+                } else {
+                    e0 *= w.wz; e1 *= w.wz; e2 *= w.dwz;
+                }
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) {
+                    if (o >= P) continue;
+                    const float v0 = __shfl_down_sync(0xffffffffu, e0, o);
+                    const float v1 = __shfl_down_sync(0xffffffffu, e1, o);
+                    const float v2 = __shfl_down_sync(0xffffffffu, e2, o);
+                    if (k + o < P) {
+                        e0 += v0;
+                        e1 += v1;
+                        e2 += v2;
+                    }
+                }
+                if (use && k == 0) {
+                    const int dst = sperm[idx];
+                    const float s = qC * r.w;
+                    float F0, F1, F2;
+                    if (MODE == 0) {
+                        F0 = s * e0; F1 = s * e1; F2 = s * e2;
+                    } else {
+                        F0 = s * e0 * g.ih[0] + sfk;
+                        F1 = s * e1 * g.ih[1] + sf1;
+                        F2 = s * e2 * g.ih[2] + sf2;
+                    }
+                    f[3 * (int64_t)dst + 0] = F0;
+                    f[3 * (int64_t)dst + 1] = F1;
+                    f[3 * (int64_t)dst + 2] = F2;
+                }
+            }
+        }
+        __syncthreads();  // the buffer and the order list are free for the next copies
+        cs = ns; ce = ne;
+        ns = n2s; ne = n2e;
+    }
+}
+
 template <typename R, int P, int MODE>
 static size_t ff_brick_bytes() {
     const int E = TILE_B + P - 1;
     return (size_t)E * E * E * sizeof(R) * ((MODE == 0) ? 4 : 1);
+}
+
+// Persistent fieldforce: CTAs per SM at its shared-memory size, found once
+// per process (prepare_fieldforce) for each order and mode, and the SM count.
+static int g_persist_ctas[2][MAXP + 1];
+static int g_num_sms = 0;
+
+template <int P, int MODE>
+static cudaError_t prepare_persist() {
+    using PG = PersistGeom<P, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(k_fieldforce_persist<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PG::BYTES);
+    int nb = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fieldforce_persist<P, MODE>, PG::NT, PG::BYTES);
+    if (e == cudaSuccess && g_num_sms == 0) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (e == cudaSuccess) g_persist_ctas[MODE][P] = nb > 0 ? nb : 1;
+    return e;
+}
+
+// The scalar brick's rows are four aligned 16-byte copies when every z tile
+// is 8 points wide (tile origins and Mz multiples of 8).
+inline bool persist_rows_aligned(const Geom<float> &g) { return g.M[2] % 8 == 0 && g.T[2] * 8 == g.M[2]; }
+
+template <int P, int MODE>
+static void launch_persist(const Geom<float> &g, const SortBufs &b, const float *field, float *f, float qC,
+                           const SelfCoef &sc, bool pdl, cudaStream_t s) {
+    using PG = PersistGeom<P, MODE>;
+    const int slots = (g_num_sms > 0 ? g_num_sms : 152) * (g_persist_ctas[MODE][P] > 0 ? g_persist_ctas[MODE][P] : 1);
+    const int grid = g.ntiles < slots ? g.ntiles : slots;
+    const int aligned = persist_rows_aligned(g) ? 1 : 0;
+    if (pdl)
+        launch_pdl(k_fieldforce_persist<P, MODE>, dim3(grid), dim3(PG::NT), PG::BYTES, s, g, b, field, f, qC, sc,
+                   aligned);
+    else
+        k_fieldforce_persist<P, MODE><<<grid, PG::NT, PG::BYTES, s>>>(g, b, field, f, qC, sc, aligned);
 }
 
 template <typename R, int P, int MODE>
@@ -415,6 +761,12 @@ static void launch_ff(const Geom<R> &g, int64_t n, const SortBufs &b, const R *f
     // the energy gradient (MODE 2) gathers a scalar potential, which reads
     // best through L1 on every measured workload; the plan's tuned variant
     // is chosen on force steps and applies to MODE 0 / 1 only
+    if constexpr (std::is_same<R, float>::value && MODE != 2) {
+        if (g.ff_tiled == 2) {
+            launch_persist<P, MODE>(g, b, field, f, qC, sc, pdl, s);
+            return;
+        }
+    }
     if (g.ff_tiled && MODE != 2) {
         if (pdl)
             launch_pdl(k_fieldforce_tiled<R, P, MODE>, dim3(g.ntiles), dim3(FF_THREADS), ff_brick_bytes<R, P, MODE>(),
@@ -472,6 +824,10 @@ template <typename R, int P>
 static cudaError_t prepare_ff_p() {
     cudaError_t e = cudaFuncSetAttribute(k_fieldforce_tiled<R, P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)ff_brick_bytes<R, P, 0>());
+    if constexpr (std::is_same<R, float>::value) {
+        if (e == cudaSuccess) e = prepare_persist<P, 0>();
+        if (e == cudaSuccess) e = prepare_persist<P, 1>();
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fieldforce_tiled<R, P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)ff_brick_bytes<R, P, 1>());

@@ -555,7 +555,8 @@ void drop_graph(pppm_plan *p) {
 }
 
 bool variant_ok(const pppm_plan *p, int v) {
-    if (v & ~63) return false;
+    if (v & ~127) return false;
+    if ((v & 64) && (p->fp64 || (v & 1))) return false;  // the persistent fieldforce: FP32 step types, one variant
     if ((v & 16) && (v & 2)) return false;      // one tile shape at a time
     if ((v & 32) && (v & 4)) return false;      // one make_rho brick layout at a time
     if ((v & 8) && !p->fft_own) return false;  // FP32 plans with power-of-two mesh edges 16..128
@@ -566,7 +567,8 @@ bool variant_ok(const pppm_plan *p, int v) {
 
 // Variant bits: 0 tile-staged fieldforce, 1 long tiles (16 along z), 2
 // four-copy make_rho brick, 3 hand-written Poisson solve, 4 small tiles (4^3),
-// 5 make_rho brick with compile-time strides.
+// 5 make_rho brick with compile-time strides, 6 persistent double-buffered
+// tile-staged fieldforce.
 // The tile shape changes the sort; the histogram is cleared for the new shape.
 void set_variants(pppm_plan *p, int v) {
     p->variants = v;
@@ -577,7 +579,7 @@ void set_variants(pppm_plan *p, int v) {
         p->gf.TE[d] = p->gd.TE[d] = p->TE[d];
     }
     p->gf.ntiles = p->gd.ntiles = p->ntiles;
-    p->gf.ff_tiled = p->gd.ff_tiled = (v & 1) ? 1 : 0;
+    p->gf.ff_tiled = p->gd.ff_tiled = (v & 64) ? 2 : ((v & 1) ? 1 : 0);
     p->gf.rho_copies = p->gd.rho_copies = (v & 4) ? 1 : ((v & 32) ? 2 : 0);
     if (p->sb.tile_count) cudaMemsetAsync(p->sb.tile_count, 0, 4 * (size_t)p->ntiles_alloc, p->stream);
     drop_graph(p);
@@ -1075,7 +1077,7 @@ int pppm_autotune(pppm_plan *p, int64_t n, const void *x, const void *q, void *f
     float best = 1e30f;
     int best_v = p->variants;
     int rc = PPPM_OK;
-    for (int v = 0; v <= 63 && rc == PPPM_OK; ++v) {
+    for (int v = 0; v <= 127 && rc == PPPM_OK; ++v) {
         if (!variant_ok(p, v)) continue;
         set_variants(p, v);
         float vbest = 1e30f;

@@ -53,7 +53,8 @@ struct Geom {
     R h[3];
     R coef[MAXP][MAXP];   // coef[k][l]: weight of stencil point k, power l of delta
     R dcoef[MAXP][MAXP];  // d/ddelta of the same polynomials
-    int ff_tiled;         // fieldforce variant: 0 per-particle through L1, 1 tile-staged brick
+    int ff_tiled;         // fieldforce variant: 0 per-particle through L1, 1 tile-staged brick (one CTA a
+                          // tile), 2 persistent double-buffered tile-staged brick (FP32 step types)
     int rho_copies;       // make_rho brick: 0 one, tile strides; 1 four interleaved copies (FP32C);
                           // 2 one, strides of the largest tile
     int lut_bins;         // coefficient table entries (0: exact polynomials), see pppm_set_lut

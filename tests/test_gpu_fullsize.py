@@ -147,3 +147,11 @@ def test_c3_subsample_fp32c_ad(torch):
     verr = np.linalg.norm(ev[1:7] - ref["virial"]) / np.linalg.norm(ref["virial"])
     print(f"c3 FP32C ad 1% subsample: force {ferr:.2e} energy {eerr:.2e} virial {verr:.2e}")
     assert ferr < 1e-4 and eerr < 1e-4 and verr < 1e-4
+    # the persistent fieldforce (aligned four-chunk brick rows on this 256^3 mesh)
+    for v in (32 | 64, 64):
+        plan.set_variant(v)
+        fv, _ = plan.compute(x, q)
+        plan.sync()
+        fv = fv.double().cpu().numpy()
+        assert rel_rms(fv[sub], ref["f"]) < 1e-4
+        assert rel_rms(fv, f) < 1e-6  # the same arithmetic up to summation order

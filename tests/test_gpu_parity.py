@@ -228,6 +228,14 @@ def test_orders_on_ragged_mesh(torch, P, mode, prec):
     f0, ev0 = plan.compute(torch.tensor(x, dtype=dt, device="cuda"), torch.tensor(q, dtype=dt, device="cuda"))
     plan.sync()
     check_all(f0.double().cpu().numpy(), ev0.cpu().numpy(), ref, prec, f"P={P} {mode} 8^3 tiles")
+    if prec == "fp32c":
+        # the persistent fieldforce on uneven tiles (element-wise brick copies,
+        # every brick edge wrapping), 8^3 and 4^3 tiles
+        for v in (96, 80):
+            plan.set_variant(v)
+            f0, ev0 = plan.compute(torch.tensor(x, dtype=dt, device="cuda"), torch.tensor(q, dtype=dt, device="cuda"))
+            plan.sync()
+            check_all(f0.double().cpu().numpy(), ev0.cpu().numpy(), ref, prec, f"P={P} {mode} variant {v}")
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
@@ -268,6 +276,19 @@ def test_dense_tile(torch, prec, P):
     print(prec, "dense tile rho rel RMS", rerr)
     assert rerr < (1e-12 if prec == "fp64" else 1e-5)
     check_all(f, ev, ref, prec, "dense tile")
+    if prec != "fp64":
+        # the persistent fieldforce: 70,000 charges in one tile is 274 sub-chunks of 256
+        from paper_1702_04250_gb300 import pppm
+
+        for mode in ("ik", "ad"):
+            ref_m = ref if mode == "ik" else OraclePPPM(box, mesh, P, g, "ad", 1.0).compute(xo, qo)
+            pm = pppm.PPPM(box, n, P, mesh, g, mode=mode, precision=prec)
+            pm.set_variant(96)
+            fm, evm = pm.compute(torch.tensor(x, dtype=torch.float32, device="cuda"),
+                                 torch.tensor(q, dtype=torch.float32, device="cuda"))
+            pm.sync()
+            check_all(fm.double().cpu().numpy(), evm.cpu().numpy(), ref_m, prec, f"dense tile persistent {mode}")
+            pm.close()
 
 
 @pytest.mark.parametrize("prec,P,n,spread", [("fp32c", 5, 256, 1.5), ("fp32c", 7, 257, 1.5),
@@ -392,21 +413,24 @@ def test_fieldforce_variants_and_autotune(torch, c2_refs, mode):
     plan = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode, "fp32c", w.qqrd2e)
     # fieldforce per particle / tile-staged x make_rho one / four brick copies
     # x cuFFT / hand-written Poisson solve x 8^3 / 4^3 tiles
-    for v in (0, 1, 4, 5, 8, 9, 12, 13, 16, 17, 20, 25, 29, 32, 41, 57):
+    # ... x the persistent double-buffered fieldforce (bit 6)
+    for v in (0, 1, 4, 5, 8, 9, 12, 13, 16, 17, 20, 25, 29, 32, 41, 57, 64, 68, 72, 80, 96, 104, 120):
         plan.set_variant(v)
         f, ev = plan.compute(x, q)
         plan.sync()
         check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"variant {v} {mode}")
     choice = plan.autotune(x, q)
-    assert choice & ~0x3D == 0 and not (choice & 4 and choice & 32)  # bits 0, 2, 3, 4, 5
+    assert choice & ~0x7D == 0 and not (choice & 4 and choice & 32)  # bits 0, 2, 3, 4, 5, 6
+    assert not (choice & 1 and choice & 64)
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"autotuned {choice}")
-    for bad in (2, 3, 6, 7, 10, 18, 36, 64):  # long tiles are reserved; exclusive pairs; unknown bits
+    for bad in (2, 3, 6, 7, 10, 18, 36, 65, 128):  # long tiles are reserved; exclusive pairs; unknown bits
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(bad)
     p64 = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode, "fp64", w.qqrd2e)
-    for bad in (4, 8):  # the brick copies are the FP32C accumulator; the own FFT is FP32
+    for bad in (4, 8, 64):  # the brick copies are the FP32C accumulator; the own FFT and the persistent
+        # fieldforce are FP32
         with pytest.raises(pppm.PPPMError):
             p64.set_variant(bad)
 
@@ -426,7 +450,7 @@ def test_order7_variants(torch, mode):
     q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
     plan = pppm.PPPM(w.box, w.n, 7, w.mesh, g, mode, "fp32c", w.qqrd2e)
     assert plan.info()["tile"] == 8 and plan.info()["ntiles"] == 512
-    for v in (0, 1, 4, 5, 8, 13, 16, 29, 32, 41):
+    for v in (0, 1, 4, 5, 8, 13, 16, 29, 32, 41, 64, 96, 104, 112):
         plan.set_variant(v)
         f, ev = plan.compute(x, q)
         plan.sync()
@@ -435,7 +459,7 @@ def test_order7_variants(torch, mode):
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(bad)
     choice = plan.autotune(x, q)
-    assert choice & ~0x3D == 0
+    assert choice & ~0x7D == 0
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, "fp32c", f"P=7 autotuned {choice}")
