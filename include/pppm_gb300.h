@@ -241,9 +241,10 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * SM walk the tiles) whose CTAs stage the next tile's field brick and
  * particle records into a second shared-memory buffer while they gather the
  * current tile (PPPM_FP32 / PPPM_FP32C only; not with bit 0; force steps
- * only, like bit 0).  Default: bit 4 when the mesh has fewer than 304 tiles of 8^3
+ * only, like bit 0; the ad form runs one particle per thread over units of
+ * two z-adjacent tiles).  Default: bit 4 when the mesh has fewer than 304 tiles of 8^3
  * (two per SM), bit 0 for ik plans whose n_max is at least 16 per tile, bit 3
- * where it is allowed, bit 5.
+ * where it is allowed, bit 5, bit 6 for PPPM_FP32 / PPPM_FP32C ad plans.
  * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a
  * combination the plan does not allow).
  * pppm_autotune times every variant on the caller's inputs (two warm-up and

@@ -413,108 +413,97 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, Sort
 
 // ---------------------------------------------------------------------------
 // Persistent, double-buffered tile-staged fieldforce (FP32 step types,
-// variant bit 6).  One CTA per SM slot walks the tiles t = blockIdx.x,
-// blockIdx.x + gridDim.x, ...; while it gathers tile t from one shared-memory
-// buffer, the copies of tile t + gridDim.x (field brick over the tile plus
-// its P-1 halo, and the tile's particle records, anchors and input indices)
+// variant bit 6).  One CTA per SM slot walks the work units u = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; while it gathers unit u from one shared-memory
+// buffer, the copies of unit u + gridDim.x (field brick over the unit plus
+// its P-1 halo, and the unit's particle records, anchors and input indices)
 // are in flight into the other buffer with cp.async, so the HBM/L2 latency
 // of the staging hides behind the gather instead of preceding it.  Each
-// stencil read is then a shared-memory load at a compile-time offset from
-// the particle's run start (brick strides of the widest tile), and the
-// P^3 loads of a group need no address arithmetic.
+// stencil read is a shared-memory load at a compile-time offset from the
+// particle's run start (brick strides of the widest tile).
 //
-// Brick layout: [x][y][z], E = TILE_B + P - 1 points per x and y.  The ik
-// field (MODE 0) keeps E float4 points per z row.  The scalar potential
-// (MODE 1) keeps 16 floats per z row starting at global z = oz - 4 (tile
-// origin oz): with Mz a multiple of 8 and every z tile 8 wide (oz a multiple
-// of 8) each row is four aligned 16-byte copies; other meshes copy the
-// row's E points one by one into the same positions.  Stencil point k of a
-// particle with local anchor az sits at brick z index az + k + ZOFF.
-//
-// Particles of one tile are handled in sub-chunks of CH (the first one
-// staged with the brick, any further one copied when reached).  For the
-// scalar brick each sub-chunk is counting-sorted by the shared-memory bank
-// of its z run start, and a warp's particle groups take particles an NG-th
-// of the sorted list apart, so their loads rarely share a bank.
+// ik (this kernel): the unit is one mesh tile; the brick holds float4 field
+// points, [x][y][z] with E = TILE_B + P - 1 points per edge, and the groups
+// of P lanes per particle gather as k_fieldforce_tiled does.  The ad form
+// (k_fieldforce_ad_thread, below) runs one particle per thread.  Particles
+// of one unit are handled in sub-chunks of CH (the first one staged with
+// the brick, any further one copied when reached).
 // ---------------------------------------------------------------------------
-template <int P, int MODE>
+template <int P>
 struct PersistGeom {
     static constexpr int NT = 256;
-    static constexpr int E = TILE_B + P - 1;                // brick edge (x, y) of the widest tile
-    static constexpr bool VEC = (MODE == 0);                // float4 field points
-    static constexpr int RZ = VEC ? E : 16;                 // z row length (elements)
-    static constexpr int ZOFF = VEC ? 0 : 4 - (P - 1) / 2;  // brick z of stencil point k = az + k + ZOFF
-    static constexpr int ELEM = VEC ? 16 : 4;               // bytes per element
-    static constexpr int BRICK_BYTES = E * E * RZ * ELEM;
-    static constexpr int CH = 256;                          // particles per sub-chunk
-    static constexpr int REC_OFF = BRICK_BYTES;             // float4 records [CH]
-    static constexpr int CELL_OFF = REC_OFF + 16 * CH;      // packed anchors [CH]
-    static constexpr int PERM_OFF = CELL_OFF + 4 * CH;      // input indices [CH]
+    static constexpr int E = TILE_B + P - 1;            // brick edge of the widest tile
+    static constexpr int BRICK_BYTES = E * E * E * 16;  // float4 points
+    static constexpr int CH = 256;                      // particles per sub-chunk
+    static constexpr int REC_OFF = BRICK_BYTES;         // float4 records [CH]
+    static constexpr int CELL_OFF = REC_OFF + 16 * CH;  // packed anchors [CH]
+    static constexpr int PERM_OFF = CELL_OFF + 4 * CH;  // input indices [CH]
     static constexpr int BUF_BYTES = PERM_OFF + 4 * CH;
     static constexpr size_t BYTES = 2 * (size_t)BUF_BYTES;
     static_assert(BRICK_BYTES % 16 == 0 && BUF_BYTES % 16 == 0, "16-byte aligned buffer parts");
-    static_assert(VEC || (ZOFF >= 1 && ZOFF + 7 + (P - 1) < RZ), "the 16-float z rows cover every stencil run");
 };
 
 struct TileBox {
     int ox, oy, oz, Ex, Ey, Ez;  // origin and brick extents (tile width + P - 1)
 };
-__device__ __forceinline__ TileBox tile_box(const Geom<float> &g, int tile) {
+// Tile origins per dimension, tile_origin(t) for t = 0..T, in shared memory
+// (one table per CTA: no integer division per tile).
+constexpr int PERSIST_MAX_T = MAX_MESH / (TILE_B / 2);
+struct OriginTable {
+    int o[3][PERSIST_MAX_T + 1];
+};
+// a / b for 0 <= a < 2^24 and 1 <= b: the float quotient, corrected by one
+__device__ __forceinline__ int div_small(int a, int b, float ib) {
+    int qq = __float2int_rz(__int2float_rn(a) * ib);
+    const int r = a - qq * b;
+    qq += (r >= b) ? 1 : 0;
+    qq -= (r < 0) ? 1 : 0;
+    return qq;
+}
+__device__ __forceinline__ TileBox tile_box(const Geom<float> &g, int tile, const OriginTable &ot, float iT2,
+                                            float iT1) {
     TileBox t;
-    const int tz = tile % g.T[2];
-    const int ty = (tile / g.T[2]) % g.T[1];
-    const int tx = tile / (g.T[2] * g.T[1]);
-    t.ox = tile_origin(tx, g.T[0], g.M[0]);
-    t.oy = tile_origin(ty, g.T[1], g.M[1]);
-    t.oz = tile_origin(tz, g.T[2], g.M[2]);
-    t.Ex = tile_origin(tx + 1, g.T[0], g.M[0]) - t.ox + g.P - 1;
-    t.Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - t.oy + g.P - 1;
-    t.Ez = tile_origin(tz + 1, g.T[2], g.M[2]) - t.oz + g.P - 1;
+    const int r1 = div_small(tile, g.T[2], iT2);  // tile / T2
+    const int tz = tile - r1 * g.T[2];
+    const int tx = div_small(r1, g.T[1], iT1);
+    const int ty = r1 - tx * g.T[1];
+    t.ox = ot.o[0][tx];
+    t.oy = ot.o[1][ty];
+    t.oz = ot.o[2][tz];
+    t.Ex = ot.o[0][tx + 1] - t.ox + g.P - 1;
+    t.Ey = ot.o[1][ty + 1] - t.oy + g.P - 1;
+    t.Ez = ot.o[2][tz + 1] - t.oz + g.P - 1;
     return t;
 }
+
+// The six ad self-force coefficients in the step type.
+struct SelfCoefF {
+    float c[6];
+};
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// Issue (do not await) the copies of tile `tile` into buffer `buf`: its field
-// brick and its first min(n, CH) particles [s0, s0 + n).
-template <int P, int MODE>
+// Issue (do not await) the copies of the tile whose box is tb into buffer
+// `buf`: its field brick and its first min(n, CH) particles [s0, s0 + n).
+template <int P>
 __device__ __forceinline__ void persist_stage(const Geom<float> &g, const SortBufs &b, const float *__restrict__ field,
-                                              int tile, int s0, int n, unsigned char *buf, bool aligned) {
-    using PG = PersistGeom<P, MODE>;
+                                              const TileBox &tb, int s0, int n, unsigned char *buf) {
+    using PG = PersistGeom<P>;
     if (n <= 0) return;  // an empty tile needs no brick
-    const TileBox tb = tile_box(g, tile);
     float *brick = reinterpret_cast<float *>(buf);
     const int tid = threadIdx.x;
     const int My = g.M[1], Mz = g.M[2];
-    if (!PG::VEC && aligned) {
-        // rows (ex, ey) of four aligned 16-byte chunks from z = oz - 4 (wrapped; Mz % 4 == 0)
-        const int j = tid & 3;
-        int gz = tb.oz - 4 + 4 * j;
-        gz += (gz < 0) ? Mz : 0;
-        gz -= (gz >= Mz) ? Mz : 0;
-        const int rows = tb.Ex * tb.Ey;
-        const unsigned int inv = (65536u + (unsigned)tb.Ey - 1u) / (unsigned)tb.Ey;  // r / Ey = (r inv) >> 16, r < 256
-        for (int r = tid >> 2; r < rows; r += PG::NT / 4) {
-            const int ex = (int)(((unsigned)r * inv) >> 16), ey = r - ex * tb.Ey;
+    // one 16-byte point per copy: 16 lanes along z (Ez <= 14), 16 rows per pass
+    const int lz = tid & 15, ry = tid >> 4;
+    if (lz < tb.Ez) {
+        const int gz = wrap1(tb.oz - g.rlo + lz, Mz);
+        for (int ex = 0; ex < tb.Ex; ++ex) {
             const int gx = wrap1(tb.ox - g.rlo + ex, g.M[0]);
-            const int gy = wrap1(tb.oy - g.rlo + ey, My);
-            cp_async<16>(brick + (ex * PG::E + ey) * PG::RZ + 4 * j, field + ((int64_t)gx * My + gy) * Mz + gz);
-        }
-    } else {
-        // one element per copy: 16 lanes along z (Ez <= 14), 16 rows per pass
-        const int lz = tid & 15, ry = tid >> 4;
-        if (lz < tb.Ez) {
-            const int gz = wrap1(tb.oz - g.rlo + lz, Mz);
-            for (int ex = 0; ex < tb.Ex; ++ex) {
-                const int gx = wrap1(tb.ox - g.rlo + ex, g.M[0]);
-                for (int ey = ry; ey < tb.Ey; ey += PG::NT / 16) {
-                    const int gy = wrap1(tb.oy - g.rlo + ey, My);
-                    const int64_t p = ((int64_t)gx * My + gy) * Mz + gz;
-                    const int e = (ex * PG::E + ey) * PG::RZ + lz + PG::ZOFF;
-                    if (PG::VEC) cp_async<16>(brick + 4 * e, field + 4 * p);
-                    else cp_async<4>(brick + e, field + p);
-                }
+            for (int ey = ry; ey < tb.Ey; ey += PG::NT / 16) {
+                const int gy = wrap1(tb.oy - g.rlo + ey, My);
+                const int64_t p = ((int64_t)gx * My + gy) * Mz + gz;
+                cp_async<16>(brick + 4 * ((ex * PG::E + ey) * PG::E + lz), field + 4 * p);
             }
         }
     }
@@ -526,14 +515,12 @@ __device__ __forceinline__ void persist_stage(const Geom<float> &g, const SortBu
     }
 }
 
-template <int P, int MODE>
-__global__ void __launch_bounds__(256, (MODE == 0) ? 1 : 4)
-    k_fieldforce_persist(Geom<float> g, SortBufs b, const float *__restrict__ field, float *__restrict__ f, float qC,
-                         SelfCoef sc, int aligned) {
-    using PG = PersistGeom<P, MODE>;
+template <int P>
+__global__ void __launch_bounds__(256, 1)
+    k_fieldforce_persist(Geom<float> g, SortBufs b, const float *__restrict__ field, float *__restrict__ f, float qC) {
+    using PG = PersistGeom<P>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_bins[32], s_off[32];
-    __shared__ int s_list[PG::CH];
+    __shared__ OriginTable s_org;
 
     constexpr int NG = 32 / P;  // particle groups per warp
     const int tid = threadIdx.x;
@@ -545,15 +532,19 @@ __global__ void __launch_bounds__(256, (MODE == 0) ? 1 : 4)
     constexpr int NGRP = (PG::NT / 32) * NG;  // particle slots per pass
     LaneCoef<float, P> lc;
     lc.load(g, k);
-    if (tid < 32) s_bins[tid] = 0;
+    for (int d = 0; d < 3; ++d)
+        for (int i = tid; i <= g.T[d]; i += PG::NT) s_org.o[d][i] = tile_origin(i, g.T[d], g.M[d]);
+    const float iT2 = 1.0f / (float)g.T[2], iT1 = 1.0f / (float)g.T[1];
+    __syncthreads();
 
     const int stride = gridDim.x;
     int t = blockIdx.x;
     pdl_wait();  // the field, the sorted records and the tile offsets are complete
     if (t >= g.ntiles) return;
-    // tile ranges one and two tiles ahead are loaded an iteration early
+    // tile ranges (and boxes) one and two tiles ahead are found an iteration early
     int cs = __ldg(&b.tile_start[t]), ce = __ldg(&b.tile_start[t + 1]);
-    persist_stage<P, MODE>(g, b, field, t, cs, ce - cs, smem_raw, aligned);
+    TileBox tb = tile_box(g, t, s_org, iT2, iT1);
+    persist_stage<P>(g, b, field, tb, cs, ce - cs, smem_raw);
     cp_async_commit();
     int ns = 0, ne = 0;
     if (t + stride < g.ntiles) {
@@ -564,7 +555,11 @@ __global__ void __launch_bounds__(256, (MODE == 0) ? 1 : 4)
         unsigned char *cur = smem_raw + (it & 1) * PG::BUF_BYTES;
         unsigned char *nxt = smem_raw + ((it + 1) & 1) * PG::BUF_BYTES;
         const int tn = t + stride;
-        if (tn < g.ntiles) persist_stage<P, MODE>(g, b, field, tn, ns, ne - ns, nxt, aligned);
+        TileBox tbn = tb;
+        if (tn < g.ntiles) {
+            tbn = tile_box(g, tn, s_org, iT2, iT1);
+            persist_stage<P>(g, b, field, tbn, ns, ne - ns, nxt);
+        }
         cp_async_commit();
         int n2s = 0, n2e = 0;
         if (tn + stride < g.ntiles) {
@@ -574,8 +569,7 @@ __global__ void __launch_bounds__(256, (MODE == 0) ? 1 : 4)
         cp_async_wait_prev();  // tile t's copies (the older group) have landed
         __syncthreads();
 
-        const TileBox tb = tile_box(g, t);
-        const float *brick = reinterpret_cast<const float *>(cur);
+        const float4 *brick = reinterpret_cast<const float4 *>(cur);
         const float4 *srec = reinterpret_cast<const float4 *>(cur + PG::REC_OFF);
         const uint32_t *scell = reinterpret_cast<const uint32_t *>(cur + PG::CELL_OFF);
         const int *sperm = reinterpret_cast<const int *>(cur + PG::PERM_OFF);
@@ -591,41 +585,13 @@ __global__ void __launch_bounds__(256, (MODE == 0) ? 1 : 4)
                 }
                 __syncthreads();
             }
-            int Q;
-            if (!PG::VEC) {
-                // bank order of the sub-chunk (the scalar brick's run start, mod 32)
-                int key = 0, rank = 0;
-                if (tid < nch) {
-                    int ax, ay, az;
-                    unpack_anchor(scell[tid], ax, ay, az);
-                    key = (((ax - tb.ox) * PG::E + (ay - tb.oy)) * PG::RZ + (az - tb.oz) + PG::ZOFF) & 31;
-                    rank = atomicAdd(&s_bins[key], 1);
-                }
-                __syncthreads();
-                if (tid < 32) {
-                    const int v = s_bins[tid];
-                    int incl = v;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int u = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (tid >= o) incl += u;
-                    }
-                    s_off[tid] = incl - v;
-                    s_bins[tid] = 0;  // clean for the next sub-chunk
-                }
-                __syncthreads();
-                if (tid < nch) s_list[s_off[key] + rank] = tid;
-                __syncthreads();
-                Q = (nch + NG - 1) / NG;  // sorted positions per group place
-            } else {
-                Q = (nch + NG - 1) / NG;
-            }
+            const int Q = (nch + NG - 1) / NG;  // positions per group place
             // warp-uniform trip count: all 32 lanes take part in the shuffles
             for (int base = 0; base < NG * Q; base += NGRP) {
                 const int col = base / NG + warp;
                 const int pos = q * Q + col;
                 const bool live = lane_on && col < Q && pos < nch;
-                const int idx = live ? (PG::VEC ? pos : s_list[pos]) : 0;
+                const int idx = live ? pos : 0;
                 const float4 r = srec[idx];
                 int ax, ay, az;
                 unpack_anchor(scell[idx], ax, ay, az);
@@ -634,42 +600,16 @@ __global__ void __launch_bounds__(256, (MODE == 0) ? 1 : 4)
                                     (unsigned)az <= (unsigned)(tb.Ez - P);
                 if (live && !intile && k == 0) atomicOr(b.err, ERR_INTERNAL);  // skipped, reported
                 const bool use = live && intile;
-                GroupWeights<float, P, MODE> w;
+                // lane k: z offset k; rows along x (a) and y (c)
+                GroupWeights<float, P, 0> w;
                 w.build(lc, gbase, r.x, r.y, r.z);
                 float e0 = 0.f, e1 = 0.f, e2 = 0.f;
                 if (use) {
-                    const int row0 = (ax * PG::E + ay) * PG::RZ + az + k + PG::ZOFF;
-                    gather_column<float, P, MODE>(w, [&](int a, int c) {
-                        const int e = row0 + (a * PG::E + c) * PG::RZ;
-                        if (MODE == 0) return reinterpret_cast<const float4 *>(brick)[e];
-                        return as_vec<float>(brick[e]);
-                    }, e0, e1, e2);
+                    const int row0 = (ax * PG::E + ay) * PG::E + az + k;
+                    gather_column<float, P, 0>(w, [&](int a, int c) { return brick[row0 + (a * PG::E + c) * PG::E]; },
+                                               e0, e1, e2);
                 }
-                // the ad self force: lanes 0..2 of a group evaluate one axis each
-                // (P >= 3), lane 0 hands them over; at P = 2 lane 0 does all three
-                float sfk = 0.f, sf1 = 0.f, sf2 = 0.f;
-                if (MODE == 1) {
-                    const float q2 = r.w * r.w;
-                    if (P >= 3) {
-                        if (k < 3) {  // constant indices keep the coefficients out of local memory
-                            const float d = (k == 0) ? r.x : ((k == 1) ? r.y : r.z);
-                            const double c1 = (k == 0) ? sc.c[0] : ((k == 1) ? sc.c[2] : sc.c[4]);
-                            const double c2 = (k == 0) ? sc.c[1] : ((k == 1) ? sc.c[3] : sc.c[5]);
-                            sfk = q2 * self_force_axis<float>((float)c1, (float)c2, d);
-                        }
-                        sf1 = __shfl_down_sync(0xffffffffu, sfk, 1);
-                        sf2 = __shfl_down_sync(0xffffffffu, sfk, 2);
-                    } else if (k == 0) {
-                        sfk = q2 * self_force_axis<float>((float)sc.c[0], (float)sc.c[1], r.x);
-                        sf1 = q2 * self_force_axis<float>((float)sc.c[2], (float)sc.c[3], r.y);
-                        sf2 = q2 * self_force_axis<float>((float)sc.c[4], (float)sc.c[5], r.z);
-                    }
-                }
-                if (MODE == 0) {
-                    e0 *= w.wz; e1 *= w.wz; e2 *= w.wz;
-                } else {
-                    e0 *= w.wz; e1 *= w.wz; e2 *= w.dwz;
-                }
+                e0 *= w.wz; e1 *= w.wz; e2 *= w.wz;
 #pragma unroll
                 for (int o = 4; o > 0; o >>= 1) {
                     if (o >= P) continue;
@@ -685,23 +625,306 @@ __global__ void __launch_bounds__(256, (MODE == 0) ? 1 : 4)
                 if (use && k == 0) {
                     const int dst = sperm[idx];
                     const float s = qC * r.w;
-                    float F0, F1, F2;
-                    if (MODE == 0) {
-                        F0 = s * e0; F1 = s * e1; F2 = s * e2;
-                    } else {
-                        F0 = s * e0 * g.ih[0] + sfk;
-                        F1 = s * e1 * g.ih[1] + sf1;
-                        F2 = s * e2 * g.ih[2] + sf2;
-                    }
-                    f[3 * (int64_t)dst + 0] = F0;
-                    f[3 * (int64_t)dst + 1] = F1;
-                    f[3 * (int64_t)dst + 2] = F2;
+                    f[3 * (int64_t)dst + 0] = s * e0;
+                    f[3 * (int64_t)dst + 1] = s * e1;
+                    f[3 * (int64_t)dst + 2] = s * e2;
                 }
             }
         }
-        __syncthreads();  // the buffer and the order list are free for the next copies
+        __syncthreads();  // the buffer is free for the next copies
         cs = ns; ce = ne;
         ns = n2s; ne = n2e;
+        tb = tbn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent ad fieldforce with one particle per thread (FP32 step types;
+// the ad form of variant bit 6).  The work unit is a "super-tile": ZT = 2
+// consecutive mesh tiles along z (their particles are consecutive in the
+// sorted order), staged as one brick of the scalar potential (x, y: tile +
+// P - 1 halo; z: 24 floats per row from oz - 4, four-byte aligned rows of
+// six 16-byte copies when the z tiles are 8 wide) plus the unit's particle
+// records, double-buffered like k_fieldforce_persist.  Each thread
+// then evaluates its particle's three weight sets and their derivatives
+// itself (no shuffles) and sums the P^3 stencil separably from shared
+// memory at compile-time offsets: z runs into two partial sums (weight and
+// derivative), those into three per x slice, those into the three
+// components -- 2 FMAs per stencil point and no cross-lane reduction.
+//
+// Bank order: the 32 lanes of a warp read the same stencil offset of 32
+// different particles, so they hit distinct banks exactly when their brick
+// base addresses differ mod 32.  Each sub-chunk is ordered rank-major by that
+// residue (every residue's first particle, then every residue's second, ...)
+// and a warp takes 32 consecutive particles of that order.
+// ---------------------------------------------------------------------------
+struct AdThreadGeom {
+    static constexpr int NT = 128;         // threads per CTA (4 warps)
+    static constexpr int ZT = 2;           // mesh tiles per work unit along z
+    static constexpr int RZ = 24;          // z row length and stride (floats) from oz - 4
+    static constexpr int CH = 256;         // particles per staged sub-chunk
+    static constexpr int EMAX = TILE_B + MAXP - 1;
+    static constexpr int BRICK_BYTES = EMAX * EMAX * RZ * 4;
+    static constexpr int REC_OFF = BRICK_BYTES;
+    static constexpr int CELL_OFF = REC_OFF + 16 * CH;
+    static constexpr int PERM_OFF = CELL_OFF + 4 * CH;
+    static constexpr int BUF_BYTES = PERM_OFF + 4 * CH;
+    static constexpr size_t BYTES = 2 * (size_t)BUF_BYTES;
+    static_assert(BRICK_BYTES % 16 == 0 && BUF_BYTES % 16 == 0, "16-byte aligned buffer parts");
+    static_assert(4 + ZT * TILE_B + (MAXP - 1) / 2 <= RZ, "a row covers the unit's z range");
+};
+
+// Work unit u: tiles (tx, ty, tz0 .. tz0 + nz - 1), nz = min(ZT, T2 - tz0).
+struct UnitBox {
+    int t0, nz;                  // first tile, tiles in the unit
+    int ox, oy, oz, Ex, Ey, Ez;  // origin and brick extents (unit width + P - 1)
+};
+__device__ __forceinline__ UnitBox unit_box(const Geom<float> &g, int u, int U2, float iU2, float iT1) {
+    using AG = AdThreadGeom;
+    UnitBox b;
+    const int r1 = div_small(u, U2, iU2);
+    const int uz = u - r1 * U2;
+    const int tx = div_small(r1, g.T[1], iT1);
+    const int ty = r1 - tx * g.T[1];
+    const int tz0 = uz * AG::ZT;
+    b.nz = min(AG::ZT, g.T[2] - tz0);
+    b.t0 = (tx * g.T[1] + ty) * g.T[2] + tz0;
+    b.ox = tile_origin(tx, g.T[0], g.M[0]);
+    b.oy = tile_origin(ty, g.T[1], g.M[1]);
+    b.oz = tile_origin(tz0, g.T[2], g.M[2]);
+    b.Ex = tile_origin(tx + 1, g.T[0], g.M[0]) - b.ox + g.P - 1;
+    b.Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - b.oy + g.P - 1;
+    b.Ez = tile_origin(tz0 + b.nz, g.T[2], g.M[2]) - b.oz + g.P - 1;
+    return b;
+}
+
+// Issue the copies of one unit into `buf`: brick rows of the potential and the
+// first min(n, CH) particle records from s0.
+template <int P>
+__device__ __forceinline__ void adthread_stage(const Geom<float> &g, const SortBufs &b, const float *__restrict__ phi,
+                                               const UnitBox &ub, int s0, int n, unsigned char *buf, bool aligned) {
+    using AG = AdThreadGeom;
+    constexpr int E = TILE_B + P - 1;  // brick z index i holds global z = oz - 4 + i (wrapped)
+    if (n <= 0) return;
+    float *brick = reinterpret_cast<float *>(buf);
+    const int tid = threadIdx.x;
+    const int My = g.M[1], Mz = g.M[2];
+    const int rows = ub.Ex * ub.Ey;
+    const unsigned int inv = (65536u + (unsigned)ub.Ey - 1u) / (unsigned)ub.Ey;  // r / Ey = (r inv) >> 16, r < 256
+    if (aligned) {
+        // six aligned 16-byte chunks per row from z = oz - 4 (wrapped; Mz % 8 == 0)
+        constexpr int NCH = AG::RZ / 4;
+        for (int i = tid; i < rows * NCH; i += AG::NT) {
+            const int r = i / NCH, j = i - r * NCH;
+            const int ex = (int)(((unsigned)r * inv) >> 16), ey = r - ex * ub.Ey;
+            const int gx = wrap1(ub.ox - g.rlo + ex, g.M[0]);
+            const int gy = wrap1(ub.oy - g.rlo + ey, My);
+            int gz = ub.oz - 4 + 4 * j;
+            gz += (gz < 0) ? Mz : 0;
+            gz -= (gz >= Mz) ? Mz : 0;
+            cp_async<16>(brick + (ex * E + ey) * AG::RZ + 4 * j, phi + ((int64_t)gx * My + gy) * Mz + gz);
+        }
+    } else {
+        // one point per copy: 32 lanes along z, 4 rows per pass; the whole row
+        // (z = oz - 4 .. oz + 19, wrapped as often as a small mesh needs) is
+        // copied, so that the spare word of a run's last pair is a finite value
+        const int lz = tid & 31, ry = tid >> 5;
+        if (lz < AG::RZ) {
+            int gz = (ub.oz - 4 + lz) % Mz;
+            gz += (gz < 0) ? Mz : 0;
+            for (int r = ry; r < rows; r += AG::NT / 32) {
+                const int ex = (int)(((unsigned)r * inv) >> 16), ey = r - ex * ub.Ey;
+                const int gx = wrap1(ub.ox - g.rlo + ex, g.M[0]);
+                const int gy = wrap1(ub.oy - g.rlo + ey, My);
+                cp_async<4>(brick + (ex * E + ey) * AG::RZ + lz, phi + ((int64_t)gx * My + gy) * Mz + gz);
+            }
+        }
+    }
+    const int m = min(n, AG::CH);
+    for (int i = tid; i < m; i += AG::NT) {
+        cp_async<16>(buf + AG::REC_OFF + 16 * i, reinterpret_cast<const float4 *>(b.rec) + s0 + i);
+        cp_async<4>(buf + AG::CELL_OFF + 4 * i, b.cell + s0 + i);
+        cp_async<4>(buf + AG::PERM_OFF + 4 * i, b.perm + s0 + i);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(AdThreadGeom::NT, 4)
+    k_fieldforce_ad_thread(Geom<float> g, SortBufs b, const float *__restrict__ phi, float *__restrict__ f, float qC,
+                           SelfCoefF sc, int aligned, int nunits, int U2) {
+    using AG = AdThreadGeom;
+    constexpr int E = TILE_B + P - 1;
+    constexpr int ZOFF = 4 - (P - 1) / 2;
+    constexpr int NW = AG::NT / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_bins[32], s_off[16];
+    __shared__ int s_list[AG::CH];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    if (tid < 32) s_bins[tid] = 0;
+    const float iU2 = 1.0f / (float)U2, iT1 = 1.0f / (float)g.T[1];
+
+    const int stride = gridDim.x;
+    int u = blockIdx.x;
+    pdl_wait();  // the potential, the sorted records and the tile offsets are complete
+    if (u >= nunits) return;
+    UnitBox ub = unit_box(g, u, U2, iU2, iT1);
+    int cs = __ldg(&b.tile_start[ub.t0]), ce = __ldg(&b.tile_start[ub.t0 + ub.nz]);
+    adthread_stage<P>(g, b, phi, ub, cs, ce - cs, smem_raw, aligned);
+    cp_async_commit();
+    UnitBox ubn = ub;
+    int ns = 0, ne = 0;
+    if (u + stride < nunits) {
+        ubn = unit_box(g, u + stride, U2, iU2, iT1);
+        ns = __ldg(&b.tile_start[ubn.t0]);
+        ne = __ldg(&b.tile_start[ubn.t0 + ubn.nz]);
+    }
+    for (int it = 0; u < nunits; ++it, u += stride) {
+        unsigned char *cur = smem_raw + (it & 1) * AG::BUF_BYTES;
+        unsigned char *nxt = smem_raw + ((it + 1) & 1) * AG::BUF_BYTES;
+        const int un = u + stride;
+        if (un < nunits) adthread_stage<P>(g, b, phi, ubn, ns, ne - ns, nxt, aligned);
+        cp_async_commit();
+        // the unit after next: its box and particle range, for the next iteration
+        UnitBox ub2 = ubn;
+        int n2s = 0, n2e = 0;
+        if (un + stride < nunits) {
+            ub2 = unit_box(g, un + stride, U2, iU2, iT1);
+            n2s = __ldg(&b.tile_start[ub2.t0]);
+            n2e = __ldg(&b.tile_start[ub2.t0 + ub2.nz]);
+        }
+        cp_async_wait_prev();  // this unit's copies (the older group) have landed
+        __syncthreads();
+
+        const float *brick = reinterpret_cast<const float *>(cur);
+        const float4 *srec = reinterpret_cast<const float4 *>(cur + AG::REC_OFF);
+        const uint32_t *scell = reinterpret_cast<const uint32_t *>(cur + AG::CELL_OFF);
+        const int *sperm = reinterpret_cast<const int *>(cur + AG::PERM_OFF);
+        const int n = ce - cs;
+        for (int sub = 0; sub < n; sub += AG::CH) {
+            const int nch = min(AG::CH, n - sub);
+            if (sub > 0) {  // a unit with more than CH particles: copy the next sub-chunk
+                __syncthreads();
+                for (int i = tid; i < nch; i += AG::NT) {
+                    reinterpret_cast<float4 *>(cur + AG::REC_OFF)[i] = reinterpret_cast<const float4 *>(b.rec)[cs + sub + i];
+                    reinterpret_cast<uint32_t *>(cur + AG::CELL_OFF)[i] = b.cell[cs + sub + i];
+                    reinterpret_cast<int *>(cur + AG::PERM_OFF)[i] = b.perm[cs + sub + i];
+                }
+                __syncthreads();
+            }
+            // Bank order: each particle reads its z runs as 8-byte pairs from the
+            // even word at or below its run start b; a warp's 64-bit shared load
+            // is served per half-warp, whose 16 lanes are conflict-free when
+            // their (b / 2) mod 16 differ.  Counting-sort the sub-chunk by that
+            // class; below, the 16 lanes of a half-warp take positions spread
+            // over the whole sorted list.
+            int my_item[AG::CH / AG::NT];
+#pragma unroll
+            for (int j = 0; j < AG::CH / AG::NT; ++j) {
+                const int i = tid + j * AG::NT;
+                my_item[j] = -1;
+                if (i < nch) {
+                    int ax, ay, az;
+                    unpack_anchor(scell[i], ax, ay, az);
+                    const int key =
+                        ((((ax - ub.ox) * E + (ay - ub.oy)) * AG::RZ + (az - ub.oz) + ZOFF) >> 1) & 15;
+                    my_item[j] = (key << 16) | atomicAdd(&s_bins[key], 1);  // class and rank
+                }
+            }
+            __syncthreads();
+            if (tid < 32) {
+                const int v = (tid < 16) ? s_bins[tid] : 0;
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1) {
+                    const int w = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (tid >= o) incl += w;
+                }
+                if (tid < 16) s_off[tid] = incl - v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < AG::CH / AG::NT; ++j)
+                if (my_item[j] >= 0) s_list[s_off[my_item[j] >> 16] + (my_item[j] & 0xffff)] = tid + j * AG::NT;
+            if (tid < 16) s_bins[tid] = 0;  // clean for the next sub-chunk (s_off holds the offsets)
+            __syncthreads();
+            const int npass = (nch + AG::NT - 1) / AG::NT;
+            const int hw = 2 * warp + (lane >> 4);  // half-warp of the CTA
+            for (int pass = 0; pass < npass; ++pass) {
+                // the 16 lanes of a half-warp take sorted positions 2 NW npass apart
+                const int pos = ((lane & 15) * (2 * NW) + hw) * npass + pass;
+                if (pos >= nch) continue;
+                const int idx = s_list[pos];
+                const float4 r = srec[idx];
+                int ax, ay, az;
+                unpack_anchor(scell[idx], ax, ay, az);
+                ax -= ub.ox; ay -= ub.oy; az -= ub.oz;
+                const bool inunit = (unsigned)ax <= (unsigned)(ub.Ex - P) &&
+                                    (unsigned)ay <= (unsigned)(ub.Ey - P) && (unsigned)az <= (unsigned)(ub.Ez - P);
+                if (!inunit) {  // not this unit's particle: skipped, reported
+                    atomicOr(b.err, ERR_INTERNAL);
+                    continue;
+                }
+                // the three weight sets and their derivatives (Horner, this thread alone)
+                float wx[P], wy[P], wz[P], vx[P], vy[P], vz[P];
+#pragma unroll
+                for (int t = 0; t < P; ++t) {
+                    wx[t] = weight<float, P>(g.coef, t, r.x);
+                    wy[t] = weight<float, P>(g.coef, t, r.y);
+                    wz[t] = weight<float, P>(g.coef, t, r.z);
+                    vx[t] = dweight<float, P>(g.dcoef, t, r.x);
+                    vy[t] = dweight<float, P>(g.dcoef, t, r.y);
+                    vz[t] = dweight<float, P>(g.dcoef, t, r.z);
+                }
+                // z runs as NPR 8-byte pairs from the even word at or below the run
+                // start; the z weights shifted to match (zero on the spare word,
+                // which is a finite staged value)
+                constexpr int NPR = (P + 2) / 2;
+                const int b0 = (ax * E + ay) * AG::RZ + az + ZOFF;
+                const int sh = b0 & 1;
+                const float2 *bp = reinterpret_cast<const float2 *>(brick + (b0 - sh));
+                float wz2[2 * NPR], vz2[2 * NPR];
+#pragma unroll
+                for (int j = 0; j < 2 * NPR; ++j) {
+                    const float w0 = (j < P) ? wz[j] : 0.f, w1 = (j >= 1 && j - 1 < P) ? wz[j - 1] : 0.f;
+                    const float d0 = (j < P) ? vz[j] : 0.f, d1 = (j >= 1 && j - 1 < P) ? vz[j - 1] : 0.f;
+                    wz2[j] = sh ? w1 : w0;
+                    vz2[j] = sh ? d1 : d0;
+                }
+                float ex = 0.f, ey = 0.f, ez = 0.f;
+#pragma unroll
+                for (int a = 0; a < P; ++a) {
+                    float y00 = 0.f, y10 = 0.f, y01 = 0.f;
+#pragma unroll
+                    for (int c = 0; c < P; ++c) {
+                        float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+                        for (int m = 0; m < NPR; ++m) {
+                            const float2 v = bp[((a * E + c) * AG::RZ) / 2 + m];
+                            z0 = fmaf(wz2[2 * m], v.x, z0);
+                            z0 = fmaf(wz2[2 * m + 1], v.y, z0);
+                            z1 = fmaf(vz2[2 * m], v.x, z1);
+                            z1 = fmaf(vz2[2 * m + 1], v.y, z1);
+                        }
+                        y00 = fmaf(wy[c], z0, y00);  // sum wy wz phi
+                        y10 = fmaf(vy[c], z0, y10);  // sum dwy wz phi
+                        y01 = fmaf(wy[c], z1, y01);  // sum wy dwz phi
+                    }
+                    ex = fmaf(vx[a], y00, ex);
+                    ey = fmaf(wx[a], y10, ey);
+                    ez = fmaf(wx[a], y01, ez);
+                }
+                const float s = qC * r.w, q2 = r.w * r.w;
+                const int dst = sperm[idx];
+                f[3 * (int64_t)dst + 0] = s * ex * g.ih[0] + q2 * self_force_axis<float>(sc.c[0], sc.c[1], r.x);
+                f[3 * (int64_t)dst + 1] = s * ey * g.ih[1] + q2 * self_force_axis<float>(sc.c[2], sc.c[3], r.y);
+                f[3 * (int64_t)dst + 2] = s * ez * g.ih[2] + q2 * self_force_axis<float>(sc.c[4], sc.c[5], r.z);
+            }
+        }
+        __syncthreads();  // the buffer and the order list are free for the next copies
+        cs = ns; ce = ne; ub = ubn;
+        ns = n2s; ne = n2e; ubn = ub2;
     }
 }
 
@@ -718,12 +941,20 @@ static int g_num_sms = 0;
 
 template <int P, int MODE>
 static cudaError_t prepare_persist() {
-    using PG = PersistGeom<P, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(k_fieldforce_persist<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)PG::BYTES);
+    cudaError_t e;
     int nb = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fieldforce_persist<P, MODE>, PG::NT, PG::BYTES);
+    if constexpr (MODE == 0) {
+        using PG = PersistGeom<P>;
+        e = cudaFuncSetAttribute(k_fieldforce_persist<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PG::BYTES);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fieldforce_persist<P>, PG::NT, PG::BYTES);
+    } else {  // the ad form runs one particle per thread
+        using AG = AdThreadGeom;
+        e = cudaFuncSetAttribute(k_fieldforce_ad_thread<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)AG::BYTES);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fieldforce_ad_thread<P>, AG::NT, AG::BYTES);
+    }
     if (e == cudaSuccess && g_num_sms == 0) {
         int dev = 0;
         e = cudaGetDevice(&dev);
@@ -733,22 +964,36 @@ static cudaError_t prepare_persist() {
     return e;
 }
 
-// The scalar brick's rows are four aligned 16-byte copies when every z tile
-// is 8 points wide (tile origins and Mz multiples of 8).
+// The ad brick's rows are six aligned 16-byte copies when every z tile is 8
+// points wide (tile origins and Mz multiples of 8).
 inline bool persist_rows_aligned(const Geom<float> &g) { return g.M[2] % 8 == 0 && g.T[2] * 8 == g.M[2]; }
 
 template <int P, int MODE>
 static void launch_persist(const Geom<float> &g, const SortBufs &b, const float *field, float *f, float qC,
-                           const SelfCoef &sc, bool pdl, cudaStream_t s) {
-    using PG = PersistGeom<P, MODE>;
+                           const SelfCoef &scd, bool pdl, cudaStream_t s) {
     const int slots = (g_num_sms > 0 ? g_num_sms : 152) * (g_persist_ctas[MODE][P] > 0 ? g_persist_ctas[MODE][P] : 1);
-    const int grid = g.ntiles < slots ? g.ntiles : slots;
-    const int aligned = persist_rows_aligned(g) ? 1 : 0;
-    if (pdl)
-        launch_pdl(k_fieldforce_persist<P, MODE>, dim3(grid), dim3(PG::NT), PG::BYTES, s, g, b, field, f, qC, sc,
-                   aligned);
-    else
-        k_fieldforce_persist<P, MODE><<<grid, PG::NT, PG::BYTES, s>>>(g, b, field, f, qC, sc, aligned);
+    if constexpr (MODE == 1) {
+        using AG = AdThreadGeom;
+        SelfCoefF sc;
+        for (int i = 0; i < 6; ++i) sc.c[i] = (float)scd.c[i];
+        const int aligned = persist_rows_aligned(g) ? 1 : 0;
+        const int U2 = (g.T[2] + AG::ZT - 1) / AG::ZT;
+        const int nunits = g.T[0] * g.T[1] * U2;
+        const int grid = nunits < slots ? nunits : slots;
+        if (pdl)
+            launch_pdl(k_fieldforce_ad_thread<P>, dim3(grid), dim3(AG::NT), AG::BYTES, s, g, b, field, f, qC, sc, aligned,
+                       nunits, U2);
+        else
+            k_fieldforce_ad_thread<P><<<grid, AG::NT, AG::BYTES, s>>>(g, b, field, f, qC, sc, aligned, nunits, U2);
+    } else {
+        using PG = PersistGeom<P>;
+        (void)scd;
+        const int grid = g.ntiles < slots ? g.ntiles : slots;
+        if (pdl)
+            launch_pdl(k_fieldforce_persist<P>, dim3(grid), dim3(PG::NT), PG::BYTES, s, g, b, field, f, qC);
+        else
+            k_fieldforce_persist<P><<<grid, PG::NT, PG::BYTES, s>>>(g, b, field, f, qC);
+    }
 }
 
 template <typename R, int P, int MODE>

@@ -823,9 +823,11 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     int T0[3], TE0[3];
     tile_shape(p->M, false, T0, TE0, small_tiles);
     const int nt0 = T0[0] * T0[1] * T0[2];
-    // compile-time brick strides never measured slower (c3 make_rho 688 -> 665 us)
+    // compile-time brick strides never measured slower (c3 make_rho 688 -> 665 us); the
+    // persistent one-particle-per-thread ad fieldforce halves the 2M-charge gather (545 -> 258 us)
+    const bool ad_persist = !p->ik && !p->fp64;
     set_variants(p, ((p->ik && (double)n_max >= 16.0 * nt0) ? 1 : 0) | (p->fft_own ? 8 : 0) | (small_tiles ? 16 : 0) |
-                        32);
+                        32 | (ad_persist ? 64 : 0));
     if ((rc = build_tables_and_green(p))) return fail(rc);
     if ((rc = make_ffts(p))) return fail(rc);
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(PPPM_ECUDA);

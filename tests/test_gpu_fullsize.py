@@ -3,8 +3,9 @@
 c5: 99,999 water-like charges, 100 A cube, mesh 96^3, order 5, ik -- the
 differentiable energy: autograd gradients vs central finite differences
 (FP64, h = 1e-4 A, 64 seeded atoms), vs the oracle's exact gradients, vs the
-oracle's ik forces (1e-4: ik forces and -dE/dx differ at the discretisation
-level), and FP32 vs FP64.
+oracle's ik forces (they differ at the discretisation level: the bound is
+the sum of the two forces' measured errors against the exact Ewald sum on
+this workload, tests/golden/ik_gradient_errors.txt), and FP32 vs FP64.
 
 c3: 2,048,001 water-like charges, 272 A cube, mesh 256^3, order 7, ad, FP32C
 -- forces on a 1% subsample (every 100th atom), energy and virial vs the FP64
@@ -68,12 +69,18 @@ def test_c5_autograd_matches_oracle_and_forces(torch, c5):
     assert rel_rms(gx, rdx) < 1e-9
     assert rel_rms(gq, rdq) < 1e-9
     # against the oracle's ik forces: the same force discretised two ways
-    # (ik differentiation vs the exact gradient of the ik-G energy); each is
-    # within ~1e-4 of the Ewald force at this mesh, and they differ by
-    # 1.1e-4 here, so the bound is 2e-4
+    # (ik differentiation vs the exact gradient of the ik-G energy).  Each was
+    # measured against the direct Ewald sum on this workload (golden table):
+    # e_ik = 7.8e-5, e_grad = 1.26e-4, so by the triangle inequality their
+    # difference is at most e_ik + e_grad; the oracle's own difference is d,
+    # which the GPU's exact gradients must reproduce
+    from test_oracle_ik_gradient import table
+
+    r = table()[("c5", 96)]
     e = rel_rms(-gx, ref["f"])
-    print("c5 |dE/dx + F_ik| / |F_ik| =", e)
-    assert e < 2e-4
+    print("c5 |dE/dx + F_ik| / |F_ik| =", e, "bound", (r["e_ik"] + r["e_grad"]) * r["ratio"])
+    assert e <= (r["e_ik"] + r["e_grad"]) * r["ratio"]
+    assert abs(e - r["d"]) <= 1e-3 * r["d"]
 
 
 def test_c5_autograd_finite_differences(torch, c5):
