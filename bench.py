@@ -191,10 +191,11 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def known_traffic(stage, workload_name, source):
+def known_traffic(stage, workload_name, source, tag=None):
     """DRAM bytes per launch from profiles/dram_traffic.txt for this stage as
-    implemented in `source`, or None when no capture of it exists or the
-    kernel's sources changed since (the line stores their hash)."""
+    implemented in `source` (and, with tag, in that kernel variant), or None
+    when no capture of it exists or the kernel's sources changed since (the
+    line stores their hash)."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
@@ -210,7 +211,7 @@ def known_traffic(stage, workload_name, source):
             continue
         st, wl, src, sha, nbytes = parts[:5]
         variant = parts[5] if len(parts) > 5 else None
-        if st == stage and wl == workload_name and src == source:
+        if st == stage and wl == workload_name and src == source and (tag is None or variant == tag):
             m = hashlib.sha1()
             for f in (src, "paper_1702_04250_gb300/csrc/pppm_common.cuh"):
                 m.update(open(os.path.join(ROOT, f), "rb").read())
@@ -348,10 +349,21 @@ def result_errors(f, ev, f_ref, ev_ref):
             "virial_rel": float(np.linalg.norm(ev[1:7] - ev_ref[1:7]) / np.linalg.norm(ev_ref[1:7]))}
 
 
-def kernel_roofline(stage, w, ms, ik, peak, peak_kind, traffic_src, variant_ok):
+def variant_tag(stage, variant, ik):
+    """The kernel a plan variant mask runs for a stage, as dram_traffic.txt tags it."""
+    if stage == "make_rho":
+        return "copies4" if variant & 4 else ("cs" if variant & 32 else "tile")
+    if stage == "fieldforce":
+        if variant & 64:
+            return "ik-persist" if ik else "ad-thread"
+        return "tiled" if variant & 1 else "l1"
+    return "-"
+
+
+def kernel_roofline(stage, w, ms, ik, peak, peak_kind, traffic_src, variant):
     nbytes = alg_bytes(stage, w.n, w.mesh, ik)
     achieved = nbytes / (ms * 1e-3) / 1e9
-    tr = known_traffic(stage, w.name, traffic_src) if variant_ok else None
+    tr = known_traffic(stage, w.name, traffic_src, variant_tag(stage, variant, ik))
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": tr["bytes"] if tr else None,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
@@ -378,7 +390,10 @@ def gpu_arm(args, rank, world):
     plan = make_plan(w, g, HEADLINE_MODE, "fp32c")
     f = torch.empty((w.n, 3), dtype=torch.float32, device="cuda")
     ev = torch.zeros(8, dtype=torch.float64, device="cuda")
-    variant = plan.autotune(x32, q32)  # what a user of the plan does once
+    # the plan's default kernel variants (the autotuner picks the same mask on this
+    # workload when it times without a profiler; under ncu its timings are
+    # serialised and it can pick otherwise, so the headline does not depend on it)
+    variant = plan.variant()
     plan.compute(x32, q32, f, ev)
     plan.sync()
     f_fp32c = f.double().cpu().numpy()
@@ -424,12 +439,10 @@ def gpu_arm(args, rank, world):
 
     peak, peak_kind = measured_peak()
     src = "paper_1702_04250_gb300/csrc/"
-    # the committed c3 captures: the per-particle L1 fieldforce (variant bit 0 clear), the one-brick make_rho
     kernels = {
-        "make_rho": kernel_roofline("make_rho", w, stages["make_rho"], ik, peak, peak_kind, src + "k_rho.cu",
-                                    not variant & 4),
+        "make_rho": kernel_roofline("make_rho", w, stages["make_rho"], ik, peak, peak_kind, src + "k_rho.cu", variant),
         "fieldforce": kernel_roofline("fieldforce", w, stages["fieldforce"], ik, peak, peak_kind,
-                                      src + "k_force.cu", not variant & 1),
+                                      src + "k_force.cu", variant),
     }
     top = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
     roof = dict(kernels[top])
@@ -512,10 +525,9 @@ def c2_leg(torch, flush, steps=400):
     t_plain, _ = time_steps(torch, plan, x32, q32, f, ev, steps, 3, flush, sync_ranks=False)
     peak, kind = measured_peak()
     src = "paper_1702_04250_gb300/csrc/"
-    roof = {"make_rho": kernel_roofline("make_rho", w, stages["make_rho"], True, peak, kind, src + "k_rho.cu",
-                                        not variant & 4),
+    roof = {"make_rho": kernel_roofline("make_rho", w, stages["make_rho"], True, peak, kind, src + "k_rho.cu", variant),
             "fieldforce": kernel_roofline("fieldforce", w, stages["fieldforce"], True, peak, kind,
-                                          src + "k_force.cu", bool(variant & 1))}
+                                          src + "k_force.cu", variant)}
     xh = torch.tensor(w.x, dtype=torch.float32).pin_memory()
     qh = torch.tensor(w.q, dtype=torch.float32).pin_memory()
     fh = torch.empty((w.n, 3), dtype=torch.float32).pin_memory()

@@ -253,6 +253,9 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * fastest, writes its bitmask to choice_out (nullable), and leaves f holding
  * a valid result.  Both drop any captured graph. */
 int pppm_set_variant(pppm_plan *p, int variants);
+/* The plan's current variant bitmask (the default, the last pppm_set_variant
+ * or the autotuner's choice) into *variants; PPPM_EINVAL for NULL. */
+int pppm_get_variant(const pppm_plan *p, int *variants);
 
 /* Lookup-table stencil coefficients (Sec. 3.1 "precompute", Table 1's LUT-500
  * and LUT-5000): the coefficients are tabulated at `entries` equally spaced

@@ -1110,6 +1110,12 @@ int pppm_autotune(pppm_plan *p, int64_t n, const void *x, const void *q, void *f
     return rc;
 }
 
+int pppm_get_variant(const pppm_plan *p, int *variants) {
+    if (!p || !variants) return PPPM_EINVAL;
+    *variants = p->variants;
+    return PPPM_OK;
+}
+
 int pppm_plan_info(const pppm_plan *p, int64_t info[10]) {
     if (!p || !info) return PPPM_EINVAL;
     info[0] = p->M[0];

@@ -65,12 +65,14 @@ def lib() -> ctypes.CDLL:
         L.pppm_set_profiling.argtypes = [vp, i32]
         L.pppm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         L.pppm_set_variant.argtypes = [vp, i32]
+        L.pppm_get_variant.argtypes = [vp, ctypes.POINTER(i32)]
         L.pppm_set_lut.argtypes = [vp, i32]
         L.pppm_autotune.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(i32)]
         for name in ("pppm_estimate_g", "pppm_fft_size", "pppm_kspace_error", "pppm_choose_mesh", "pppm_setup", "pppm_destroy", "pppm_set_stream", "pppm_set_graph",
                      "pppm_compute", "pppm_compute_host", "pppm_sync", "pppm_energy_grad", "pppm_potential",
                      "pppm_get_array",
-                     "pppm_plan_info", "pppm_set_profiling", "pppm_stage_times", "pppm_set_variant", "pppm_set_lut",
+                     "pppm_plan_info", "pppm_set_profiling", "pppm_stage_times", "pppm_set_variant", "pppm_get_variant",
+                     "pppm_set_lut",
                      "pppm_autotune"):
             getattr(L, name).restype = i32
         _lib = L
@@ -223,6 +225,12 @@ class PPPM:
 
     def set_variant(self, variants: int):
         _check(lib().pppm_set_variant(self._h, int(variants)), "pppm_set_variant")
+
+    def variant(self) -> int:
+        """The plan's current kernel-variant bitmask."""
+        v = ctypes.c_int()
+        _check(lib().pppm_get_variant(self._h, ctypes.byref(v)), "pppm_get_variant")
+        return v.value
 
     def set_lut(self, entries: int):
         """Tabulated stencil coefficients with `entries` samples (0: exact)."""

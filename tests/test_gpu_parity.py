@@ -419,7 +419,10 @@ def test_fieldforce_variants_and_autotune(torch, c2_refs, mode):
         f, ev = plan.compute(x, q)
         plan.sync()
         check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"variant {v} {mode}")
+    plan.set_variant(41)
+    assert plan.variant() == 41
     choice = plan.autotune(x, q)
+    assert plan.variant() == choice
     assert choice & ~0x7D == 0 and not (choice & 4 and choice & 32)  # bits 0, 2, 3, 4, 5, 6
     assert not (choice & 1 and choice & 64)
     f, ev = plan.compute(x, q)
