@@ -663,7 +663,7 @@ def mesh_leg(torch, flush, steps=40):
     w = workload("c2")
     q2 = float(np.sum(w.q ** 2))
     choice = {}
-    for mode in ("ik",):
+    for mode in ("ik", "ad"):
         for name, kind in (("primes_le_7", pppm.FFT_SMOOTH), ("powers_of_two", pppm.FFT_POW2)):
             t0 = time.perf_counter()
             mesh, g, err = pppm.choose_mesh(w.box, w.n, q2, w.order, w.r_cut, w.rel_acc, kind, mode=mode)

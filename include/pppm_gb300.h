@@ -81,20 +81,25 @@ int pppm_estimate_g(double rel_acc, double r_cut, int64_t n, double q2,
  * PPPM_EINVAL for n < 1, an unknown kind or out == NULL. */
 int pppm_fft_size(int n, int kind, int *out);
 
-/* RMS k-space force error of an ik mesh (Sec. 2.3 / Sec. 4: the accuracy a
+/* RMS k-space force error of a mesh (Sec. 2.3 / Sec. 4: the accuracy a
  * mesh, order and g deliver; the paper leaves the estimate to LAMMPS).
- * Reading: the Hockney-Eastwood functional of the optimal influence function,
- *   Q = (1/V) sum_{k != 0} { sum_m |R(k_m)|^2 - [sum_m U^2(k_m) (k.k_m)
- *       phi(k_m)]^2 / (k^2 [sum_m U^2(k_m)]^2) },
- *   phi = 4 pi exp(-k^2/4g^2)/k^2, |R|^2 = k^2 phi^2, U = prod sinc^P(k h/2),
- * aliases |m_d| <= 2 (the denominator sum exact), over this mesh's
- * wavevectors; *err_out = q2 sqrt(Q / (n V)), the RMS force error of n
- * randomly placed charges with sum q^2 = q2, in units of C e^2 / A^2 (the
- * units of pppm_estimate_g's rel_acc).  Computed in FP64 by one kernel on
- * the current device (temporary device memory, synchronous).
- * PPPM_EINVAL for diff_mode != PPPM_IK (no ad estimate is provided), order
- * outside 2..7, a mesh edge < order or > 1024, or an argument <= 0;
- * PPPM_ENOMEM / PPPM_ECUDA from the device. */
+ * Reading: the Hockney-Eastwood functional of the scheme's force error over
+ * this mesh's wavevectors k != 0, phi = 4 pi exp(-k^2/4g^2)/k^2,
+ * |R(k)|^2 = k^2 phi^2, U = prod sinc^P(k h/2), k_m = k + 2 pi m/h:
+ *   PPPM_IK  Q_k = sum_m |R(k_m)|^2 - [sum_m U^2(k_m) (k.k_m) phi(k_m)]^2
+ *                  / (k^2 [sum_m U^2(k_m)]^2)   (optimal ik influence function)
+ *   PPPM_AD  Q_k = G^2 [sum_m U^2(k_m)] [sum_m U^2(k_m) k_m^2]
+ *                  - 2 G sum_m U^2(k_m) k_m^2 phi(k_m) + sum_m |R(k_m)|^2
+ *            (each alias carries its own derivative; G = the plan's ad
+ *            influence function, sum_m U^2 phi / [sum_m U^2]^2)
+ * aliases |m_d| <= 2, the plain U^2 and U^2 k_m^2 sums exact/|m_d| <= 2000;
+ * Q = (1/V) sum_k Q_k; *err_out = q2 sqrt(Q / (n V)), the RMS force error
+ * of n randomly placed charges with sum q^2 = q2, in units of C e^2 / A^2
+ * (the units of pppm_estimate_g's rel_acc).  Computed in FP64 by one kernel
+ * on the current device (temporary device memory, synchronous).
+ * PPPM_EINVAL for an unknown diff_mode, order outside 2..7, a mesh edge
+ * < order or > 1024, or an argument <= 0; PPPM_ENOMEM / PPPM_ECUDA from the
+ * device. */
 int pppm_kspace_error(const double box[3], const int mesh[3], int order, double g_ewald, int diff_mode,
                       int64_t n, double q2, double *err_out);
 

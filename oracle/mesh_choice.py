@@ -20,6 +20,16 @@ formula):
   k_m = k + 2 pi m / h, the alias sums over |m_d| <= 2 except the full
   denominator sum.  For N charges placed at random,
       dF_rms = (sum q^2) sqrt(Q / (N V))   (force in units of C e^2 / A^2).
+* k-space error of an ad mesh (reading R20): the same functional for forces
+  taken as the gradient of the interpolated potential.  Averaging the squared
+  difference between the mesh force and R over source and target positions,
+  a target alias k_m now carries its own derivative i k_m (ik carries i k for
+  every alias), so per k
+      Q_k(G) = G^2 [sum_m U^2(k_m)] [sum_m U^2(k_m) k_m^2]
+               - 2 G sum_m U^2(k_m) k_m^2 phi(k_m) + sum_m |R(k_m)|^2,
+  evaluated at the plan's own ad influence function G (R6, influence_ad);
+  the two plain alias sums run to |m_d| <= 2000 (the second one separates
+  over dimensions), the others to |m_d| <= 2.  Same dF_rms.
 * Choice: g from the real-space estimate (``estimate_g_ewald``); then, with
   c = P, P + 1, ... points along the longest edge, mesh_d =
   fft_size(ceil(L_d c / L_max)) until dF_rms <= rel_acc (the same reading
@@ -31,9 +41,11 @@ import math
 
 import numpy as np
 
-from .pppm_oracle import _half_k, alias_sum_u2, estimate_g_ewald, half_spectrum_weights
+from .pppm_oracle import _half_k, alias_sum_u2, estimate_g_ewald, half_spectrum_weights, influence_ad
 
-__all__ = ["fft_size", "kspace_error_ik", "choose_mesh"]
+__all__ = ["fft_size", "kspace_error_ik", "kspace_error_ad", "kspace_error", "choose_mesh"]
+
+ALIAS_FULL = 2000
 
 TWO_PI = 2.0 * math.pi
 
@@ -99,8 +111,69 @@ def kspace_error_ik(box, mesh, P: int, g: float, n: int, q2: float, mmax: int = 
     return float(q2) * math.sqrt(Q / (n * V))
 
 
+def _alias_sums_1d(k, h: float, P: int, mmax: int = ALIAS_FULL):
+    """sum_m U1^2(k_m) and sum_m U1^2(k_m) k_m^2 over |m| <= mmax (one dimension)."""
+    k = np.asarray(k, dtype=np.float64)
+    m = np.arange(-mmax, mmax + 1)
+    u = np.sinc(k[:, None] * h / TWO_PI + m[None, :]) ** (2 * P)
+    km = k[:, None] + TWO_PI * m[None, :] / h
+    return np.sum(u, axis=1), np.sum(u * km * km, axis=1)
+
+
+def kspace_error_ad(box, mesh, P: int, g: float, n: int, q2: float, mmax: int = 2) -> float:
+    """RMS k-space force error of an ad mesh for n random charges (see module doc)."""
+    box = np.asarray(box, dtype=np.float64)
+    mesh = np.asarray(mesh, dtype=np.int64)
+    h = box / mesh
+    V = float(np.prod(box))
+    kx, ky, kz = _half_k(box, mesh)
+    G = influence_ad(box, mesh, P, g)
+    inv4g2 = 1.0 / (4.0 * g * g)
+    r2s = np.zeros(G.shape)
+    T = np.zeros(G.shape)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for mx in range(-mmax, mmax + 1):
+            kmx = kx + TWO_PI * mx / h[0]
+            ux = np.sinc(kx * h[0] / TWO_PI + mx) ** (2 * P)
+            for my in range(-mmax, mmax + 1):
+                kmy = ky + TWO_PI * my / h[1]
+                uy = np.sinc(ky * h[1] / TWO_PI + my) ** (2 * P)
+                for mz in range(-mmax, mmax + 1):
+                    kmz = kz + TWO_PI * mz / h[2]
+                    uz = np.sinc(kz * h[2] / TWO_PI + mz) ** (2 * P)
+                    km2 = kmx[:, None, None] ** 2 + kmy[None, :, None] ** 2 + kmz[None, None, :] ** 2
+                    phi = 4.0 * math.pi * np.exp(-km2 * inv4g2) / km2
+                    u2 = ux[:, None, None] * uy[None, :, None] * uz[None, None, :]
+                    r2 = km2 * phi * phi  # |R(k_m)|^2
+                    t = u2 * km2 * phi    # U^2 (k_m . k_m) phi: the alias's own derivative against R(k_m)
+                    r2[~np.isfinite(r2)] = 0.0  # k = 0, m = 0 only
+                    t[~np.isfinite(t)] = 0.0
+                    r2s += r2
+                    T += t
+    s0x, s2x = _alias_sums_1d(kx, h[0], P)
+    s0y, s2y = _alias_sums_1d(ky, h[1], P)
+    s0z, s2z = _alias_sums_1d(kz, h[2], P)
+    S0 = s0x[:, None, None] * s0y[None, :, None] * s0z[None, None, :]
+    S2 = (s2x[:, None, None] * s0y[None, :, None] * s0z[None, None, :]
+          + s0x[:, None, None] * s2y[None, :, None] * s0z[None, None, :]
+          + s0x[:, None, None] * s0y[None, :, None] * s2z[None, None, :])
+    term = G * G * S0 * S2 - 2.0 * G * T + r2s
+    term[0, 0, 0] = 0.0
+    w = half_spectrum_weights(int(mesh[2]))[None, None, :]
+    Q = float(np.sum(w * term)) / V
+    return float(q2) * math.sqrt(max(Q, 0.0) / (n * V))
+
+
+def kspace_error(box, mesh, P: int, g: float, n: int, q2: float, mode: str = "ik") -> float:
+    if mode == "ik":
+        return kspace_error_ik(box, mesh, P, g, n, q2)
+    if mode == "ad":
+        return kspace_error_ad(box, mesh, P, g, n, q2)
+    raise ValueError(mode)
+
+
 def choose_mesh(box, n: int, q2: float, P: int, r_cut: float, rel_acc: float, kind: int = 1,
-                max_mesh: int = 1024):
+                max_mesh: int = 1024, mode: str = "ik"):
     """(mesh, g, estimated error): the first mesh of the scan that meets rel_acc."""
     box = [float(b) for b in box]
     g = estimate_g_ewald(rel_acc, r_cut, n, q2, box)
@@ -112,7 +185,7 @@ def choose_mesh(box, n: int, q2: float, P: int, r_cut: float, rel_acc: float, ki
         if max(mesh) > max_mesh:
             raise ValueError("no mesh up to the size limit meets the accuracy")
         if mesh != prev:
-            err = kspace_error_ik(box, mesh, P, g, n, q2)
+            err = kspace_error(box, mesh, P, g, n, q2, mode)
             if err <= rel_acc:
                 return mesh, g, err
             prev = mesh

@@ -108,13 +108,19 @@ void launch_green_setup(const GreenSetup &gs, double *G64, double *sf_sums, cuda
 }
 
 // ---------------------------------------------------------------------------
-// Setup-time k-space error estimate of an ik mesh (mesh choice for a target
-// accuracy): per half-spectrum k != 0, with weight w,
-//   w { sum_m 16 pi^2 exp(-k_m^2/2g^2) / k_m^2
-//       - [sum_m U^2(k_m) (k.k_m) 4 pi exp(-k_m^2/4g^2)/k_m^2]^2 / (k^2 D(k)^2) }
-// (the Hockney-Eastwood functional of the optimal influence function; D =
-// the full alias sum of U^2).  One FP64 partial per CTA, summed by the host
-// in CTA order.
+// Setup-time k-space error estimate of a mesh (mesh choice for a target
+// accuracy): per half-spectrum k != 0, with weight w and
+// phi(k) = 4 pi exp(-k^2/4g^2)/k^2,
+//  ik: w { sum_m 16 pi^2 exp(-k_m^2/2g^2) / k_m^2
+//          - [sum_m U^2(k_m) (k.k_m) phi(k_m)]^2 / (k^2 D(k)^2) }
+//      (the Hockney-Eastwood functional of the optimal influence function; D =
+//      the full alias sum of U^2);
+//  ad: w { G^2 D S2 - 2 G sum_m U^2(k_m) k_m^2 phi(k_m) + sum_m 16 pi^2 exp(-k_m^2/2g^2) / k_m^2 }
+//      (the functional of forces taken as the gradient of the interpolated
+//      potential, each alias with its own derivative, at the plan's ad
+//      influence function G = sum_m U^2(k_m) phi(k_m) / D^2; S2 = the full
+//      alias sum of U^2(k_m) k_m^2, which separates over dimensions).
+// One FP64 partial per CTA, summed by the host in CTA order.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(GREEN_THREADS) k_kspace_error(KErrSetup ks, double *__restrict__ part) {
     __shared__ double sh[GREEN_THREADS / 32];
@@ -132,7 +138,7 @@ __global__ void __launch_bounds__(GREEN_THREADS) k_kspace_error(KErrSetup ks, do
         const double k[3] = {ks.ktab[ix], ks.ktab[off[1] + iy], ks.ktab[off[2] + iz]};
         const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
         if (k2 == 0.0) continue;
-        double num = 0.0, s1 = 0.0;
+        double num = 0.0, s1 = 0.0, gnum = 0.0, tsum = 0.0;
         for (int mx = -2; mx <= 2; ++mx) {
             const double kmx = k[0] + twopi * mx / ks.h[0];
             const double ax = ks.atab[(mx + 2) * len + ix], ex = ks.etab[(mx + 2) * len + ix];
@@ -145,13 +151,26 @@ __global__ void __launch_bounds__(GREEN_THREADS) k_kspace_error(KErrSetup ks, do
                     const double ez = ks.etab[(mz + 2) * len + off[2] + iz];
                     const double km2 = kmx * kmx + kmy * kmy + kmz * kmz;
                     s1 += 16.0 * M_PI * M_PI * ex * ey * ez / km2;
-                    num += 4.0 * M_PI * ax * ay * az / km2 * (k[0] * kmx + k[1] * kmy + k[2] * kmz);
+                    if (ks.ad) {
+                        const double up = 4.0 * M_PI * ax * ay * az;  // U^2 k_m^2 phi(k_m)
+                        gnum += up / km2;                             // U^2 phi(k_m)
+                        tsum += up;
+                    } else {
+                        num += 4.0 * M_PI * ax * ay * az / km2 * (k[0] * kmx + k[1] * kmy + k[2] * kmz);
+                    }
                 }
             }
         }
-        const double D = ks.dtab[ix] * ks.dtab[off[1] + iy] * ks.dtab[off[2] + iz];
+        const double dx = ks.dtab[ix], dy = ks.dtab[off[1] + iy], dz = ks.dtab[off[2] + iz];
+        const double D = dx * dy * dz;
         const double w = (iz == 0 || (2 * (Mzh - 1) == ks.M[2] && iz == Mzh - 1)) ? 1.0 : 2.0;
-        acc += w * (s1 - num * num / (k2 * D * D));
+        if (ks.ad) {
+            const double G = gnum / (D * D);
+            const double S2 = ks.s2tab[ix] * dy * dz + dx * ks.s2tab[off[1] + iy] * dz + dx * dy * ks.s2tab[off[2] + iz];
+            acc += w * (G * G * D * S2 - 2.0 * G * tsum + s1);
+        } else {
+            acc += w * (s1 - num * num / (k2 * D * D));
+        }
     }
     const double v = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;

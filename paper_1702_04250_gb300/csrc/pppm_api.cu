@@ -289,33 +289,57 @@ int fft_size_host(int n, int kind) {
     }
 }
 
-// RMS k-space force error of an ik mesh for n random charges with
-// sum q^2 = q2 (units C e^2 / A^2): q2 sqrt(Q / (n V)), Q the
+// Full alias sum of U1^2(k_m) k_m^2 per dimension (|m| <= 2000), laid out as
+// ktab: the ad error functional's S2 factors.
+void alias_s2_table(const int M[3], const double h[3], int P, std::vector<double> &s2tab) {
+    const int Mzh = M[2] / 2 + 1;
+    const int dimlen[3] = {M[0], M[1], Mzh};
+    const int off[3] = {0, M[0], M[0] + M[1]};
+    s2tab.assign((size_t)M[0] + M[1] + Mzh, 0.0);
+    for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < dimlen[d]; ++i) {
+            const double kappa = grid_kappa(i, M[d]);
+            double s = 0.0;
+            for (int m = -2000; m <= 2000; ++m) {
+                const double km = (kappa + 2.0 * M_PI * m) / h[d];
+                s += alias_cross(kappa + 2.0 * M_PI * m, 0, P, 0) * km * km;
+            }
+            s2tab[off[d] + i] = s;
+        }
+}
+
+// RMS k-space force error of an ik (ad = false) or ad mesh for n random
+// charges with sum q^2 = q2 (units C e^2 / A^2): q2 sqrt(Q / (n V)), Q the
 // Hockney-Eastwood functional of k_kspace_error divided by V.  Synchronous,
 // on the calling thread's default stream.
-int kspace_error_ik(const int M[3], const double box[3], int P, double g, int64_t n, double q2, double *err) {
+int kspace_error_mesh(const int M[3], const double box[3], int P, double g, bool ad, int64_t n, double q2,
+                      double *err) {
     double h[3];
     for (int d = 0; d < 3; ++d) h[d] = box[d] / M[d];
     const double V = box[0] * box[1] * box[2];
     const int Mzh = M[2] / 2 + 1;
     const int len = M[0] + M[1] + Mzh;
-    std::vector<double> ktab, kdiff, atab, dtab, etab;
+    std::vector<double> ktab, kdiff, atab, dtab, etab, s2tab;
     alias_tables(M, h, P, g, ktab, kdiff, atab, dtab, nullptr, &etab);
-    double *tmp = nullptr;  // ktab | atab | dtab | etab | partials
-    const size_t words = (size_t)len * 12 + KERR_MAX_BLOCKS;
+    if (ad) alias_s2_table(M, h, P, s2tab);
+    else s2tab.assign(len, 0.0);
+    double *tmp = nullptr;  // ktab | atab | dtab | etab | s2tab | partials
+    const size_t words = (size_t)len * 13 + KERR_MAX_BLOCKS;
     if (cudaMalloc(&tmp, words * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return PPPM_ENOMEM;
     }
     double *d_ktab = tmp, *d_atab = tmp + len, *d_dtab = d_atab + 5 * (size_t)len, *d_etab = d_dtab + len;
-    double *d_part = d_etab + 5 * (size_t)len;
+    double *d_s2tab = d_etab + 5 * (size_t)len;
+    double *d_part = d_s2tab + len;
     std::vector<double> part(KERR_MAX_BLOCKS, 0.0);
     int rc = PPPM_OK, nb = 0;
     do {
         if (cudaMemcpy(d_ktab, ktab.data(), sizeof(double) * len, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(d_atab, atab.data(), sizeof(double) * 5 * len, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(d_dtab, dtab.data(), sizeof(double) * len, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(d_etab, etab.data(), sizeof(double) * 5 * len, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaMemcpy(d_etab, etab.data(), sizeof(double) * 5 * len, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d_s2tab, s2tab.data(), sizeof(double) * len, cudaMemcpyHostToDevice) != cudaSuccess) {
             rc = PPPM_ECUDA;
             break;
         }
@@ -329,6 +353,8 @@ int kspace_error_ik(const int M[3], const double box[3], int P, double g, int64_
         ks.atab = d_atab;
         ks.dtab = d_dtab;
         ks.etab = d_etab;
+        ks.s2tab = d_s2tab;
+        ks.ad = ad ? 1 : 0;
         nb = launch_kspace_error(ks, d_part, 0);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpy(part.data(), d_part, sizeof(double) * nb, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -652,17 +678,18 @@ int pppm_kspace_error(const double box[3], const int mesh[3], int order, double 
                       double q2, double *err_out) {
     if (!box || !mesh || !err_out || n <= 0 || !(q2 > 0) || !(g_ewald > 0) || !std::isfinite(g_ewald))
         return PPPM_EINVAL;
-    if (order < 2 || order > MAXP || diff_mode != PPPM_IK) return PPPM_EINVAL;
+    if (order < 2 || order > MAXP || (diff_mode != PPPM_IK && diff_mode != PPPM_AD)) return PPPM_EINVAL;
     for (int d = 0; d < 3; ++d) {
         if (!(box[d] > 0) || !std::isfinite(box[d])) return PPPM_EINVAL;
         if (mesh[d] < order || mesh[d] > MAX_MESH) return PPPM_EINVAL;
     }
-    return kspace_error_ik(mesh, box, order, g_ewald, n, q2, err_out);
+    return kspace_error_mesh(mesh, box, order, g_ewald, diff_mode == PPPM_AD, n, q2, err_out);
 }
 
 int pppm_choose_mesh(const double box[3], int64_t n, double q2, int order, int diff_mode, double r_cut,
                      double rel_acc, int kind, int mesh_out[3], double *g_out, double *err_out) {
-    if (!box || !mesh_out || !g_out || order < 2 || order > MAXP || diff_mode != PPPM_IK || kind < 0 || kind > 2)
+    if (!box || !mesh_out || !g_out || order < 2 || order > MAXP || (diff_mode != PPPM_IK && diff_mode != PPPM_AD) ||
+        kind < 0 || kind > 2)
         return PPPM_EINVAL;
     double g = 0.0;
     int rc = pppm_estimate_g(rel_acc, r_cut, n, q2, box, &g);
@@ -679,7 +706,7 @@ int pppm_choose_mesh(const double box[3], int64_t n, double q2, int order, int d
         }
         if (mesh[0] == prev[0] && mesh[1] == prev[1] && mesh[2] == prev[2]) continue;
         double err = 0.0;
-        if ((rc = kspace_error_ik(mesh, box, order, g, n, q2, &err))) return rc;
+        if ((rc = kspace_error_mesh(mesh, box, order, g, diff_mode == PPPM_AD, n, q2, &err))) return rc;
         if (err <= rel_acc) {
             for (int d = 0; d < 3; ++d) mesh_out[d] = mesh[d];
             *g_out = g;

@@ -410,15 +410,17 @@ struct GreenSetup {
     const double *btab;    // [3 n][Mx + My + Mzh] self-force alias sums, n = 0,1,2
 };
 void launch_green_setup(const GreenSetup &gs, double *G64, double *sf_sums, cudaStream_t s);
-// Setup-time k-space error estimate of an ik mesh: tables as for GreenSetup
-// plus etab[5][Mx + My + Mzh] = exp(-k_m^2 / 2g^2) per dimension and alias.
-// Writes one partial sum of the error functional per CTA (at most
-// KERR_MAX_BLOCKS) and returns the CTA count.
+// Setup-time k-space error estimate of an ik or ad mesh: tables as for
+// GreenSetup plus etab[5][Mx + My + Mzh] = exp(-k_m^2 / 2g^2) per dimension
+// and alias, and (ad) s2tab[Mx + My + Mzh] = the full alias sum of
+// U1^2(k_m) k_m^2 per dimension.  Writes one partial sum of the error
+// functional per CTA (at most KERR_MAX_BLOCKS) and returns the CTA count.
 constexpr int KERR_MAX_BLOCKS = 152 * 8;
 struct KErrSetup {
     int M[3], Mzh;
+    int ad;  // 1: forces as the gradient of the interpolated potential
     double h[3];
-    const double *ktab, *atab, *dtab, *etab;
+    const double *ktab, *atab, *dtab, *etab, *s2tab;
 };
 int launch_kspace_error(const KErrSetup &ks, double *part, cudaStream_t s);
 // Host driver of the above for one system (pppm_api.cu): G64 on the device,

@@ -110,10 +110,10 @@ def fft_size(n: int, kind: int = FFT_SMOOTH) -> int:
 
 
 def kspace_error(box, mesh, order: int, g_ewald: float, n: int, q2: float, mode: str = "ik") -> float:
-    """Estimated RMS k-space force error of an ik mesh (units of C e^2 / A^2)."""
+    """Estimated RMS k-space force error of an ik or ad mesh (units of C e^2 / A^2)."""
     out = ctypes.c_double()
     m = (ctypes.c_int * 3)(*[int(v) for v in mesh])
-    _check(lib().pppm_kspace_error(_d3(box), m, int(order), float(g_ewald), MODES[mode], int(n), float(q2),
+    _check(lib().pppm_kspace_error(_d3(box), m, int(order), float(g_ewald), MODES.get(mode, -1), int(n), float(q2),
                                    ctypes.byref(out)), "pppm_kspace_error")
     return out.value
 
@@ -124,7 +124,7 @@ def choose_mesh(box, n: int, q2: float, order: int, r_cut: float, rel_acc: float
     mesh = (ctypes.c_int * 3)()
     g = ctypes.c_double()
     err = ctypes.c_double()
-    _check(lib().pppm_choose_mesh(_d3(box), int(n), float(q2), int(order), MODES[mode], float(r_cut),
+    _check(lib().pppm_choose_mesh(_d3(box), int(n), float(q2), int(order), MODES.get(mode, -1), float(r_cut),
                                   float(rel_acc), int(kind), mesh, ctypes.byref(g), ctypes.byref(err)),
            "pppm_choose_mesh")
     return tuple(mesh), g.value, err.value
