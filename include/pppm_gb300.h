@@ -335,12 +335,15 @@ int pppm_batch_set_graph(pppm_batch *b, int enable);
 int pppm_batch_sync(pppm_batch *b);
 /* Kernel variants of a batch: bit P (P = 2..7) makes the FP32C make_rho of
  * the order-P systems accumulate in four interleaved brick copies (see
- * pppm_set_variant bit 2); PPPM_EINVAL for other bits or precisions.
- * pppm_batch_autotune times the whole call (eager launches; one warm-up and
- * five timed calls per setting) with each present order's bit flipped in
- * turn, keeps the faster setting per order, writes the mask to choice_out
- * (nullable) and leaves f holding a valid result.  Both drop the captured
- * graph; a non-FP32C batch keeps mask 0. */
+ * pppm_set_variant bit 2; PPPM_EINVAL for other precisions); bit 8 + P runs
+ * the order-P fieldforce tile-staged, one CTA per system tile staging its
+ * field brick in shared memory (see pppm_set_variant bit 0; any precision).
+ * PPPM_EINVAL for other bits.  pppm_batch_autotune times the whole call as
+ * the batch runs it (one graph per setting when graph mode is on; one
+ * warm-up and five timed calls, scored by the fastest) with each present
+ * order's make_rho bit (FP32C only) and fieldforce bit flipped in turn,
+ * keeps every flip that is faster, writes the mask to choice_out (nullable)
+ * and leaves f holding a valid result.  Both drop the captured graph. */
 int pppm_batch_set_variant(pppm_batch *b, int variants);
 int pppm_batch_autotune(pppm_batch *b, const void *x, const void *q, void *f, int *choice_out);
 /* [0] systems, [1] total particles, [2] mesh-size classes, [3] distinct orders */

@@ -324,15 +324,17 @@ __global__ void __launch_bounds__(FF_THREADS) k_batch_fieldforce(const BatchSys<
                                 blockIdx.x - bl.boff[e]);
 }
 
+// One CTA per mesh tile (tile = the CTA's index within its system): stage the
+// field brick, then gather.  An ik field in three planes (g.planar_stride > 0,
+// the batched path) is staged point by point into the same float4 brick.
 template <typename R, int P, int MODE>
-__global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, SortBufs b,
-                                                                 const R *__restrict__ field, R *__restrict__ f,
-                                                                 R *__restrict__ dq, R qC, SelfCoef sc, R gself,
-                                                                 R gbg) {
+__device__ __forceinline__ void fieldforce_tiled_body(const Geom<R> &g, const SortBufs &b,
+                                                      const R *__restrict__ field, R *__restrict__ f,
+                                                      R *__restrict__ dq, R qC, const double *c, R gself, R gbg,
+                                                      int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *brick = reinterpret_cast<R *>(smem_raw);
 
-    const int tile = blockIdx.x;
     const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
     if (start == end) return;
     const int tz = tile % g.T[2];
@@ -359,7 +361,12 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, Sort
                     const int64_t p = ((int64_t)gx * g.M[1] + gy) * g.M[2] + gz;
                     const int e = (ex * Ey + ey) * Ez + lz;
                     if (MODE == 0) {
-                        if (sizeof(R) == 4) {
+                        if (g.planar_stride > 0) {  // three planes: one copy per component
+                            const int64_t ps = g.planar_stride;
+                            cp_async<sizeof(R)>(brick + 4 * e, field + p);
+                            cp_async<sizeof(R)>(brick + 4 * e + 1, field + p + ps);
+                            cp_async<sizeof(R)>(brick + 4 * e + 2, field + p + 2 * ps);
+                        } else if (sizeof(R) == 4) {
                             cp_async<16>(brick + 4 * e, field + 4 * p);
                         } else {
                             cp_async<16>(brick + 4 * e, field + 4 * p);
@@ -406,9 +413,25 @@ __global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, Sort
                 return as_vec<R>(brick[e]);
             }, e0, e1, e2);
         }
-        finish_particle<R, P, MODE>(g, b, live, k, j, w, e0, e1, e2, r.x, r.y, r.z, r.w, f, dq, qC, sc.c, gself,
-                                    gbg);
+        finish_particle<R, P, MODE>(g, b, live, k, j, w, e0, e1, e2, r.x, r.y, r.z, r.w, f, dq, qC, c, gself, gbg);
     }
+}
+
+template <typename R, int P, int MODE>
+__global__ void __launch_bounds__(FF_THREADS) k_fieldforce_tiled(Geom<R> g, SortBufs b,
+                                                                 const R *__restrict__ field, R *__restrict__ f,
+                                                                 R *__restrict__ dq, R qC, SelfCoef sc, R gself,
+                                                                 R gbg) {
+    fieldforce_tiled_body<R, P, MODE>(g, b, field, f, dq, qC, sc.c, gself, gbg, blockIdx.x);
+}
+
+template <typename R, int P, int MODE>
+__global__ void __launch_bounds__(FF_THREADS) k_batch_fieldforce_tiled(const BatchSys<R> *__restrict__ sys,
+                                                                       BatchList bl, R *__restrict__ f, R qC) {
+    const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
+    const BatchSys<R> &S = sys[bl.ids[e]];
+    fieldforce_tiled_body<R, P, MODE>(S.g, S.sb, S.field, f + 3 * S.poff, nullptr, qC, S.sf, R(0), R(0),
+                                      blockIdx.x - bl.boff[e]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1079,6 +1102,12 @@ static cudaError_t prepare_ff_p() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fieldforce_tiled<R, P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)ff_brick_bytes<R, P, 2>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_fieldforce_tiled<R, P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ff_brick_bytes<R, P, 0>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_fieldforce_tiled<R, P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ff_brick_bytes<R, P, 1>());
     return e;
 }
 
@@ -1096,31 +1125,40 @@ cudaError_t prepare_fieldforce(int P) {
 }
 
 template <typename R, int P>
-static void launch_batch_ff(const BatchSys<R> *sys, const BatchList &bl, bool ik, R *f, R qC, cudaStream_t s) {
+static void launch_batch_ff(const BatchSys<R> *sys, const BatchList &bl, bool ik, bool tiled, R *f, R qC,
+                            cudaStream_t s) {
+    if (tiled) {
+        if (ik)
+            k_batch_fieldforce_tiled<R, P, 0><<<bl.nblocks, FF_THREADS, ff_brick_bytes<R, P, 0>(), s>>>(sys, bl, f, qC);
+        else
+            k_batch_fieldforce_tiled<R, P, 1><<<bl.nblocks, FF_THREADS, ff_brick_bytes<R, P, 1>(), s>>>(sys, bl, f, qC);
+        return;
+    }
     if (ik)
         k_batch_fieldforce<R, P, 0><<<bl.nblocks, FF_THREADS, 0, s>>>(sys, bl, f, qC);
     else
         k_batch_fieldforce<R, P, 1><<<bl.nblocks, FF_THREADS, 0, s>>>(sys, bl, f, qC);
 }
 
-// CTA counts in bl are ceil(n / ff_particles_per_cta(P)) per system (one group of P lanes per particle).
+// CTA counts in bl: ceil(n / ff_particles_per_cta(P)) per system (one group of
+// P lanes per particle), or the system's tile count when tiled.
 template <typename R>
-void launch_batch_fieldforce(const BatchSys<R> *sys, const BatchList &bl, int P, bool ik, R *f, R qC,
+void launch_batch_fieldforce(const BatchSys<R> *sys, const BatchList &bl, int P, bool ik, bool tiled, R *f, R qC,
                              cudaStream_t s) {
     if (bl.nblocks == 0) return;
     switch (P) {
-        case 2: launch_batch_ff<R, 2>(sys, bl, ik, f, qC, s); break;
-        case 3: launch_batch_ff<R, 3>(sys, bl, ik, f, qC, s); break;
-        case 4: launch_batch_ff<R, 4>(sys, bl, ik, f, qC, s); break;
-        case 5: launch_batch_ff<R, 5>(sys, bl, ik, f, qC, s); break;
-        case 6: launch_batch_ff<R, 6>(sys, bl, ik, f, qC, s); break;
-        case 7: launch_batch_ff<R, 7>(sys, bl, ik, f, qC, s); break;
+        case 2: launch_batch_ff<R, 2>(sys, bl, ik, tiled, f, qC, s); break;
+        case 3: launch_batch_ff<R, 3>(sys, bl, ik, tiled, f, qC, s); break;
+        case 4: launch_batch_ff<R, 4>(sys, bl, ik, tiled, f, qC, s); break;
+        case 5: launch_batch_ff<R, 5>(sys, bl, ik, tiled, f, qC, s); break;
+        case 6: launch_batch_ff<R, 6>(sys, bl, ik, tiled, f, qC, s); break;
+        case 7: launch_batch_ff<R, 7>(sys, bl, ik, tiled, f, qC, s); break;
         default: break;
     }
 }
-template void launch_batch_fieldforce<float>(const BatchSys<float> *, const BatchList &, int, bool, float *, float,
-                                             cudaStream_t);
-template void launch_batch_fieldforce<double>(const BatchSys<double> *, const BatchList &, int, bool, double *,
+template void launch_batch_fieldforce<float>(const BatchSys<float> *, const BatchList &, int, bool, bool, float *,
+                                             float, cudaStream_t);
+template void launch_batch_fieldforce<double>(const BatchSys<double> *, const BatchList &, int, bool, bool, double *,
                                               double, cudaStream_t);
 
 template cudaError_t prepare_fieldforce<float>(int);

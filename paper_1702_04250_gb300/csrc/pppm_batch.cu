@@ -6,8 +6,9 @@
 // Distribute-Force, Sec. 3.2 Poisson solve) on a list of systems: CTAs of all
 // systems are laid out back to back and every CTA finds its system by binary
 // search.  Stages templated on the order P run once per order present.  The
-// 3-D FFTs run as one batched cuFFT transform per mesh-size class (systems
-// with the same mesh are stored contiguously).  The energy/virial sums run on
+// 3-D FFTs run as one batched cuFFT transform per mesh-size class and
+// direction (systems with the same mesh are stored contiguously; the ik
+// inverse batches the three field components of every system).  The energy/virial sums run on
 // a forked stream beside the inverse FFTs and fieldforce.
 #include <algorithm>
 #include <cmath>
@@ -61,13 +62,14 @@ struct pppm_batch {
     void *d_sys = nullptr;              // BatchSys<R>[nsys]
     int *d_lists = nullptr;
     BatchList map_list{}, green_list{};
-    BatchList rho_list[MAXP + 1] = {}, ff_list[MAXP + 1] = {};
+    BatchList rho_list[MAXP + 1] = {}, ff_list[MAXP + 1] = {}, ff_tile_list[MAXP + 1] = {};
     std::vector<MeshClass> classes;
     int *err = nullptr;
     bool graph_on = false;
     cudaGraphExec_t gexec = nullptr;
     const void *gkey[4] = {nullptr, nullptr, nullptr, nullptr};
-    int variants = 0;  // bit P: FP32C make_rho of order P in four brick copies
+    int variants = 0;  // bit P: FP32C make_rho of order P in four brick copies;
+                       // bit 8 + P: tile-staged fieldforce for order P
     std::vector<void *> allocs;
 };
 
@@ -296,6 +298,7 @@ int batch_build(pppm_batch *b, const double *box, const int64_t *n, const int *o
         pend.push_back({&b->ff_list[P], add_list(b->ff_list[P], ids, [&](int s) {
                            return (hs[s].n + ff_particles_per_cta(P) - 1) / ff_particles_per_cta(P);
                        })});
+        pend.push_back({&b->ff_tile_list[P], add_list(b->ff_tile_list[P], ids, [&](int s) { return hs[s].g.ntiles; })});
     }
     if ((rc = bmalloc(b, (void **)&b->d_lists, sizeof(int) * std::max<size_t>(host.size(), 1)))) return rc;
     if (!host.empty() &&
@@ -318,8 +321,9 @@ int batch_build(pppm_batch *b, const double *box, const int64_t *n, const int *o
             return PPPM_ECUFFT;
         mc.have_r2c = true;
         cufftResult r;
-        if (b->ik)  // one component per exec: 3 spectra per system in, 3 padded planes per system out
-            r = cufftPlanMany(&mc.c2r, 3, nn, hemb, 1, (int)(3 * mc.Mhalf), inemb, 1, (int)(3 * mc.Mpad), tc2r, k);
+        if (b->ik)  // the 3 components of every system as one batch: spectra [sys][3][Mhalf] in,
+                    // padded planes [sys][3][Mpad] out
+            r = cufftPlanMany(&mc.c2r, 3, nn, hemb, 1, (int)mc.Mhalf, inemb, 1, (int)mc.Mpad, tc2r, 3 * k);
         else
             r = cufftPlanMany(&mc.c2r, 3, nn, hemb, 1, (int)mc.Mhalf, inemb, 1, (int)mc.Mtot, tc2r, k);
         if (r != CUFFT_SUCCESS) return PPPM_ECUFFT;
@@ -377,18 +381,16 @@ int batch_enqueue(pppm_batch *b, const R *x, const R *q, R *f, double *ev) {
     for (size_t i = 0; i < b->classes.size(); ++i) {
         auto &mc = b->classes[i];
         if (cufftSetStream(mc.c2r, b->lanes[i % nl]) != CUFFT_SUCCESS) return PPPM_ECUFFT;
-        const int ncomp = b->ik ? 3 : 1;
-        for (int a = 0; a < ncomp; ++a) {
-            char *in = (char *)mc.spec + 2 * rs * mc.Mhalf * a;
-            R *out = (R *)mc.field + (b->ik ? mc.Mpad * a : 0);
-            cufftResult r = b->fp64 ? cufftExecZ2D(mc.c2r, (cufftDoubleComplex *)in, (cufftDoubleReal *)out)
-                                    : cufftExecC2R(mc.c2r, (cufftComplex *)in, (cufftReal *)out);
-            if (r != CUFFT_SUCCESS) return PPPM_ECUFFT;
-        }
+        cufftResult r = b->fp64 ? cufftExecZ2D(mc.c2r, (cufftDoubleComplex *)mc.spec, (cufftDoubleReal *)mc.field)
+                                : cufftExecC2R(mc.c2r, (cufftComplex *)mc.spec, (cufftReal *)mc.field);
+        if (r != CUFFT_SUCCESS) return PPPM_ECUFFT;
     }
     if (!fan_in(b, s) || !fan_out(b, s)) return PPPM_ECUDA;
-    for (int P = 2; P <= MAXP; ++P)
-        launch_batch_fieldforce<R>(sys, b->ff_list[P], P, b->ik, f, (R)b->C, b->lanes[P % nl]);
+    for (int P = 2; P <= MAXP; ++P) {
+        const bool tiled = ((b->variants >> (8 + P)) & 1) != 0;
+        launch_batch_fieldforce<R>(sys, tiled ? b->ff_tile_list[P] : b->ff_list[P], P, b->ik, tiled, f, (R)b->C,
+                                   b->lanes[P % nl]);
+    }
     if (!fan_in(b, s)) return PPPM_ECUDA;
     if (cudaStreamWaitEvent(s, b->join, 0) != cudaSuccess) return PPPM_ECUDA;
     return cudaGetLastError() == cudaSuccess ? PPPM_OK : PPPM_ECUDA;
@@ -462,6 +464,7 @@ int pppm_batch_setup(pppm_batch **out, int nsys, const double *box, const int64_
         for (int s = 0; s < nsys; ++s) used |= order[s] == P;
         if (!used) continue;
         cudaError_t e = b->fp64 ? prepare_make_rho<double>(P, false) : prepare_make_rho<float>(P, b->comp);
+        if (e == cudaSuccess) e = b->fp64 ? prepare_fieldforce<double>(P) : prepare_fieldforce<float>(P);
         if (e != cudaSuccess) rc = PPPM_ECUDA;
     }
     if (!rc) rc = b->fp64 ? batch_build<double>(b, box, n, order, mesh, g_ewald)
@@ -521,8 +524,8 @@ int pppm_batch_compute(pppm_batch *b, const void *x, const void *q, void *f, dou
 }
 
 int pppm_batch_set_variant(pppm_batch *b, int variants) {
-    if (!b || (variants & ~0xFC)) return PPPM_EINVAL;
-    if (variants && !b->comp) return PPPM_EINVAL;  // the brick copies are the FP32C accumulator
+    if (!b || (variants & ~0xFCFC)) return PPPM_EINVAL;
+    if ((variants & 0xFC) && !b->comp) return PPPM_EINVAL;  // the brick copies are the FP32C accumulator
     b->variants = variants;
     if (b->gexec) {
         cudaGraphExecDestroy(b->gexec);
@@ -531,53 +534,58 @@ int pppm_batch_set_variant(pppm_batch *b, int variants) {
     return PPPM_OK;
 }
 
+constexpr int BATCH_TUNE_TIMED = 5;  // timed calls per setting, after one warm-up
+
 int pppm_batch_autotune(pppm_batch *b, const void *x, const void *q, void *f, int *choice_out) {
     if (!b) return PPPM_EINVAL;
     if (b->ntot > 0 && (!x || !q || !f)) return PPPM_EINVAL;
     int best = b->variants;
-    if (b->comp) {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PPPM_ECUDA;
-        auto time_calls = [&](int v, float &ms_out) -> int {
-            b->variants = v;
-            float tot = 0.0f;
-            for (int it = 0; it < 6; ++it) {  // one warm-up, five timed (eager launches)
-                if (cudaEventRecord(e0, b->stream) != cudaSuccess) return PPPM_ECUDA;
-                const int rc = batch_enqueue_any(b, x, q, f, nullptr);
-                if (rc) return rc;
-                if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
-                    return PPPM_ECUDA;
-                float ms = 0.0f;
-                if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return PPPM_ECUDA;
-                if (it > 0) tot += ms;
-            }
-            ms_out = tot;
-            return PPPM_OK;
-        };
-        float t_best = 0.0f;
-        int rc = time_calls(best, t_best);
-        // each order's make_rho is its own launch: choose its brick on its own
-        for (int P = 2; P <= MAXP && rc == PPPM_OK; ++P) {
-            if (b->rho_list[P].nblocks == 0) continue;
-            const int v = best ^ (1 << P);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PPPM_ECUDA;
+    // each setting is timed the way the batch runs (one graph when graph mode
+    // is on), scored by its fastest call
+    auto time_calls = [&](int v, float &ms_out) -> int {
+        const int rc0 = pppm_batch_set_variant(b, v);
+        if (rc0) return rc0;
+        float fastest = 1e30f;
+        for (int it = 0; it < 1 + BATCH_TUNE_TIMED; ++it) {
+            if (cudaEventRecord(e0, b->stream) != cudaSuccess) return PPPM_ECUDA;
+            const int rc = pppm_batch_compute(b, x, q, f, nullptr);
+            if (rc) return rc;
+            if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return PPPM_ECUDA;
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return PPPM_ECUDA;
+            if (it > 0) fastest = fminf(fastest, ms);
+        }
+        ms_out = fastest;
+        return PPPM_OK;
+    };
+    float t_best = 0.0f;
+    int rc = time_calls(best, t_best);
+    // each order's make_rho and fieldforce are launches of their own: choose
+    // each one's kernel on its own, flipping one bit at a time
+    for (int P = 2; P <= MAXP && rc == PPPM_OK; ++P) {
+        if (b->rho_list[P].nblocks == 0) continue;
+        for (int bit : {P, 8 + P}) {
+            if (bit < 8 && !b->comp) continue;  // the brick copies are the FP32C accumulator
+            const int v = best ^ (1 << bit);
             float t = 0.0f;
             rc = time_calls(v, t);
-            if (rc == PPPM_OK && t < t_best) {
+            if (rc) break;
+            if (t < t_best) {
                 t_best = t;
                 best = v;
             }
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        b->variants = best;
-        if (b->gexec) {
-            cudaGraphExecDestroy(b->gexec);
-            b->gexec = nullptr;
-        }
-        if (rc) return rc;
-        // leave f holding the chosen setting's result
-        if ((rc = batch_enqueue_any(b, x, q, f, nullptr))) return rc;
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int rs = pppm_batch_set_variant(b, best);
+    if (rc) return rc;
+    if (rs) return rs;
+    // leave f holding the chosen setting's result
+    if ((rc = pppm_batch_compute(b, x, q, f, nullptr))) return rc;
     if (choice_out) *choice_out = best;
     return PPPM_OK;
 }

@@ -396,7 +396,7 @@ void launch_batch_green(const BatchSys<R> *sys, const BatchList &all, bool ik, c
 template <typename R>
 void launch_batch_energy_final(const BatchSys<R> *sys, int nsys, double *ev, cudaStream_t s);
 template <typename R>
-void launch_batch_fieldforce(const BatchSys<R> *sys, const BatchList &byP, int P, bool ik, R *f, R qC,
+void launch_batch_fieldforce(const BatchSys<R> *sys, const BatchList &byP, int P, bool ik, bool tiled, R *f, R qC,
                              cudaStream_t s);
 
 // Setup: G(k) in FP64 over the half spectrum and the ad self-force sums.

@@ -88,8 +88,10 @@ def test_small_batch_vs_oracle(torch, mode, prec):
 
 
 def test_batch_variants_and_autotune(torch):
-    """Every order's make_rho brick (one or four copies) gives the same
-    result; autotune returns a valid mask; FP64 batches refuse the bits."""
+    """Every order's make_rho brick (one or four copies) and fieldforce
+    (per particle through L1, or tile-staged from the planar field) give the
+    same result; autotune returns a valid mask; FP64 batches refuse the
+    make_rho bits but take the fieldforce ones."""
     from paper_1702_04250_gb300 import pppm
 
     systems = small_batch()
@@ -97,22 +99,42 @@ def test_batch_variants_and_autotune(torch):
     q = torch.tensor(np.concatenate([s["q"] for s in systems]), dtype=torch.float32, device="cuda")
     b = pppm.PPPMBatch(systems, mode="ik", precision="fp32c")
     outs = []
-    for v in (0, 0xFC):
+    for v in (0, 0xFC, 0xFC00, 0xFCFC, 0x0800 | 0x20):
         b.set_variant(v)
         f, ev = b.compute(x, q)
         b.sync()
         outs.append((f.double().cpu().numpy(), ev.cpu().numpy().copy()))
-    assert rel_rms(outs[1][0], outs[0][0]) < 1e-5
+    for o in outs[1:]:
+        assert rel_rms(o[0], outs[0][0]) < 1e-5
     choice = b.autotune(x, q)
-    assert choice & ~0xFC == 0
+    assert choice & ~0xFCFC == 0
     f, ev = b.compute(x, q)
     b.sync()
     assert rel_rms(f.double().cpu().numpy(), outs[0][0]) < 1e-5
     with pytest.raises(pppm.PPPMError):
         b.set_variant(1)
+    with pytest.raises(pppm.PPPMError):
+        b.set_variant(1 << 16)
     b64 = pppm.PPPMBatch(systems, mode="ik", precision="fp64")
     with pytest.raises(pppm.PPPMError):
         b64.set_variant(1 << 5)
+    x64, q64 = x.double(), q.double()
+    f0, _ = b64.compute(x64, q64)
+    b64.sync()
+    f0 = f0.cpu().numpy()
+    b64.set_variant(0xFC00)  # tile-staged fieldforce of every order, FP64
+    f1, _ = b64.compute(x64, q64)
+    b64.sync()
+    assert rel_rms(f1.cpu().numpy(), f0) < 1e-12
+    for mode in ("ad",):
+        ba = pppm.PPPMBatch(systems, mode=mode, precision="fp32c")
+        fa0, _ = ba.compute(x, q)
+        ba.sync()
+        fa0 = fa0.double().cpu().numpy()
+        ba.set_variant(0xFC00)
+        fa1, _ = ba.compute(x, q)
+        ba.sync()
+        assert rel_rms(fa1.double().cpu().numpy(), fa0) < 1e-5
 
 
 def test_small_batch_graph_matches(torch):
