@@ -120,8 +120,13 @@ def _alias_sums_1d(k, h: float, P: int, mmax: int = ALIAS_FULL):
     return np.sum(u, axis=1), np.sum(u * km * km, axis=1)
 
 
-def kspace_error_ad(box, mesh, P: int, g: float, n: int, q2: float, mmax: int = 2) -> float:
-    """RMS k-space force error of an ad mesh for n random charges (see module doc)."""
+def kspace_error_ad(box, mesh, P: int, g: float, n: int, q2: float, mmax: int = 2, conditioning: bool = False):
+    """RMS k-space force error of an ad mesh for n random charges (see module doc).
+
+    With conditioning=True, returns (error, kappa), kappa = the sum of the
+    three terms' magnitudes over their signed sum: on accurate meshes the
+    terms cancel (the Cauchy-Schwarz gap between sum |R|^2 and T^2/(S0 S2)),
+    and FP64 rounding of the alias sums is amplified by kappa."""
     box = np.asarray(box, dtype=np.float64)
     mesh = np.asarray(mesh, dtype=np.int64)
     h = box / mesh
@@ -157,11 +162,17 @@ def kspace_error_ad(box, mesh, P: int, g: float, n: int, q2: float, mmax: int = 
     S2 = (s2x[:, None, None] * s0y[None, :, None] * s0z[None, None, :]
           + s0x[:, None, None] * s2y[None, :, None] * s0z[None, None, :]
           + s0x[:, None, None] * s0y[None, :, None] * s2z[None, None, :])
-    term = G * G * S0 * S2 - 2.0 * G * T + r2s
+    a, b, c = G * G * S0 * S2, 2.0 * G * T, r2s
+    term = a - b + c
     term[0, 0, 0] = 0.0
     w = half_spectrum_weights(int(mesh[2]))[None, None, :]
     Q = float(np.sum(w * term)) / V
-    return float(q2) * math.sqrt(max(Q, 0.0) / (n * V))
+    err = float(q2) * math.sqrt(max(Q, 0.0) / (n * V))
+    if not conditioning:
+        return err
+    mag = np.abs(a) + np.abs(b) + np.abs(c)
+    mag[0, 0, 0] = 0.0
+    return err, float(np.sum(w * mag)) / V / Q
 
 
 def kspace_error(box, mesh, P: int, g: float, n: int, q2: float, mode: str = "ik") -> float:

@@ -44,6 +44,16 @@ def test_kspace_error_vs_oracle(pppm, box, mesh, P, g):
     assert gpu == pytest.approx(ref, rel=1e-6)
 
 
+def ad_tolerance(kappa):
+    """Relative tolerance of an ad estimate: its three terms cancel by a factor
+    kappa (the oracle's conditioning, 1e2 to 1e11 on these meshes), which
+    amplifies FP64 rounding of the alias sums (2^-53 each, the device's exact
+    cosine series against the oracle's 4001-term sums); the error is the
+    square root of the functional, halving the relative spread; 8 for the
+    sums' accumulated roundings."""
+    return max(1e-6, 8 * 2.0 ** -53 * kappa / 2)
+
+
 @pytest.mark.parametrize("box,mesh,P,g", [
     ((10.0, 10.0, 10.0), (8, 8, 8), 3, 0.35),
     ((12.0, 13.2, 10.8), (10, 12, 14), 4, 0.4),
@@ -53,11 +63,11 @@ def test_kspace_error_vs_oracle(pppm, box, mesh, P, g):
 ])
 def test_ad_kspace_error_vs_oracle(pppm, box, mesh, P, g):
     """The ad functional: G^2 S0 S2 - 2 G T + sum |R|^2 per k, at the plan's
-    ad influence function; the same cancellation bound as ik."""
+    ad influence function, within the tolerance its conditioning allows."""
     n, q2 = 1234, 987.5
     gpu = pppm.kspace_error(box, mesh, P, g, n, q2, mode="ad")
-    ref = kspace_error_ad(box, mesh, P, g, n, q2)
-    assert gpu == pytest.approx(ref, rel=1e-6)
+    ref, kappa = kspace_error_ad(box, mesh, P, g, n, q2, conditioning=True)
+    assert gpu == pytest.approx(ref, rel=ad_tolerance(kappa))
     assert gpu > pppm.kspace_error(box, mesh, P, g, n, q2)  # ad is the less accurate form
 
 
@@ -85,7 +95,8 @@ def test_choose_mesh_ad_vs_oracle(pppm, box, n, P, r_cut, acc, kind):
     mesh, g, err = pppm.choose_mesh(box, n, q2, P, r_cut, acc, kind, mode="ad")
     rmesh, rg, rerr = choose_mesh(box, n, q2, P, r_cut, acc, kind, mode="ad")
     assert mesh == rmesh
-    assert err == pytest.approx(rerr, rel=1e-6) and err <= acc
+    _, kappa = kspace_error_ad(box, rmesh, P, rg, n, q2, conditioning=True)
+    assert err == pytest.approx(rerr, rel=ad_tolerance(kappa)) and err <= acc
     ik_mesh, _, _ = pppm.choose_mesh(box, n, q2, P, r_cut, acc, kind)
     assert np.prod(mesh) >= np.prod(ik_mesh)  # ad needs at least the ik mesh
 
