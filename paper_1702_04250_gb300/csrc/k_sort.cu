@@ -5,10 +5,12 @@
 // particles contiguously.
 //
 // Two kernels:
-//  k_particle_map  anchor + tile histogram (atomic ranks) and per-block sums
-//                  of q and q^2.  With more than SMALL_TILES tiles the last
-//                  block to finish turns the histogram into tile offsets
-//                  (exclusive scan).
+//  k_particle_map  anchor + tile histogram (atomic ranks, one atomic per run
+//                  of consecutive lanes with the same tile) and per-block
+//                  sums of q and q^2; one particle per thread, or
+//                  MAP_NPT_BIG on large systems.  With more than SMALL_TILES
+//                  tiles the last block to finish turns the histogram into
+//                  tile offsets (exclusive scan).
 //  k_scatter       with at most SMALL_TILES tiles every block first scans the
 //                  histogram in shared memory (no grid-wide step in between);
 //                  then each particle's (delta, q) record, packed anchor and
@@ -44,10 +46,19 @@ __device__ __forceinline__ void anchors(const Geom<R> &g, const R (&xi)[3], int 
         grid_anchor<R>(xi[k], g.L[k], g.iL[k], g.ih[k], g.ih_lo[k], g.M[k], g.P, a[k], d[k]);
 }
 
+// tile_of without a division where the tiles are all TE = 8 (or 4) wide:
+// with M = T TE, ((n + 1) T - 1) / M = n / TE for every 0 <= n < M
+template <typename R>
+__device__ __forceinline__ int tile_of_dim(const Geom<R> &g, int d, int n) {
+    if (g.T[d] * g.TE[d] == g.M[d]) {
+        if (g.TE[d] == TILE_B) return n >> 3;
+        if (g.TE[d] == TILE_B / 2) return n >> 2;
+    }
+    return tile_of(n, g.T[d], g.M[d]);
+}
 template <typename R>
 __device__ __forceinline__ int tile_index(const Geom<R> &g, const int (&a)[3]) {
-    return (tile_of(a[0], g.T[0], g.M[0]) * g.T[1] + tile_of(a[1], g.T[1], g.M[1])) * g.T[2] +
-           tile_of(a[2], g.T[2], g.M[2]);
+    return (tile_of_dim(g, 0, a[0]) * g.T[1] + tile_of_dim(g, 1, a[1])) * g.T[2] + tile_of_dim(g, 2, a[2]);
 }
 
 // Block sums of two values: warps reduce in the step type, the per-warp
@@ -81,7 +92,9 @@ __device__ __forceinline__ void clear_mesh(R *__restrict__ rho, int64_t mtot, in
     for (int64_t k = nv * V + t0; k < mtot; k += stride) rho[k] = R(0);
 }
 
-template <typename R>
+// NPT particles per thread: the block takes particles [lb, lb + 1) x
+// NPT blockDim.x, pass u the u-th blockDim.x of them (coalesced).
+template <typename R, int NPT = 1>
 __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const R *__restrict__ x,
                                                   const R *__restrict__ q, const SortBufs &b, int big, int lb,
                                                   int nlb, R *__restrict__ rho_zero = nullptr, int64_t mtot = 0) {
@@ -89,32 +102,37 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
     __shared__ int sh_scan[MAP_THREADS / 32];
     __shared__ bool last;
     if (rho_zero) clear_mesh<R>(rho_zero, mtot, lb, nlb);
-    const int i = lb * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
+    const unsigned int upto = 0xffffffffu >> (31 - lane);  // lanes 0 .. lane
     R qs = R(0), qq = R(0);
-    int tile = -1 - lane;  // a key no other lane or tile has
-    uint32_t packed = 0;
-    if (i < n) {
-        R xi[3], qi;
-        if (!load_particle<R>(x, q, i, xi, qi)) atomicOr(b.err, ERR_NONFINITE);
-        int a[3];
-        R d[3];
-        anchors<R>(g, xi, a, d);
-        tile = tile_index<R>(g, a);
-        packed = pack_anchor(a[0], a[1], a[2]);
-        qs = qi;
-        qq = qi * qi;
-    }
-    // ranks within the tile: one atomic per distinct tile of the warp (the
-    // atoms of a molecule usually share one), handed out in lane order
-    const unsigned int peers = __match_any_sync(0xffffffffu, tile);
-    const int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (i < n && lane == leader) base = atomicAdd(&b.tile_count[tile], __popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (i < n) {
-        b.rank[i] = base + __popc(peers & ((1u << lane) - 1u));
-        b.anchor[i] = packed;
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        const int i = (lb * NPT + u) * (int)blockDim.x + (int)threadIdx.x;
+        int tile = -1 - lane;  // a key no other lane or tile has
+        if (i < n) {
+            R xi[3], qi;
+            if (!load_particle<R>(x, q, i, xi, qi)) atomicOr(b.err, ERR_NONFINITE);
+            int a[3];
+            R d[3];
+            anchors<R>(g, xi, a, d);
+            tile = tile_index<R>(g, a);
+            b.anchor[i] = pack_anchor(a[0], a[1], a[2]);
+            qs += qi;
+            qq += qi * qi;
+        }
+        // ranks within the tile: one atomic per run of lanes with the same
+        // tile (the atoms of a molecule are consecutive and usually share
+        // one), handed out in lane order; lanes with the same tile in
+        // different runs take separate atomics
+        const int prev = __shfl_up_sync(0xffffffffu, tile, 1);
+        const unsigned int starts = __ballot_sync(0xffffffffu, lane == 0 || tile != prev);
+        const int rs = 31 - __clz(starts & upto);                   // first lane of this lane's run
+        const unsigned int after = starts & ~upto;
+        const int re = after ? __ffs(after) - 1 : 32;               // one past its last lane
+        int base = 0;
+        if (i < n && lane == rs) base = atomicAdd(&b.tile_count[tile], re - rs);
+        base = __shfl_sync(0xffffffffu, base, rs);
+        if (i < n) b.rank[i] = base + lane - rs;
     }
     // per-block sums of q and q^2, reduced later off the critical path
     double s1, s2;
@@ -220,11 +238,11 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
     if (threadIdx.x == 0) *b.counter = 0u;
 }
 
-template <typename R>
+template <typename R, int NPT>
 __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, const R *__restrict__ x,
                                                               const R *__restrict__ q, SortBufs b, int big,
                                                               R *__restrict__ rho_zero, int64_t mtot) {
-    particle_map_body<R>(g, n, x, q, b, big, blockIdx.x, gridDim.x, rho_zero, mtot);
+    particle_map_body<R, NPT>(g, n, x, q, b, big, blockIdx.x, gridDim.x, rho_zero, mtot);
 }
 
 // Block-wide exclusive scan of the tile histogram into shared memory
@@ -355,9 +373,14 @@ template void launch_batch_sort<double>(const BatchSys<double> *, const BatchLis
 template <typename R>
 void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const SortBufs &b,
                  cudaStream_t s, R *rho_zero, int64_t mtot) {
+    static_assert(MAP_THREADS == 256, "map_blocks counts blocks of 256 threads");
     const int nb = (int)((n + MAP_THREADS - 1) / MAP_THREADS);
+    const int nbm = map_blocks(n);
     const int big = g.ntiles > SMALL_TILES;
-    k_particle_map<R><<<nb, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, big, rho_zero, mtot);
+    if (map_npt(n) == MAP_NPT_BIG)
+        k_particle_map<R, MAP_NPT_BIG><<<nbm, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, big, rho_zero, mtot);
+    else
+        k_particle_map<R, 1><<<nbm, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, big, rho_zero, mtot);
     launch_pdl(k_scatter<R>, dim3(nb), dim3(MAP_THREADS), 0, s, g, (int)n, x, q, b, big);
 }
 

@@ -478,7 +478,7 @@ int enqueue_t(pppm_plan *p, const Geom<R> &gp, int64_t n, const void *x, const v
     launch_make_rho<R>(g, n, p->sb, (R *)p->rho, p->comp, s, true, !need_mark(1) && !chk);
     if ((rc = check("make_rho"))) return rc;
     const bool ik_spec = (kind == 0) && p->ik;
-    const int mn = (int)((n + 255) / 256);
+    const int mn = map_blocks(n);  // k_particle_map blocks, one q, q^2 partial each
     if constexpr (std::is_same<R, float>::value) {
         if (p->variants & 8) {
             // forward plane pass | x pass with G and the energy partials | inverse plane pass
@@ -615,6 +615,9 @@ void set_variants(pppm_plan *p, int v) {
 // dereference it (pinned host memory mapped into the unified address space,
 // e.g. from cudaHostAlloc or cudaHostRegister), else nullptr.  Asked on every
 // call: a cached answer could outlive the buffer.
+// pppm_compute_host copies mapped inputs in bulk from this many particles on
+constexpr int64_t DIRECT_IN_MAX_N = 1 << 18;
+
 void *device_alias(const void *host) {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
@@ -944,13 +947,18 @@ int pppm_compute_host(pppm_plan *p, int64_t n, const void *x_host, const void *q
     if (!p || n < 0 || n > p->n_max) return PPPM_EINVAL;
     if (!valid_ptr_arg(n, x_host) || !valid_ptr_arg(n, q_host) || !valid_ptr_arg(n, f_host)) return PPPM_EINVAL;
     const size_t rs = p->fp64 ? 8 : 4;
-    // Pinned buffers mapped into the device's address space are read (x, q)
-    // and written (energy/virial) by the kernels themselves over the
-    // host-device link; other buffers go through the plan's device staging.
+    // Pinned buffers mapped into the device's address space may be read (x, q,
+    // see below) and written (energy/virial) by the kernels themselves over
+    // the host-device link; other buffers go through the plan's device staging.
     const void *xa = (n > 0) ? device_alias(x_host) : nullptr;
     const void *qa = (n > 0) ? device_alias(q_host) : nullptr;
     double *eva = (n > 0 && ev_host) ? static_cast<double *>(device_alias(ev_host)) : nullptr;
-    const bool direct_in = xa && qa;
+    // Mapped x and q are read in place by the sort kernels on small systems
+    // (no copy launches); from DIRECT_IN_MAX_N particles on they are copied in
+    // bulk first, since the sort's two passes would read them twice over the
+    // link (measured on GB300, whole call: 32,001 charges 66 us in place vs
+    // 70 us copied; 2,048,001 charges 1.42 ms in place vs 1.34 ms copied).
+    const bool direct_in = xa && qa && n < DIRECT_IN_MAX_N;
     if (n > 0 && !direct_in) {
         CK(cudaMemcpyAsync(p->hx, x_host, 3 * rs * n, cudaMemcpyHostToDevice, p->stream));
         CK(cudaMemcpyAsync(p->hq, q_host, rs * n, cudaMemcpyHostToDevice, p->stream));

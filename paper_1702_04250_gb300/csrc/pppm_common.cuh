@@ -230,6 +230,14 @@ struct SortBufs {
 template <typename R>
 void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const SortBufs &b,
                  cudaStream_t s, R *rho_zero = nullptr, int64_t mtot = 0);
+// Particles per thread of launch_sort's k_particle_map: one, or four on
+// systems large enough to fill the GPU with a quarter of the blocks (fewer
+// blocks: fewer per-block charge sums, FP64 adds and histogram-scan tickets).
+constexpr int MAP_NPT_BIG = 4;
+constexpr int64_t MAP_NPT_MIN_N = 1 << 19;
+inline int map_npt(int64_t n) { return n >= MAP_NPT_MIN_N ? MAP_NPT_BIG : 1; }
+// k_particle_map's blocks (its per-block q, q^2 partials) for n particles
+inline int map_blocks(int64_t n) { return (int)((n + 256LL * map_npt(n) - 1) / (256LL * map_npt(n))); }
 
 template <typename R>
 cudaError_t prepare_make_rho(int P, bool compensated);  // once per process/device, before capture
