@@ -238,7 +238,7 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * function with the energy/virial sums, inverse FFT(s); Sec. 2.1 step 2) runs
  * as three hand-written kernels instead of cuFFT plus two kernels; allowed
  * for PPPM_FP32 / PPPM_FP32C plans whose three mesh edges are each 16, 32, 64
- * or 128, or cubic meshes of edge 48 or 96 (PPPM_EINVAL otherwise).  Results agree with the cuFFT path to FP32
+ * or 128, or cubic meshes of edge 48, 96 or 256 (PPPM_EINVAL otherwise).  Results agree with the cuFFT path to FP32
  * rounding.  Bit 4: mesh tiles of 4 points per edge instead of 8 (eight
  * times the tiles and CTAs of the sort, make_rho and the tile-staged
  * fieldforce, a larger halo share); not with bit 1.  Bit 5: make_rho's brick
@@ -250,7 +250,8 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * only, like bit 0; the ad form runs one particle per thread over units of
  * two z-adjacent tiles).  Default: bit 4 when the mesh has fewer than 304 tiles of 8^3
  * (two per SM), bit 0 for ik plans whose n_max is at least 16 per tile, bit 3
- * where it is allowed, bit 5, bit 6 for PPPM_FP32 / PPPM_FP32C ad plans.
+ * where it is allowed except on 256^3 meshes (cuFFT measured faster there),
+ * bit 5, bit 6 for PPPM_FP32 / PPPM_FP32C ad plans.
  * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a
  * combination the plan does not allow).
  * pppm_autotune times every variant on the caller's inputs (two warm-up and

@@ -585,7 +585,7 @@ bool variant_ok(const pppm_plan *p, int v) {
     if ((v & 64) && (p->fp64 || (v & 1))) return false;  // the persistent fieldforce: FP32 step types, one variant
     if ((v & 16) && (v & 2)) return false;      // one tile shape at a time
     if ((v & 32) && (v & 4)) return false;      // one make_rho brick layout at a time
-    if ((v & 8) && !p->fft_own) return false;  // FP32 plans with power-of-two mesh edges 16..128
+    if ((v & 8) && !p->fft_own) return false;  // FP32 plans on meshes the hand-written solve serves
     if ((v & 4) && !p->comp) return false;  // the four-copy brick is the FP32C accumulator
     if ((v & 2) && !long_tiles_allowed(p->P, p->comp)) return false;
     return !((v & 1) && (v & 2));  // the tile-staged fieldforce brick holds 8^3 tiles only
@@ -771,7 +771,8 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     const size_t rs = p->fp64 ? 8 : 4;
     const int64_t nm = std::max<int64_t>(n_max, 1);
     const int nblk_map = (int)((nm + 255) / 256);
-    const int nblk_green = 152 * 8;
+    // k_green's partials (at most 152 x 8 CTAs), or the hand-written x pass's
+    const int nblk_green = std::max(152 * 8, custom_fft_parts(p->M));
     do {
         if ((rc = dmalloc(p, &p->sb.anchor, 4 * nm))) break;
         if ((rc = dmalloc(p, &p->sb.rank, 4 * nm))) break;
@@ -856,7 +857,7 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     // compile-time brick strides never measured slower (c3 make_rho 688 -> 665 us); the
     // persistent one-particle-per-thread ad fieldforce halves the 2M-charge gather (545 -> 258 us)
     const bool ad_persist = !p->ik && !p->fp64;
-    set_variants(p, ((p->ik && (double)n_max >= 16.0 * nt0) ? 1 : 0) | (p->fft_own ? 8 : 0) | (small_tiles ? 16 : 0) |
+    set_variants(p, ((p->ik && (double)n_max >= 16.0 * nt0) ? 1 : 0) | (p->fft_own && custom_fft_default(p->M) ? 8 : 0) | (small_tiles ? 16 : 0) |
                         32 | (ad_persist ? 64 : 0));
     if ((rc = build_tables_and_green(p))) return fail(rc);
     if ((rc = make_ffts(p))) return fail(rc);

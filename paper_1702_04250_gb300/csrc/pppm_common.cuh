@@ -330,13 +330,16 @@ void launch_energy_final(const GreenBufs &b, const EnergyConsts &ec, int green_n
                          double *ev_user, cudaStream_t s);
 
 // Hand-written Poisson solve for FP32 plans with power-of-two mesh edges
-// 16..128 (k_fft.cu): step 0 forward plane pass (rho -> rho_hat), step 1 x
+// 16..128, or cubic meshes of edge 48, 96 or 256 (k_fft.cu): step 0 forward
+// plane pass (rho -> rho_hat), step 1 x
 // pass with the influence function and the energy/virial partials (in place
 // of launch_green; returns the number of partials, for launch_energy_final),
 // step 2 inverse plane pass (spec -> field).  pdl: the launch directly
 // follows its stream predecessor kernel.
 bool custom_fft_supported(const int M[3]);
 cudaError_t prepare_custom_fft(const int M[3]);  // shared-memory opt-in, before capture
+int custom_fft_parts(const int M[3]);            // energy/virial partials of step 1 (0: unsupported mesh)
+bool custom_fft_default(const int M[3]);         // the plan's default variants include the hand-written solve
 int launch_custom_fft(int step, const Geom<float> &g, bool ik_spec, const float *rho, void *rho_hat, void *spec,
                       float *field, const GreenBufs &b, const EnergyConsts &ec, bool pdl, cudaStream_t s);
 

@@ -1,5 +1,5 @@
 """The hand-written Poisson solve (variant bit 3: FP32 plans, power-of-two
-mesh edges 16..128 or cubic 48^3 / 96^3) vs the oracle's FP64 Poisson solve on the GPU's own mesh
+mesh edges 16..128 or cubic 48^3 / 96^3 / 256^3) vs the oracle's FP64 Poisson solve on the GPU's own mesh
 charge, vs the cuFFT path of the same plan, and end to end vs the oracle.
 
 Mesh-level bar: the field (ik) or potential (ad) within 2e-6 of its largest
@@ -57,6 +57,7 @@ MESHES = [
     ((16, 128, 128), (9.0, 66.0, 70.0)),
     ((48, 48, 48), (30.0, 30.0, 30.0)),   # mixed radix: 12 points per lane
     ((96, 96, 96), (60.0, 60.0, 60.0)),   # mixed radix: 24 points per lane
+    ((256, 256, 256), (160.0, 160.0, 160.0)),  # plane passes on clusters of four CTAs
 ]
 
 

@@ -154,14 +154,20 @@ def test_c3_subsample_fp32c_ad(torch):
     verr = np.linalg.norm(ev[1:7] - ref["virial"]) / np.linalg.norm(ref["virial"])
     print(f"c3 FP32C ad 1% subsample: force {ferr:.2e} energy {eerr:.2e} virial {verr:.2e}")
     assert ferr < 1e-4 and eerr < 1e-4 and verr < 1e-4
-    # the persistent fieldforce (aligned four-chunk brick rows on this 256^3 mesh)
-    for v in (32 | 64, 64):
+    # the default keeps cuFFT on 256^3 (bit 3 measured slower there)
+    assert plan.variant() & 8 == 0
+    # the persistent fieldforce (aligned four-chunk brick rows on this 256^3
+    # mesh), and the hand-written Poisson solve on clusters of CTAs
+    for v in (32 | 64, 64, 32 | 64 | 8):
         plan.set_variant(v)
-        fv, _ = plan.compute(x, q)
+        fv, evv = plan.compute(x, q)
         plan.sync()
         fv = fv.double().cpu().numpy()
+        evv = evv.cpu().numpy()
         ev_err = rel_rms(fv[sub], ref["f"])
         assert ev_err < 1e-4
+        assert abs(evv[0] - ref["energy"]) < 1e-4 * abs(ref["energy"])
+        assert np.linalg.norm(evv[1:7] - ref["virial"]) < 1e-4 * np.linalg.norm(ref["virial"])
         # two FP32C forms, each this close to the oracle, are at most the sum apart
         # (variants differ in the fixed-point scale of the mesh and the summation order)
         assert rel_rms(fv, f) < 2 * max(ferr, ev_err)
