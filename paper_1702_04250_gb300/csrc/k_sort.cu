@@ -4,13 +4,13 @@
 // mesh tile of their anchor, so that make_rho and fieldforce see each tile's
 // particles contiguously.
 //
-// Two kernels:
+// Kernels:
 //  k_particle_map  anchor + tile histogram (atomic ranks, one atomic per run
 //                  of consecutive lanes with the same tile) and per-block
 //                  sums of q and q^2; one particle per thread, or
-//                  MAP_NPT_BIG on large systems.  With more than SMALL_TILES
-//                  tiles the last block to finish turns the histogram into
-//                  tile offsets (exclusive scan).
+//                  MAP_NPT_BIG on large systems.
+//  k_tile_scan     with more than SMALL_TILES tiles: one CTA turns the
+//                  histogram into tile offsets (exclusive scan).
 //  k_scatter       with at most SMALL_TILES tiles every block first scans the
 //                  histogram in shared memory (no grid-wide step in between);
 //                  then each particle's (delta, q) record, packed anchor and
@@ -22,7 +22,6 @@ namespace pppm {
 
 constexpr int MAP_THREADS = 256;
 constexpr int SMALL_TILES = 4096;  // histogram scanned per scatter block up to this many tiles
-constexpr int SCAN_BATCH = 4;      // histogram loads in flight per thread in the last-block scan (keeps 32 registers)
 
 template <typename R>
 __device__ __forceinline__ bool load_particle(const R *__restrict__ x, const R *__restrict__ q,
@@ -96,11 +95,9 @@ __device__ __forceinline__ void clear_mesh(R *__restrict__ rho, int64_t mtot, in
 // NPT blockDim.x, pass u the u-th blockDim.x of them (coalesced).
 template <typename R, int NPT = 1>
 __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const R *__restrict__ x,
-                                                  const R *__restrict__ q, const SortBufs &b, int big, int lb,
-                                                  int nlb, R *__restrict__ rho_zero = nullptr, int64_t mtot = 0) {
+                                                  const R *__restrict__ q, const SortBufs &b, int lb, int nlb,
+                                                  R *__restrict__ rho_zero = nullptr, int64_t mtot = 0) {
     __shared__ double sh[32];
-    __shared__ int sh_scan[MAP_THREADS / 32];
-    __shared__ bool last;
     if (rho_zero) clear_mesh<R>(rho_zero, mtot, lb, nlb);
     const int lane = threadIdx.x & 31;
     const unsigned int upto = 0xffffffffu >> (31 - lane);  // lanes 0 .. lane
@@ -142,107 +139,94 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
         b.blk[2 * lb + 1] = s2;
     }
     pdl_trigger();
-    if (!big) return;  // small tile counts: k_scatter scans the histogram itself
-
-    // the histogram atomics returned their ranks, so they are complete at L2
-    // before this block takes its ticket
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int ticket = atomicAdd(b.counter, 1u);
-        last = (ticket == nlb - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-
-    // ---- last block: exclusive scan of the tile histogram ---------------
-    const int nt = g.ntiles;
-    // each thread owns a chunk of a multiple of 4 tiles (whole chunks load as
-    // int4; the histogram comes from cudaMalloc, 16-byte aligned) and keeps
-    // SCAN_BATCH loads in flight: this block alone runs while the rest of the
-    // step waits, so its time is L2 round trips, not bandwidth
-    const int chunk = ((nt + blockDim.x - 1) / blockDim.x + 3) & ~3;
-    const int lo = min(nt, (int)threadIdx.x * chunk), hi = min(nt, lo + chunk);
-    const bool whole = (hi - lo == chunk);
-    const int4 *c4 = reinterpret_cast<const int4 *>(b.tile_count + lo);
-    const int n4 = chunk / 4;
-    int local = 0;
-    if (whole) {
-        for (int k0 = 0; k0 < n4; k0 += SCAN_BATCH) {
-            int4 v[SCAN_BATCH];
-#pragma unroll
-            for (int u = 0; u < SCAN_BATCH; ++u) v[u] = (k0 + u < n4) ? __ldcg(c4 + k0 + u) : make_int4(0, 0, 0, 0);
-#pragma unroll
-            for (int u = 0; u < SCAN_BATCH; ++u) local += v[u].x + v[u].y + v[u].z + v[u].w;
-        }
-    } else {
-        for (int k0 = lo; k0 < hi; k0 += SCAN_BATCH) {
-            int v[SCAN_BATCH];
-#pragma unroll
-            for (int u = 0; u < SCAN_BATCH; ++u) v[u] = (k0 + u < hi) ? __ldcg(&b.tile_count[k0 + u]) : 0;
-#pragma unroll
-            for (int u = 0; u < SCAN_BATCH; ++u) local += v[u];
-        }
-    }
-    const int w = threadIdx.x >> 5;
-    int incl = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) sh_scan[w] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            const int v = sh_scan[k];
-            sh_scan[k] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
-    int run = sh_scan[w] + incl - local;
-    if (whole) {
-        for (int k0 = 0; k0 < n4; k0 += SCAN_BATCH) {
-            int4 v[SCAN_BATCH];
-#pragma unroll
-            for (int u = 0; u < SCAN_BATCH; ++u) v[u] = (k0 + u < n4) ? __ldcg(c4 + k0 + u) : make_int4(0, 0, 0, 0);
-#pragma unroll
-            for (int u = 0; u < SCAN_BATCH; ++u) {
-                if (k0 + u < n4) {
-                    int *t = b.tile_start + lo + 4 * (k0 + u);
-                    t[0] = run;
-                    t[1] = run + v[u].x;
-                    t[2] = run + v[u].x + v[u].y;
-                    t[3] = run + v[u].x + v[u].y + v[u].z;
-                    run += v[u].x + v[u].y + v[u].z + v[u].w;
-                }
-            }
-        }
-    } else {
-        for (int k0 = lo; k0 < hi; k0 += SCAN_BATCH) {
-            int v[SCAN_BATCH];
-#pragma unroll
-            for (int u = 0; u < SCAN_BATCH; ++u) v[u] = (k0 + u < hi) ? __ldcg(&b.tile_count[k0 + u]) : 0;
-#pragma unroll
-            for (int u = 0; u < SCAN_BATCH; ++u) {
-                if (k0 + u < hi) {
-                    b.tile_start[k0 + u] = run;
-                    run += v[u];
-                }
-            }
-        }
-    }
-    if (hi == nt && lo < hi) b.tile_start[nt] = run;
-    if (threadIdx.x == 0) *b.counter = 0u;
 }
 
 template <typename R, int NPT>
 __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, const R *__restrict__ x,
-                                                              const R *__restrict__ q, SortBufs b, int big,
+                                                              const R *__restrict__ q, SortBufs b,
                                                               R *__restrict__ rho_zero, int64_t mtot) {
-    particle_map_body<R, NPT>(g, n, x, q, b, big, blockIdx.x, gridDim.x, rho_zero, mtot);
+    particle_map_body<R, NPT>(g, n, x, q, b, blockIdx.x, gridDim.x, rho_zero, mtot);
+}
+
+// Exclusive scan of the tile histogram into tile offsets (more than
+// SMALL_TILES tiles): one CTA of SCAN_THREADS threads, each owning a run of
+// a multiple of 4 tiles (int4 loads; the histogram comes from cudaMalloc,
+// 16-byte aligned) with up to SCAN_V of them in flight.  Runs of at most
+// 4 SCAN_V tiles (32,768 tiles and fewer) stay in registers between the sum
+// and the write.  The step waits on this CTA alone, so its time is L2 round
+// trips: one load round trip where the runs fit in registers.
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_V = 8;
+__global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(const int *__restrict__ count, int *__restrict__ start,
+                                                            int nt) {
+    __shared__ int sh_w[SCAN_THREADS / 32];
+    pdl_wait();  // every histogram atomic of particle_map is complete
+    const int per = ((nt + SCAN_THREADS - 1) / SCAN_THREADS + 3) & ~3;
+    const int lo = min(nt, (int)threadIdx.x * per), hi = min(nt, lo + per);
+    const bool whole = (hi - lo == per);
+    const int4 *c4 = reinterpret_cast<const int4 *>(count + lo);
+    const int n4 = per / 4;
+    int4 v[SCAN_V];
+    int local = 0;
+    if (whole) {
+        for (int k0 = 0; k0 < n4; k0 += SCAN_V) {
+#pragma unroll
+            for (int u = 0; u < SCAN_V; ++u) v[u] = (k0 + u < n4) ? __ldcg(c4 + k0 + u) : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < SCAN_V; ++u) local += v[u].x + v[u].y + v[u].z + v[u].w;
+        }
+    } else {
+        for (int k = lo; k < hi; ++k) local += __ldcg(count + k);
+    }
+    pdl_trigger();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sh_w[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int t = sh_w[lane];
+        int it = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, it, o);
+            if (lane >= o) it += y;
+        }
+        sh_w[lane] = it - t;
+    }
+    __syncthreads();
+    int run = sh_w[w] + incl - local;
+    if (whole) {
+        for (int k0 = 0; k0 < n4; k0 += SCAN_V) {
+            if (n4 > SCAN_V) {  // runs longer than the registers hold: load again
+#pragma unroll
+                for (int u = 0; u < SCAN_V; ++u) v[u] = (k0 + u < n4) ? __ldcg(c4 + k0 + u) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < SCAN_V; ++u) {
+                if (k0 + u < n4) {
+                    int4 o;
+                    o.x = run;
+                    o.y = run + v[u].x;
+                    o.z = o.y + v[u].y;
+                    o.w = o.z + v[u].z;
+                    run = o.w + v[u].w;
+                    reinterpret_cast<int4 *>(start + lo)[k0 + u] = o;
+                }
+            }
+        }
+    } else {
+        for (int k = lo; k < hi; ++k) {
+            start[k] = run;
+            run += __ldcg(count + k);
+        }
+    }
+    if (hi == nt && lo < hi) start[nt] = run;
+    if (nt == 0 && threadIdx.x == 0) start[0] = 0;
 }
 
 // Block-wide exclusive scan of the tile histogram into shared memory
@@ -348,7 +332,7 @@ __global__ void __launch_bounds__(MAP_THREADS) k_batch_map(const BatchSys<R> *__
                                                            const R *__restrict__ x, const R *__restrict__ q) {
     const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
     const BatchSys<R> &S = sys[bl.ids[e]];
-    particle_map_body<R>(S.g, S.n, x + 3 * S.poff, q + S.poff, S.sb, 0, blockIdx.x - bl.boff[e],
+    particle_map_body<R>(S.g, S.n, x + 3 * S.poff, q + S.poff, S.sb, blockIdx.x - bl.boff[e],
                          bl.boff[e + 1] - bl.boff[e]);
 }
 template <typename R>
@@ -378,9 +362,11 @@ void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const Sort
     const int nbm = map_blocks(n);
     const int big = g.ntiles > SMALL_TILES;
     if (map_npt(n) == MAP_NPT_BIG)
-        k_particle_map<R, MAP_NPT_BIG><<<nbm, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, big, rho_zero, mtot);
+        k_particle_map<R, MAP_NPT_BIG><<<nbm, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, rho_zero, mtot);
     else
-        k_particle_map<R, 1><<<nbm, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, big, rho_zero, mtot);
+        k_particle_map<R, 1><<<nbm, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, rho_zero, mtot);
+    if (big) launch_pdl(k_tile_scan, dim3(1), dim3(SCAN_THREADS), 0, s, (const int *)b.tile_count, b.tile_start,
+                        g.ntiles);
     launch_pdl(k_scatter<R>, dim3(nb), dim3(MAP_THREADS), 0, s, g, (int)n, x, q, b, big);
 }
 

@@ -52,7 +52,6 @@ struct pppm_plan {
     double *G64 = nullptr;
     void *Gs = nullptr, *kvec = nullptr, *kdiff = nullptr;
     double *green_part = nullptr;
-    unsigned int *counters = nullptr;  // [0] the sort's last-block ticket
     double *ev = nullptr;              // [8]
     double *d_sf = nullptr;            // [6] setup sums
     double sf[6] = {0, 0, 0, 0, 0, 0};
@@ -782,7 +781,6 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         if ((rc = dmalloc(p, &p->sb.rec, 4 * rs * nm))) break;
         if ((rc = dmalloc(p, &p->sb.cell, 4 * nm))) break;
         if ((rc = dmalloc(p, &p->sb.blk, sizeof(double) * 2 * nblk_map))) break;
-        if ((rc = dmalloc(p, &p->counters, 4 * sizeof(unsigned int)))) break;
         if ((rc = dmalloc(p, &p->sb.qsum, 2 * sizeof(double)))) break;
         if ((rc = dmalloc(p, &p->sb.err, 4 * sizeof(int)))) break;
         if ((rc = dmalloc(p, &p->rho, rs * p->Mtot))) break;
@@ -812,7 +810,6 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         release(p);
         return rc;
     }
-    p->sb.counter = p->counters;
     p->gb.G64 = p->G64;
     p->gb.Gs = p->Gs;
     p->gb.kvec = p->kvec;
@@ -831,7 +828,6 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         return code;
     };
     if (cudaMemsetAsync(p->sb.tile_count, 0, 4 * (size_t)p->ntiles_alloc, p->stream) != cudaSuccess ||
-        cudaMemsetAsync(p->counters, 0, 4 * sizeof(unsigned int), p->stream) != cudaSuccess ||
         cudaMemsetAsync(p->sb.err, 0, 4 * sizeof(int), p->stream) != cudaSuccess ||
         cudaMemsetAsync(p->ev, 0, 8 * sizeof(double), p->stream) != cudaSuccess)
         return fail(PPPM_ECUDA);

@@ -211,8 +211,7 @@ int batch_build(pppm_batch *b, const double *box, const int64_t *n, const int *o
         S.sb.cell = (uint32_t *)p;
         if ((rc = bmalloc(b, &p, sizeof(double) * 2 * std::max(S.map_nb, 1)))) return rc;
         S.sb.blk = (double *)p;
-        if ((rc = bmalloc(b, &p, 64))) return rc;  // counter | qsum | ev
-        S.sb.counter = (unsigned int *)p;
+        if ((rc = bmalloc(b, &p, 64))) return rc;  // (16 bytes unused) | qsum | ev
         S.sb.qsum = (double *)((char *)p + 16);
         S.sb.err = b->err;
         // mesh slices

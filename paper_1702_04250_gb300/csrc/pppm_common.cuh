@@ -220,7 +220,6 @@ struct SortBufs {
     void *rec;             // [n] vec4 (delta_x, delta_y, delta_z, q/vcell or q), sorted
     uint32_t *cell;        // [n] packed anchor, sorted
     double *blk;           // [2 * nblk] per-block sum q, sum q^2
-    unsigned int *counter; // [1] last-block ticket
     double *qsum;          // [2] sum q, sum q^2
     int *err;              // [1] device error word
 };

@@ -43,7 +43,7 @@ constexpr size_t OFF_REC = OFF_CELL + align256(4 * NA_MAX_N);
 constexpr size_t OFF_COUNT = OFF_REC + align256(16 * NA_MAX_N);
 constexpr size_t OFF_START = OFF_COUNT + align256(4 * NA_MAX_TILES);
 constexpr size_t OFF_BLK = OFF_START + align256(4 * (NA_MAX_TILES + 1));
-constexpr size_t OFF_MISC = OFF_BLK + align256(16 * NA_MAP_BLOCKS);  // err, counter, qsum
+constexpr size_t OFF_MISC = OFF_BLK + align256(16 * NA_MAP_BLOCKS);  // err, (16 unused), qsum
 constexpr size_t NA_BYTES = OFF_MISC + 256;                          // ~2.1 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
@@ -138,7 +138,6 @@ extern "C" int pppm_make_rho_noalloc(const double box[3], const int mesh[3], int
     b.tile_start = reinterpret_cast<int *>(base + OFF_START);
     b.blk = reinterpret_cast<double *>(base + OFF_BLK);
     b.err = reinterpret_cast<int *>(base + OFF_MISC);
-    b.counter = reinterpret_cast<unsigned int *>(base + OFF_MISC + 16);
     b.qsum = reinterpret_cast<double *>(base + OFF_MISC + 32);
 
     // the array keeps the previous call's contents: clear what must start at zero

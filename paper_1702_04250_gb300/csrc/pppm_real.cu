@@ -308,7 +308,6 @@ int pppm_real_setup(pppm_real **out, const double box[3], int64_t n_max, double 
         if ((rc = rmalloc(r, &r->sb.rec, 4 * rs * nm))) break;
         if ((rc = rmalloc(r, (void **)&r->sb.cell, 4 * nm))) break;
         if ((rc = rmalloc(r, (void **)&r->sb.blk, sizeof(double) * 2 * ((nm + 255) / 256)))) break;
-        if ((rc = rmalloc(r, (void **)&r->sb.counter, 4 * sizeof(unsigned int)))) break;
         if ((rc = rmalloc(r, (void **)&r->sb.qsum, 2 * sizeof(double)))) break;
         if ((rc = rmalloc(r, (void **)&r->sb.err, 4 * sizeof(int)))) break;
         if ((rc = rmalloc(r, &r->pos, 4 * rs * nm))) break;
@@ -316,7 +315,6 @@ int pppm_real_setup(pppm_real **out, const double box[3], int64_t n_max, double 
         if ((rc = rmalloc(r, (void **)&r->ev, 8 * sizeof(double)))) break;
     } while (0);
     if (!rc && (cudaMemsetAsync(r->sb.tile_count, 0, 4 * (size_t)ncell, r->stream) != cudaSuccess ||
-                cudaMemsetAsync(r->sb.counter, 0, 16, r->stream) != cudaSuccess ||
                 cudaMemsetAsync(r->sb.err, 0, 16, r->stream) != cudaSuccess ||
                 cudaMemsetAsync(r->ev, 0, 64, r->stream) != cudaSuccess ||
                 cudaStreamSynchronize(r->stream) != cudaSuccess))
