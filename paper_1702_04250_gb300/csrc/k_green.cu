@@ -19,6 +19,9 @@
 // Per-thread sums are taken in the step's type, combined in FP64 with warp
 // shuffles; one small kernel reduces the per-CTA partials in a fixed order
 // (on a side branch of the step graph, off the critical path).
+#include <algorithm>
+#include <type_traits>
+
 #include "pppm_common.cuh"
 
 namespace pppm {
@@ -308,15 +311,38 @@ void launch_batch_green(const BatchSys<R> *sys, const BatchList &bl, bool ik, cu
 template void launch_batch_green<float>(const BatchSys<float> *, const BatchList &, bool, cudaStream_t);
 template void launch_batch_green<double>(const BatchSys<double> *, const BatchList &, bool, cudaStream_t);
 
+// CTAs of k_green the GPU holds at once (SMs x resident CTAs per SM), per
+// step type, found once per process before any capture.
+static int g_green_wave[2] = {0, 0};
+
+template <typename R>
+cudaError_t prepare_green() {
+    const int t = std::is_same<R, float>::value ? 0 : 1;
+    if (g_green_wave[t] > 0) return cudaSuccess;
+    int dev = 0, sms = 0, a = 0, b = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_green<R, true>, GREEN_THREADS, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_green<R, false>, GREEN_THREADS, 0);
+    if (e == cudaSuccess) g_green_wave[t] = std::max(1, sms * std::min(a, b));
+    return e;
+}
+template cudaError_t prepare_green<float>();
+template cudaError_t prepare_green<double>();
+
 template <typename R>
 int launch_green(const Geom<R> &g, bool ik, const void *rho_hat, void *spec, const GreenBufs &b,
                  const EnergyConsts &ec, cudaStream_t s) {
     const int rows = g.M[0] * g.M[1];
     const int per_cta = GREEN_THREADS / 32;
     // eight z rows per warp before the CTA's energy/virial reduction, but at
-    // least two CTAs per SM while there are rows for them, and at most
+    // least two CTAs per SM while there are rows for them; at most one wave of
+    // resident CTAs (on 256^3, 1,024 CTAs of eight rows a warp took 1.35
+    // waves and left the SMs idle for 12 % of the kernel) and at most
     // 152 x 8 CTAs (the partials buffer)
     int nb = std::max((rows + 8 * per_cta - 1) / (8 * per_cta), std::min(2 * 152, (rows + per_cta - 1) / per_cta));
+    const int wave = g_green_wave[std::is_same<R, float>::value ? 0 : 1];
+    if (wave > 0) nb = std::min(nb, wave);
     nb = std::min(std::max(nb, 1), 152 * 8);
     const auto *rh = reinterpret_cast<const complex_t<R> *>(rho_hat);
     auto *sp = reinterpret_cast<complex_t<R> *>(spec);

@@ -783,6 +783,7 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         if ((rc = dmalloc(p, &p->sb.blk, sizeof(double) * 2 * nblk_map))) break;
         if ((rc = dmalloc(p, &p->sb.qsum, 2 * sizeof(double)))) break;
         if ((rc = dmalloc(p, &p->sb.err, 4 * sizeof(int)))) break;
+        if ((rc = dmalloc(p, &p->sb.queue, 2 * sizeof(unsigned int)))) break;
         if ((rc = dmalloc(p, &p->rho, rs * p->Mtot))) break;
         if ((rc = dmalloc(p, &p->rho_hat, 2 * rs * p->Mhalf))) break;
         if ((rc = dmalloc(p, &p->spec, 2 * rs * p->Mhalf * (p->ik ? 3 : 1)))) break;
@@ -829,6 +830,7 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     };
     if (cudaMemsetAsync(p->sb.tile_count, 0, 4 * (size_t)p->ntiles_alloc, p->stream) != cudaSuccess ||
         cudaMemsetAsync(p->sb.err, 0, 4 * sizeof(int), p->stream) != cudaSuccess ||
+        cudaMemsetAsync(p->sb.queue, 0, 2 * sizeof(unsigned int), p->stream) != cudaSuccess ||
         cudaMemsetAsync(p->ev, 0, 8 * sizeof(double), p->stream) != cudaSuccess)
         return fail(PPPM_ECUDA);
     if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -837,6 +839,7 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
         return fail(PPPM_ECUDA);
     cudaError_t pe = p->fp64 ? prepare_make_rho<double>(order, false) : prepare_make_rho<float>(order, p->comp);
     if (pe == cudaSuccess) pe = p->fp64 ? prepare_fieldforce<double>(order) : prepare_fieldforce<float>(order);
+    if (pe == cudaSuccess) pe = p->fp64 ? prepare_green<double>() : prepare_green<float>();
     p->fft_own = !p->fp64 && custom_fft_supported(p->M);
     if (pe == cudaSuccess && p->fft_own) pe = prepare_custom_fft(p->M);
     if (pe != cudaSuccess) return fail(PPPM_ECUDA);

@@ -221,6 +221,7 @@ struct SortBufs {
     uint32_t *cell;        // [n] packed anchor, sorted
     double *blk;           // [2 * nblk] per-block sum q, sum q^2
     double *qsum;          // [2] sum q, sum q^2
+    unsigned int *queue;   // [2] the persistent ad fieldforce's unit queue: ticket, CTAs done (zero between steps)
     int *err;              // [1] device error word
 };
 
@@ -347,6 +348,8 @@ int launch_custom_fft(int step, const Geom<float> &g, bool ik_spec, const float 
 inline int ff_particles_per_cta(int P) { return 8 * (32 / P); }
 template <typename R>
 cudaError_t prepare_fieldforce(int P);  // shared-memory opt-in of the tile-staged kernels
+template <typename R>
+cudaError_t prepare_green();  // k_green's resident-CTA count (its grid), before capture
 template <typename R>
 void launch_fieldforce(const Geom<R> &g, bool ik, int64_t n, const SortBufs &b, const R *field,
                        R *f, R qC, const double *sf_coeff, cudaStream_t s);
