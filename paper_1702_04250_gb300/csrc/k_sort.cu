@@ -149,44 +149,42 @@ __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, 
 }
 
 // Exclusive scan of the tile histogram into tile offsets (more than
-// SMALL_TILES tiles): one CTA of SCAN_THREADS threads, each owning a run of
-// a multiple of 4 tiles (int4 loads; the histogram comes from cudaMalloc,
-// 16-byte aligned) with up to SCAN_V of them in flight.  Runs of at most
-// 4 SCAN_V tiles (32,768 tiles and fewer) stay in registers between the sum
-// and the write.  The step waits on this CTA alone, so its time is L2 round
-// trips: one load round trip where the runs fit in registers.
+// SMALL_TILES tiles): one CTA of SCAN_THREADS threads.  Warp w owns a
+// contiguous segment of the histogram's int4 groups (the histogram comes
+// from cudaMalloc, 16-byte aligned) and its lanes read it 32 groups at a
+// time, coalesced; up to SCAN_V groups a lane stay in registers between the
+// sum and the write (32,768 tiles and fewer: one load round trip).  The
+// nt % 4 tiles past the last whole group follow all groups.  The step waits
+// on this CTA alone, so its time is L2 round trips.
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_V = 8;
 __global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(const int *__restrict__ count, int *__restrict__ start,
                                                             int nt) {
     __shared__ int sh_w[SCAN_THREADS / 32];
     pdl_wait();  // every histogram atomic of particle_map is complete
-    const int per = ((nt + SCAN_THREADS - 1) / SCAN_THREADS + 3) & ~3;
-    const int lo = min(nt, (int)threadIdx.x * per), hi = min(nt, lo + per);
-    const bool whole = (hi - lo == per);
-    const int4 *c4 = reinterpret_cast<const int4 *>(count + lo);
-    const int n4 = per / 4;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nt4 = nt / 4;
+    const int seg = ((nt4 + SCAN_THREADS / 32 - 1) / (SCAN_THREADS / 32) + 31) & ~31;  // groups per warp
+    const int g0 = min(nt4, w * seg), g1 = min(nt4, g0 + seg);
+    const int4 *c4 = reinterpret_cast<const int4 *>(count);
+    int4 *s4 = reinterpret_cast<int4 *>(start);
+    const bool held = seg <= 32 * SCAN_V;  // the whole segment in registers
     int4 v[SCAN_V];
-    int local = 0;
-    if (whole) {
-        for (int k0 = 0; k0 < n4; k0 += SCAN_V) {
+    // pass 1: the segment's total
+    int wsum = 0;
+    for (int b0 = g0; b0 < g1; b0 += 32 * SCAN_V) {
 #pragma unroll
-            for (int u = 0; u < SCAN_V; ++u) v[u] = (k0 + u < n4) ? __ldcg(c4 + k0 + u) : make_int4(0, 0, 0, 0);
-#pragma unroll
-            for (int u = 0; u < SCAN_V; ++u) local += v[u].x + v[u].y + v[u].z + v[u].w;
+        for (int k = 0; k < SCAN_V; ++k) {
+            const int i = b0 + 32 * k + lane;
+            v[k] = (i < g1) ? __ldcg(c4 + i) : make_int4(0, 0, 0, 0);
         }
-    } else {
-        for (int k = lo; k < hi; ++k) local += __ldcg(count + k);
+#pragma unroll
+        for (int k = 0; k < SCAN_V; ++k) wsum += v[k].x + v[k].y + v[k].z + v[k].w;
     }
     pdl_trigger();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int incl = local;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) sh_w[w] = incl;
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    if (lane == 0) sh_w[w] = wsum;
     __syncthreads();
     if (w == 0) {
         const int t = sh_w[lane];
@@ -196,37 +194,50 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(const int *__restric
             const int y = __shfl_up_sync(0xffffffffu, it, o);
             if (lane >= o) it += y;
         }
-        sh_w[lane] = it - t;
+        sh_w[lane] = it - t;  // exclusive prefix of warp segments
+        if (lane == 31) {
+            // the tail tiles after every whole group, and the total
+            int run = it;
+            for (int k = 4 * nt4; k < nt; ++k) {
+                start[k] = run;
+                run += __ldcg(count + k);
+            }
+            start[nt] = run;
+        }
     }
     __syncthreads();
-    int run = sh_w[w] + incl - local;
-    if (whole) {
-        for (int k0 = 0; k0 < n4; k0 += SCAN_V) {
-            if (n4 > SCAN_V) {  // runs longer than the registers hold: load again
+    // pass 2: group by group in segment order, lanes of a row of 32 groups
+    // scanned with shuffles, the row totals carried
+    int carry = sh_w[w];
+    for (int b0 = g0; b0 < g1; b0 += 32 * SCAN_V) {
+        if (!held) {
 #pragma unroll
-                for (int u = 0; u < SCAN_V; ++u) v[u] = (k0 + u < n4) ? __ldcg(c4 + k0 + u) : make_int4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int u = 0; u < SCAN_V; ++u) {
-                if (k0 + u < n4) {
-                    int4 o;
-                    o.x = run;
-                    o.y = run + v[u].x;
-                    o.z = o.y + v[u].y;
-                    o.w = o.z + v[u].z;
-                    run = o.w + v[u].w;
-                    reinterpret_cast<int4 *>(start + lo)[k0 + u] = o;
-                }
+            for (int k = 0; k < SCAN_V; ++k) {
+                const int i = b0 + 32 * k + lane;
+                v[k] = (i < g1) ? __ldcg(c4 + i) : make_int4(0, 0, 0, 0);
             }
         }
-    } else {
-        for (int k = lo; k < hi; ++k) {
-            start[k] = run;
-            run += __ldcg(count + k);
+#pragma unroll
+        for (int k = 0; k < SCAN_V; ++k) {
+            const int sk = v[k].x + v[k].y + v[k].z + v[k].w;
+            int incl = sk;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int i = b0 + 32 * k + lane;
+            if (i < g1) {
+                int4 o;
+                o.x = carry + incl - sk;
+                o.y = o.x + v[k].x;
+                o.z = o.y + v[k].y;
+                o.w = o.z + v[k].z;
+                s4[i] = o;
+            }
+            carry += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
-    if (hi == nt && lo < hi) start[nt] = run;
-    if (nt == 0 && threadIdx.x == 0) start[0] = 0;
 }
 
 // Block-wide exclusive scan of the tile histogram into shared memory

@@ -103,14 +103,17 @@ def test_anchor_and_sort(c1_fp64_ik):
     np.testing.assert_array_equal(sorted_tiles, owner)
 
 
-def test_sort_many_tiles_ragged_scan(torch):
-    """More tiles than the per-block shared-memory scan holds (17 x 17 x 18 =
-    5,202 tiles of a 136 x 136 x 144 mesh): the last particle_map block scans
-    the histogram, 217 threads with chunks of 24 tiles and one partial chunk
-    of 18.  Exact anchors (FP64), a permutation, tile offsets equal to the
+@pytest.mark.parametrize("box,mesh,ntiles,n", [((40.0, 40.0, 42.0), (136, 136, 144), 5202, 60_001),
+                                              ((78.0, 78.0, 80.0), (264, 264, 272), 37026, 150_001)])
+def test_sort_many_tiles_ragged_scan(torch, box, mesh, ntiles, n):
+    """More tiles than the per-block shared-memory scan holds: the one-CTA
+    scan kernel.  5,202 tiles (17 x 17 x 18): 1,300 whole int4 groups over 21
+    warps, two tail tiles; 37,026 tiles (33 x 33 x 34): segments of 320
+    groups, more than the registers hold (a second load pass), one tail
+    tile.  Exact anchors (FP64), a permutation, tile offsets equal to the
     exclusive scan of the brute-force tile counts, every particle in its tile."""
-    box, mesh, P = (40.0, 40.0, 42.0), (136, 136, 144), 5
-    x, q = uniform_alternating(60_001, box, seed=29)
+    P = 5
+    x, q = uniform_alternating(n, box, seed=29)
     plan, *_ = run(torch, box, mesh, P, 0.6, "ik", "fp64", x, q)
     h = np.array(box) / np.array(mesh)
     u = wrap_positions(x, box) / h
@@ -120,7 +123,7 @@ def test_sort_many_tiles_ragged_scan(torch):
     assert np.array_equal(np.sort(perm), np.arange(len(q)))
     inf = plan.info()
     T = [(m + inf["tile"] - 1) // inf["tile"] for m in mesh]
-    assert T[0] * T[1] * T[2] == 5202
+    assert T[0] * T[1] * T[2] == ntiles
     tile = lambda a, d: ((a + 1) * T[d] - 1) // mesh[d]
     tid = (tile(ref[:, 0], 0) * T[1] + tile(ref[:, 1], 1)) * T[2] + tile(ref[:, 2], 2)
     counts = np.bincount(tid, minlength=T[0] * T[1] * T[2])
