@@ -58,10 +58,14 @@ enum pppm_status {
 enum pppm_diff { PPPM_IK = 0, PPPM_AD = 1 };
 
 /* Arithmetic of the per-step path.  FP64: everything in double.  FP32:
- * spreading, FFTs and interpolation in float.  FP32C: as FP32, with the
- * mesh charge accumulated in compensated (hi + lo) float.  In all three the
- * Green's function, the ad self-force coefficients and the energy/virial
- * reductions are computed in double. */
+ * spreading, FFTs and interpolation in float, the mesh charge of each tile
+ * accumulated exactly in one 32-bit fixed-point word per point (every
+ * contribution rounded once, to 2^-23 of the tile's largest possible one;
+ * two words on tiles whose charge sum would cost that more than two bits).
+ * FP32C: as FP32, with the mesh charge accumulated in two words (hi + lo)
+ * that carry every contribution's exact product to 2^-37 of the largest.
+ * In all three the Green's function, the ad self-force coefficients and the
+ * energy/virial reductions are computed in double. */
 enum pppm_precision { PPPM_FP64 = 0, PPPM_FP32C = 1, PPPM_FP32 = 2 };
 
 /* Ewald splitting parameter from a target relative force accuracy.

@@ -7,6 +7,7 @@
 // the weight of stencil point k as a polynomial in delta = n - u is an exact
 // rational with denominator 2^(P-1) (P-1)!.  We build its numerators in
 // 64-bit integers and divide once, so every coefficient is correctly rounded.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -63,6 +64,22 @@ void stencil_polynomials(int P, double coef[MAXP][MAXP], double dcoef[MAXP][MAXP
             if (l >= 1) dcoef[k][l - 1] = (double)(num[l] * l) / den;
         }
     }
+}
+
+double stencil_weight_max(int P, const double coef[MAXP][MAXP]) {
+    // W_k on its piece: delta in [-1/2, 1/2] (odd P) or [-1, 0] (even P),
+    // sampled on 4,096 steps (the maxima, at the piece's middle or ends, are
+    // samples), with a 1e-4 relative margin
+    const double lo = (P & 1) ? -0.5 : -1.0;
+    double m = 0.0;
+    for (int k = 0; k < P; ++k)
+        for (int i = 0; i <= 4096; ++i) {
+            const double d = lo + i / 4096.0;
+            double w = coef[k][P - 1];
+            for (int l = P - 2; l >= 0; --l) w = w * d + coef[k][l];
+            m = std::max(m, std::fabs(w));
+        }
+    return m * (1.0 + 1e-4);
 }
 
 void spline2p_at_integers(int P, double out[MAXP + 1]) {

@@ -13,9 +13,20 @@
 // warp either way); so does the four-copy brick kernel below.
 //
 // Accumulators (ACC):
-//  ACC_NATIVE  atomics in the step type (FP64, FP32).  On sm_103a shared
+//  ACC_NATIVE  atomics in the step type (FP64).  On sm_103a shared
 //              float/double atomic adds are compare-and-swap loops whose
 //              round trip serialises each thread's updates.
+//  ACC_FIXED1  FP32: one 32-bit integer word per brick point, sum rint(v s)
+//              with s chosen per tile so that a contribution stays below
+//              2^22 and any point's sum below 2^30: one FMA, one integer
+//              add and one native integer atomic a point, exact and
+//              independent of order for the rounded contributions (each
+//              rounded once, to 2^-23 of the tile's largest possible
+//              contribution -- the rounding FP32 float accumulation makes
+//              against a running sum of that size).  A tile whose charge sum
+//              would cost that resolution more than two bits (e.g. tens of
+//              thousands of charges in one tile) takes the two-word ACC_FIXED
+//              accumulation instead; the choice is per tile, CTA-uniform.
 //  ACC_FIXED   FP32C: error-free accumulation in two 32-bit integer words per
 //              brick point, hi = sum rint(v s) and lo = sum of the rounded
 //              16-bit fractions, with the power of two s chosen per tile so
@@ -35,7 +46,7 @@ namespace pppm {
 
 constexpr int RHO_THREADS = 256;
 constexpr int GROUP = 8;
-constexpr int ACC_NATIVE = 0, ACC_FIXED = 1;
+constexpr int ACC_NATIVE = 0, ACC_FIXED = 1, ACC_FIXED1 = 2;
 constexpr int LO_CHUNK = 32768;
 constexpr int ORDER_CHUNK = RHO_THREADS;  // particles per bank-ordered sub-chunk (one per thread)
 constexpr float MAGIC = 12582912.0f;      // 1.5 * 2^23
@@ -54,10 +65,14 @@ __device__ __forceinline__ double absval(double v) { return fabs(v); }
 
 // Power-of-two fixed-point scale for one tile's particles [start, end):
 // s = 2^e with every contribution |q W s / vcell| < 2^21 (W <= 1) and every
-// brick point's sum < 2^30.  Whole CTA; ends with the CTA synchronised.
+// brick point's sum < 2^30.  With one_word non-null (ACC_FIXED1): W <= wmax3
+// (the largest weight product of the stencil), and the one-word scale,
+// contributions below 2^22, where the sum bound costs that at most two bits
+// (*one_word = true), else the two-word scale.
+// Whole CTA; ends with the CTA synchronised.
 template <typename R, int NT = RHO_THREADS>
 __device__ __forceinline__ void fixed_scale(const R *__restrict__ recp, int start, int end, float ivcell,
-                                            float &fs, float &ifs) {
+                                            float &fs, float &ifs, bool *one_word = nullptr, float wmax3 = 1.0f) {
     __shared__ float sh_red[NT / 32];
     __shared__ float sh_max[NT / 32];
     float part = 0.0f, pmax = 0.0f;
@@ -82,12 +97,20 @@ __device__ __forceinline__ void fixed_scale(const R *__restrict__ recp, int star
         bound += sh_red[w];
         bmax = fmaxf(bmax, sh_max[w]);
     }
-    bound = bound * ivcell * 1.0001f + 1e-30f;
-    bmax = bmax * ivcell * 1.0001f + 1e-30f;
+    // one_word: every weight product is at most wmax3 (< 1), which bounds
+    // both the contributions and the point sums more tightly
+    const float wb = one_word ? wmax3 : 1.0f;
+    bound = bound * ivcell * wb * 1.0001f + 1e-30f;
+    bmax = bmax * ivcell * wb * 1.0001f + 1e-30f;
     int es, em;
     frexpf(bound, &es);  // bound < 2^es
     frexpf(bmax, &em);   // largest contribution < 2^em
-    const int e = min(30 - es, 21 - em);
+    int e = min(30 - es, 21 - em);
+    if (one_word) {
+        const int e1 = min(30 - es, 22 - em);
+        *one_word = (22 - em) - e1 <= 2;
+        if (*one_word) e = e1;
+    }
     fs = ldexpf(1.0f, e);
     ifs = ldexpf(1.0f, -e);
 }
@@ -122,7 +145,7 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     // the brick is this CTA's own shared memory: cleared while the sort may
     // still be finishing (ordered before the atomics by the barrier below)
     {
-        const int words = (ACC == ACC_FIXED ? 2 * vol : vol * (int)(sizeof(R) / 4));
+        const int words = (ACC != ACC_NATIVE ? 2 * vol : vol * (int)(sizeof(R) / 4));
         int4 *w4 = reinterpret_cast<int4 *>(smem_raw);
         const int n4 = words >> 2;
         for (int e = threadIdx.x; e < n4; e += blockDim.x) w4[e] = make_int4(0, 0, 0, 0);
@@ -145,7 +168,10 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     // split with the float magic-number trick) and every brick point's sum
     // |sum v s| < 2^30 (so the hi word cannot overflow)
     float fs = 1.0f, ifs = 1.0f;
+    bool one = false;  // ACC_FIXED1: this tile accumulates in one word
     if (ACC == ACC_FIXED) fixed_scale<R>(recp, start, end, (float)g.ivcell, fs, ifs);
+    else if (ACC == ACC_FIXED1)
+        fixed_scale<R>(recp, start, end, (float)g.ivcell, fs, ifs, &one, g.wmax3 > 0.0f ? fminf(g.wmax3, 1.0f) : 1.0f);
     else __syncthreads();  // (fixed_scale ends with one)
 
     // GS lanes serve one particle (32 / GS particles per warp; the lanes past
@@ -161,7 +187,7 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     const int q = lane / GS;                     // this group's place in its warp
     const int warp = threadIdx.x >> 5;
     const int ngrp = (blockDim.x >> 5) * NG;     // particle slots per pass of the CTA
-    const R qscale = (ACC == ACC_FIXED) ? (R)(g.ivcell * (R)fs) : g.ivcell;
+    const R qscale = (ACC != ACC_NATIVE) ? (R)(g.ivcell * (R)fs) : g.ivcell;
     // this lane's polynomial (stencil offset k), held in registers for the CTA
     R ck[P];
 #pragma unroll
@@ -178,7 +204,8 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
             // row0 mod 32 and hand the warp's groups particles a quarter (an
             // NG-th) of the sorted list apart: their runs then start about
             // 32 / NG >= P banks apart.  The accumulation is exact integer
-            // arithmetic (ACC_FIXED), so the order changes no result bit.
+            // arithmetic (ACC_FIXED, ACC_FIXED1), so the order changes no
+            // result bit.
             {
                 int key = 0, rank = 0;
                 if ((int)threadIdx.x < nch) {
@@ -233,7 +260,19 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
                     wxq[t] = __shfl_sync(0xffffffffu, wx, (gbase + t) & 31) * qv;
                     wyk[t] = __shfl_sync(0xffffffffu, wy, (gbase + t) & 31);
                 }
-                if (live) {
+                if (live && ACC == ACC_FIXED1 && one) {
+                    // t = wa wy s rounded to an integer inside the FMA (|t| < 2^22)
+                    const int row = ax * SY + ay * SZ + az + k;
+#pragma unroll
+                    for (int a = 0; a < P; ++a) {
+                        const float fa = (float)(wxq[a] * wz);
+#pragma unroll
+                        for (int c = 0; c < P; ++c) {
+                            const float r1 = __fmaf_rn(fa, (float)wyk[c], MAGIC);
+                            atomicAdd(&acch[row + a * SY + c * SZ], __float_as_int(r1) - MAGIC_BITS);
+                        }
+                    }
+                } else if (live) {
                     const int row = ax * SY + ay * SZ + az + k;
 #pragma unroll
                     for (int a = 0; a < P; ++a) {
@@ -241,7 +280,7 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
 #pragma unroll
                         for (int c = 0; c < P; ++c) {
                             const int e = row + a * SY + c * SZ;
-                            if (ACC == ACC_FIXED) {
+                            if (ACC != ACC_NATIVE) {
                                 // t = wa wy s = hi + lo / 2^16, the product never
                                 // rounded on its own: adding 1.5 * 2^23 inside the
                                 // FMA rounds |t| < 2^22 to an integer held in the
@@ -263,7 +302,7 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
             }
             __syncthreads();  // the list is rewritten by the next sub-chunk
         }
-        if (ACC == ACC_FIXED && cend < end) {  // fold lo into hi before it can overflow
+        if (ACC != ACC_NATIVE && !one && cend < end) {  // fold lo into hi before it can overflow
             for (int e = threadIdx.x; e < vol; e += blockDim.x) {
                 const int l = (int)accl[e];  // signed sum of fractions in [-2^15, 2^15] each
                 acch[e] += l >> 16;          // floor division by 2^16
@@ -294,7 +333,9 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
         for (int ex = 0; ex < Ex; ++ex) {
             const int e = e0 + ex * SY;
             R v;
-            if (ACC == ACC_FIXED) {
+            if (ACC == ACC_FIXED1 && one) {
+                v = (R)((float)acch[e] * ifs);
+            } else if (ACC != ACC_NATIVE) {
                 // normalise in integers (exact), then one FP32 rounding
                 const int l = (int)accl[e];
                 const int h = acch[e] + (l >> 16);
@@ -517,7 +558,7 @@ __global__ void __launch_bounds__(RHO_THREADS) k_batch_make_rho(const BatchSys<R
 template <typename R, int P>
 static size_t brick_bytes(int acc) {
     const int E = TILE_B + P - 1;
-    return (size_t)E * E * E * (acc == ACC_FIXED ? 8 : sizeof(R));
+    return (size_t)E * E * E * (acc != ACC_NATIVE ? 8 : sizeof(R));
 }
 
 template <typename K, typename R>
@@ -542,6 +583,11 @@ static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, int acc, cudaS
     if (acc == ACC_FIXED) {
         if (cs) launch_one(k_make_rho<R, P, ACC_FIXED, true>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
         else launch_one(k_make_rho<R, P, ACC_FIXED>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
+    } else if (acc == ACC_FIXED1) {
+        if constexpr (std::is_same<R, float>::value) {
+            if (cs) launch_one(k_make_rho<R, P, ACC_FIXED1, true>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
+            else launch_one(k_make_rho<R, P, ACC_FIXED1>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
+        }
     } else {
         if (cs) launch_one(k_make_rho<R, P, ACC_NATIVE, true>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
         else launch_one(k_make_rho<R, P, ACC_NATIVE>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
@@ -569,6 +615,18 @@ static cudaError_t prepare_p(int acc) {
                                      bytes);
         return e;
     }
+    if constexpr (std::is_same<R, float>::value) {
+        if (acc == ACC_FIXED1) {
+            e = cudaFuncSetAttribute(k_make_rho<R, P, ACC_FIXED1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_make_rho<R, P, ACC_FIXED1, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_batch_make_rho<R, P, ACC_FIXED1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            return e;
+        }
+    }
     e = cudaFuncSetAttribute(k_make_rho<R, P, ACC_NATIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_batch_make_rho<R, P, ACC_NATIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -585,10 +643,14 @@ static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc,
             return;
         }
     }
-    if (acc == ACC_FIXED)
+    if (acc == ACC_FIXED) {
         k_batch_make_rho<R, P, ACC_FIXED><<<bl.nblocks, RHO_THREADS, bytes, s>>>(sys, bl);
-    else
+    } else if (acc == ACC_FIXED1) {
+        if constexpr (std::is_same<R, float>::value)
+            k_batch_make_rho<R, P, ACC_FIXED1><<<bl.nblocks, RHO_THREADS, bytes, s>>>(sys, bl);
+    } else {
         k_batch_make_rho<R, P, ACC_NATIVE><<<bl.nblocks, RHO_THREADS, bytes, s>>>(sys, bl);
+    }
 }
 
 // The meshes of the systems in the list must have been cleared.
@@ -596,7 +658,7 @@ template <typename R>
 void launch_batch_make_rho(const BatchSys<R> *sys, const BatchList &bl, int P, bool comp, bool copies4,
                            cudaStream_t s) {
     if (bl.nblocks == 0) return;
-    const int acc = comp ? ACC_FIXED : ACC_NATIVE;
+    const int acc = comp ? ACC_FIXED : (std::is_same<R, float>::value ? ACC_FIXED1 : ACC_NATIVE);
     switch (P) {
         case 2: launch_batch_p<R, 2>(sys, bl, acc, copies4, s); break;
         case 3: launch_batch_p<R, 3>(sys, bl, acc, copies4, s); break;
@@ -613,7 +675,7 @@ template void launch_batch_make_rho<double>(const BatchSys<double> *, const Batc
 
 template <typename R>
 cudaError_t prepare_make_rho(int P, bool comp) {
-    const int acc = comp ? ACC_FIXED : ACC_NATIVE;
+    const int acc = comp ? ACC_FIXED : (std::is_same<R, float>::value ? ACC_FIXED1 : ACC_NATIVE);
     switch (P) {
         case 2: return prepare_p<R, 2>(acc);
         case 3: return prepare_p<R, 3>(acc);
@@ -633,7 +695,7 @@ void launch_make_rho(const Geom<R> &g, int64_t n, const SortBufs &b, R *rho, boo
         pdl = false;  // the memset now sits between the sort and this launch
     }
     if (n == 0) return;
-    const int acc = comp ? ACC_FIXED : ACC_NATIVE;
+    const int acc = comp ? ACC_FIXED : (std::is_same<R, float>::value ? ACC_FIXED1 : ACC_NATIVE);
     switch (g.P) {
         case 2: launch_p<R, 2>(g, b, rho, acc, s, pdl); break;
         case 3: launch_p<R, 3>(g, b, rho, acc, s, pdl); break;

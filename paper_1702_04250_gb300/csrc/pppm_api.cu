@@ -151,6 +151,8 @@ void fill_geom(pppm_plan *p, Geom<R> &g, const double coef[MAXP][MAXP], const do
             g.coef[k][l] = (R)coef[k][l];
             g.dcoef[k][l] = (R)dcoef[k][l];
         }
+    const double wm = stencil_weight_max(p->P, coef);
+    g.wmax3 = (float)(wm * wm * wm * (1.0 + 1e-6));
 }
 
 void release(pppm_plan *p) {

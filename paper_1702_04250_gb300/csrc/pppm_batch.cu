@@ -135,6 +135,8 @@ void fill_geom_b(Geom<R> &g, const double box[3], const int M[3], int P, bool co
             g.coef[k][l] = (R)coef[k][l];
             g.dcoef[k][l] = (R)dcoef[k][l];
         }
+    const double wm = stencil_weight_max(P, coef);
+    g.wmax3 = (float)(wm * wm * wm * (1.0 + 1e-6));
 }
 
 // Builds every per-system descriptor, the mesh classes and the launch lists.

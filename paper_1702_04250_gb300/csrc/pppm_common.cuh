@@ -60,6 +60,7 @@ struct Geom {
     int lut_bins;         // coefficient table entries (0: exact polynomials), see pppm_set_lut
     int launch_flags;     // host side: LF_* launch options of this step
     int planar_stride;    // ik field layout: 0 interleaved (Ex,Ey,Ez,pad); > 0 three planes this far apart
+    float wmax3;          // bound on a stencil point's weight product wx wy wz (0: use 1)
 };
 
 // Geom::launch_flags: green / fieldforce may use a programmatic dependent
@@ -201,6 +202,8 @@ __device__ __forceinline__ R warp_sum_t(R v) {
 // ---------------------------------------------------------------------------
 // coef[k][l], dcoef[k][l] of the order-P stencil in delta (see top comment).
 void stencil_polynomials(int P, double coef[MAXP][MAXP], double dcoef[MAXP][MAXP]);
+// An upper bound on every stencil weight W_k(delta) of the polynomials above.
+double stencil_weight_max(int P, const double coef[MAXP][MAXP]);
 // M_{2P}(g) for g = 0..P (values at the integers of the order-2P B-spline).
 void spline2p_at_integers(int P, double out[MAXP + 1]);
 // Grid-unit wavenumber of mesh index m (Nyquist index taken as -M/2).

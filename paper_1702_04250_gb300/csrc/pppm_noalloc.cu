@@ -127,6 +127,10 @@ extern "C" int pppm_make_rho_noalloc(const double box[3], const int mesh[3], int
             g.coef[k][l] = (float)coef[k][l];
             g.dcoef[k][l] = (float)dcoef[k][l];
         }
+    {
+        const double wm = stencil_weight_max(order, coef);
+        g.wmax3 = (float)(wm * wm * wm * (1.0 + 1e-6));
+    }
 
     SortBufs b{};
     b.anchor = reinterpret_cast<uint32_t *>(base + OFF_ANCHOR);
