@@ -5,8 +5,9 @@ forward FFT, influence-function multiply with energy/virial, inverse FFT,
 fieldforce with the ad self-force epilogue) over the largest single-GPU
 workload: 682,667 rigid 3-site water-like molecules (2,048,001 charges) in a
 272 A periodic cube, mesh 256^3, order 7, ad differentiation, FP32 spreading /
-FFT / interpolation with compensated mesh accumulation and FP64 setup and
-reductions.  Inputs are resident in HBM (and larger than L2; the L2 is also
+FFT / interpolation (the mesh charge summed exactly in one fixed-point word
+per point) with FP64 setup and reductions: the fastest form that meets the
+metric's 1e-4 force error.  Inputs are resident in HBM (and larger than L2; the L2 is also
 flushed with a 256 MiB write before every timed step); each step is one
 captured CUDA graph timed with CUDA events on the plan's stream.
 
@@ -17,7 +18,8 @@ fieldforce (event-timed inside the timed region, algorithmic bytes over the
 measured HBM copy peak); the end-to-end rate through the host-buffer C-ABI
 call; the FP64 oracle timed on the host cores (one core, and independent
 replicas on all cores).  More on rank 0 under "extra" (skipped with
---no-extra): the 32,001-charge water-like system (64^3, P=5; ik and ad,
+--no-extra): the same workload in FP32C (two-word compensated mesh
+accumulation) and in the plain FP64 form; the 32,001-charge water-like system (64^3, P=5; ik and ad,
 FP32C and FP64), the batch of 256 independent systems, the real-space erfc
 sum, the mesh chosen for a target accuracy, and the differentiable energy of
 the 99,999-charge system.
@@ -45,6 +47,9 @@ sys.path.insert(0, ROOT)
 L2_FLUSH_BYTES = 256 << 20
 WORKLOAD = "c3"
 HEADLINE_MODE = "ad"
+# the fastest precision that meets the metric's 1e-4 force error on c3: FP32
+# (one fixed-point word per mesh point); FP32C (two words) is timed beside it
+HEADLINE_PREC = "fp32"
 SUBSAMPLE = 100  # forces compared with the oracle (and oracle forces timed) on every 100th charge
 
 
@@ -56,14 +61,15 @@ def workload(name=WORKLOAD):
 
 def metric_name():
     return ("PPPM k-space steps/sec at 1e-4 rel force error vs FP64 form (water-like 2,048,001 charges, "
-            "272 A cube, 256^3, P=7, ad, FP32C)")
+            "272 A cube, 256^3, P=7, ad, FP32)")
 
 
 def config_dict(w, extra=None):
     d = {"workload": "c3 water-like: 682,667 rigid 3-site molecules (2,048,001 charges), 272 A cube, mesh 256^3, "
-                     "order 7, ad, FP32C, g_ewald for 1e-4 at r_C = 10 A",
+                     "order 7, ad, FP32 (spread, FFT, interpolate; fixed-point mesh accumulation; FP64 setup "
+                     "and reductions), g_ewald for 1e-4 at r_C = 10 A",
          "n_charges": int(w.n), "mesh": list(w.mesh), "order": int(w.order), "diff": HEADLINE_MODE,
-         "precision": "fp32c",
+         "precision": HEADLINE_PREC,
          "l2": "inputs larger than L2 (mesh 64 MiB + particles 80 MiB); also flushed (256 MiB write) before "
                "every timed step", "graph": True}
     if extra:
@@ -245,10 +251,11 @@ SHARED_ATOMIC_OPS_PER_CLK_SM = 25.9
 N_SM = 152
 
 
-def onchip_make_rho(n, P, ms, sm_mhz):
+def onchip_make_rho(n, P, ms, sm_mhz, words=2):
     """make_rho against its on-chip bound: FP32C adds two int32 words per
-    stencil point in shared memory (2 N P^3 atomics per launch)."""
-    ops = 2.0 * n * P ** 3
+    stencil point in shared memory (2 N P^3 atomics per launch), FP32 one
+    (one-word tiles; words = 1)."""
+    ops = float(words) * n * P ** 3
     mhz = sm_mhz or 2070.0
     peak = SHARED_ATOMIC_OPS_PER_CLK_SM * N_SM * mhz * 1e6 / 1e9
     ach = ops / (ms * 1e-3) / 1e9
@@ -263,7 +270,7 @@ def alg_bytes(stage, n, mesh, ik):
     """Algorithmic (minimum) bytes per launch of a stage, FP32 step type, as
     the hot-path scope table counts them: particles once, mesh once.
       sort       16N read + 16N write + 8N (cell key, permutation)
-      make_rho   16N (x, q) + 8M (compensated hi + lo mesh write)
+      make_rho   16N (x, q) + 8M (the mesh term of the scope table)
       green      4M (rho_hat, M/2 complex) + 2M (G, real half spectrum) + 4M per output spectrum
       fieldforce ik: 16M (float4 field) + 32N (x, q in; F out); ad: 4M + 32N"""
     M = int(mesh[0]) * int(mesh[1]) * int(mesh[2])
@@ -349,10 +356,12 @@ def result_errors(f, ev, f_ref, ev_ref):
             "virial_rel": float(np.linalg.norm(ev[1:7] - ev_ref[1:7]) / np.linalg.norm(ev_ref[1:7]))}
 
 
-def variant_tag(stage, variant, ik):
-    """The kernel a plan variant mask runs for a stage, as dram_traffic.txt tags it."""
+def variant_tag(stage, variant, ik, prec="fp32c"):
+    """The kernel a plan variant mask (and precision) runs for a stage, as
+    dram_traffic.txt tags it."""
     if stage == "make_rho":
-        return "copies4" if variant & 4 else ("cs" if variant & 32 else "tile")
+        t = "copies4" if variant & 4 else ("cs" if variant & 32 else "tile")
+        return t if prec == "fp32c" else f"{t}-{prec}"  # FP32: the one-word accumulator
     if stage == "fieldforce":
         if variant & 64:
             return "ik-persist" if ik else "ad-thread"
@@ -360,10 +369,10 @@ def variant_tag(stage, variant, ik):
     return "-"
 
 
-def kernel_roofline(stage, w, ms, ik, peak, peak_kind, traffic_src, variant):
+def kernel_roofline(stage, w, ms, ik, peak, peak_kind, traffic_src, variant, prec="fp32c"):
     nbytes = alg_bytes(stage, w.n, w.mesh, ik)
     achieved = nbytes / (ms * 1e-3) / 1e9
-    tr = known_traffic(stage, w.name, traffic_src, variant_tag(stage, variant, ik))
+    tr = known_traffic(stage, w.name, traffic_src, variant_tag(stage, variant, ik, prec))
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": tr["bytes"] if tr else None,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
@@ -387,7 +396,7 @@ def gpu_arm(args, rank, world):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     ik = HEADLINE_MODE == "ik"
 
-    plan = make_plan(w, g, HEADLINE_MODE, "fp32c")
+    plan = make_plan(w, g, HEADLINE_MODE, HEADLINE_PREC)
     f = torch.empty((w.n, 3), dtype=torch.float32, device="cuda")
     ev = torch.zeros(8, dtype=torch.float64, device="cuda")
     # the plan's default kernel variants (the autotuner picks the same mask on this
@@ -396,14 +405,14 @@ def gpu_arm(args, rank, world):
     variant = plan.variant()
     plan.compute(x32, q32, f, ev)
     plan.sync()
-    f_fp32c = f.double().cpu().numpy()
-    ev_fp32c = ev[:7].cpu().numpy()
+    f_head = f.double().cpu().numpy()
+    ev_head = ev[:7].cpu().numpy()
 
     # accuracy of this form against the FP64 form on the same GPU and inputs
     p64 = make_plan(w, g, HEADLINE_MODE, "fp64", graph=False)
     f64, ev64 = p64.compute(x32.double(), q32.double())
     p64.sync()
-    err_fp64 = result_errors(f_fp32c, ev_fp32c, f64.cpu().numpy(), ev64.cpu().numpy())
+    err_fp64 = result_errors(f_head, ev_head, f64.cpu().numpy(), ev64.cpu().numpy())
     del f64
     p64.close()
     torch.cuda.empty_cache()
@@ -440,7 +449,8 @@ def gpu_arm(args, rank, world):
     peak, peak_kind = measured_peak()
     src = "paper_1702_04250_gb300/csrc/"
     kernels = {
-        "make_rho": kernel_roofline("make_rho", w, stages["make_rho"], ik, peak, peak_kind, src + "k_rho.cu", variant),
+        "make_rho": kernel_roofline("make_rho", w, stages["make_rho"], ik, peak, peak_kind, src + "k_rho.cu", variant,
+                                    HEADLINE_PREC),
         "fieldforce": kernel_roofline("fieldforce", w, stages["fieldforce"], ik, peak, peak_kind,
                                       src + "k_force.cu", variant),
     }
@@ -464,7 +474,7 @@ def gpu_arm(args, rank, world):
     for _ in range(ne):
         plan.compute_host_into(w.n, xh.data_ptr(), qh.data_ptr(), fh.data_ptr(), evh.data_ptr())
     e2e_s = (time.perf_counter() - t0) / ne
-    e2e_err = rel_rms(fh.double().numpy(), f_fp32c)
+    e2e_err = rel_rms(fh.double().numpy(), f_head)
     plan.close()
 
     # particle_map, scatter, make_rho, energy_final, fieldforce, and either green (the 3-D
@@ -473,7 +483,8 @@ def gpu_arm(args, rank, world):
     line = {
         "metric": metric_name(), "value": round(steps_per_s, 3), "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32c", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if HEADLINE_PREC == "fp32" else "f32c", "data": "synthetic",
         "config": config_dict(w, {"parallelism": "replicas" if world > 1 else "single",
                                   "fieldforce_variant": "tile-staged" if variant & 1 else "per-particle L1",
                                   "poisson_solve": "hand-written FFT" if own_fft else "cuFFT",
@@ -484,19 +495,62 @@ def gpu_arm(args, rank, world):
         "ms_per_step_without_kernel_events": round(ms_plain, 5),
         "steps_per_s_without_kernel_events": round(world * 1000.0 / ms_plain, 3),
         "roofline": roof,
-        "onchip": onchip_make_rho(w.n, w.order, stages["make_rho"], clocks_rep.get("sm_mhz")),
+        "onchip": onchip_make_rho(w.n, w.order, stages["make_rho"], clocks_rep.get("sm_mhz"),
+                                  1 if HEADLINE_PREC == "fp32" else 2),
         "e2e": {"value": round(world / e2e_s, 3), "unit": "steps/s", "h2d_bytes_per_step": int(16 * w.n),
                 "d2h_bytes_per_step": int(12 * w.n + 56), "call": "pppm_compute_host, pinned host buffers",
                 "force_rel_rms_vs_device_call": e2e_err},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks_rep,
     }
-    return line, (f_fp32c, ev_fp32c, g)
+    return line, (f_head, ev_head, g)
 
 
 # ---------------------------------------------------------------------------
 # extra workloads (rank 0)
 # ---------------------------------------------------------------------------
+def c3_fp32c_leg(torch, flush, steps=40):
+    """The headline workload in FP32C (two-word compensated mesh
+    accumulation) and in the plain FP64 form: steps/s, the make_rho and
+    fieldforce averages, and FP32C's errors against the FP64 form."""
+    from paper_1702_04250_gb300 import pppm
+
+    w = workload()
+    g = pppm.estimate_g(w.rel_acc, w.r_cut, w.n, float(np.sum(w.q ** 2)), w.box)
+    x32 = torch.tensor(w.x, dtype=torch.float32, device="cuda")
+    q32 = torch.tensor(w.q, dtype=torch.float32, device="cuda")
+    plan = make_plan(w, g, HEADLINE_MODE, "fp32c")
+    f = torch.empty((w.n, 3), dtype=torch.float32, device="cuda")
+    ev = torch.zeros(8, dtype=torch.float64, device="cuda")
+    plan.compute(x32, q32, f, ev)
+    plan.sync()
+    fc, evc = f.double().cpu().numpy(), ev[:7].cpu().numpy()
+    t_ms, stages = time_steps(torch, plan, x32, q32, f, ev, steps, 3, flush, profile=["make_rho", "fieldforce"],
+                              every=2, sync_ranks=False)
+    variant = plan.variant()
+    plan.close()
+    p64 = make_plan(w, g, HEADLINE_MODE, "fp64")
+    x64, q64 = x32.double(), q32.double()
+    f64, ev64 = p64.compute(x64, q64)
+    p64.sync()
+    err = result_errors(fc, evc, f64.cpu().numpy(), ev64.cpu().numpy())
+    f64b = torch.empty_like(f64)
+    t64, _ = time_steps(torch, p64, x64, q64, f64b, ev, max(10, steps // 4), 3, flush, sync_ranks=False)
+    p64.close()
+    del f64, f64b, x64, q64
+    torch.cuda.empty_cache()
+    ms = t_ms / steps
+    ms64 = t64 / max(10, steps // 4)
+    return {"workload": "the headline workload, FP32C: two 32-bit words per mesh point (exact sums of the exact "
+                        "products to 2^-37 of the largest)",
+            "steps_per_s": round(1000.0 / ms, 2), "ms_per_step": round(ms, 5),
+            "make_rho_ms": round(stages["make_rho"], 5), "fieldforce_ms": round(stages["fieldforce"], 5),
+            "error_vs_fp64_form": err, "variant_mask": int(variant),
+            "fp64_form": {"steps_per_s": round(1000.0 / ms64, 2), "ms_per_step": round(ms64, 4)},
+            "timing": f"{steps} graph steps, L2 flushed before each; every 2nd with events around make_rho and "
+                      f"fieldforce (FP64: {max(10, steps // 4)} steps, no events)"}
+
+
 def c2_leg(torch, flush, steps=400):
     """The 32,001-charge water-like system (68 A cube, 64^3, P=5): ik FP32C
     (autotuned; the hand-written Poisson solve), with its own roofline, the
@@ -901,7 +955,7 @@ def oracle_all_cores(w, o, stride, max_replicas=None):
 
 def cpu_baseline_leg(w, gpu_out=None, all_cores=True):
     """The FP64 oracle on the host cores: one core, then (all_cores) one
-    replica per core.  With gpu_out = (FP32C forces, energy/virial), also the
+    replica per core.  With gpu_out = (headline forces, energy/virial), also the
     error of the GPU results against the oracle (forces on the subsample)."""
     o = oracle_setup(w)
     x = w.x.astype(np.float32).astype(np.float64)  # the GPU's float32 inputs, exactly (reading R15)
@@ -923,8 +977,8 @@ def cpu_baseline_leg(w, gpu_out=None, all_cores=True):
                                           f"core up to half the free memory at 13 GiB each), each one sampled "
                                           f"step as above, run at the same time; value = sum of their rates"}
     if gpu_out is not None:
-        f32c, ev32c = gpu_out[0], gpu_out[1]
-        res["gpu_error_vs_oracle"] = dict(result_errors(f32c[::SUBSAMPLE], ev32c, out["f_sub"], out["ev"]),
+        fh, evh = gpu_out[0], gpu_out[1]
+        res["gpu_error_vs_oracle"] = dict(result_errors(fh[::SUBSAMPLE], evh, out["f_sub"], out["ev"]),
                                           forces_on=f"every {SUBSAMPLE}th charge ({out['f_sub'].shape[0]:,})")
     return res
 
@@ -985,7 +1039,8 @@ def main():
         import torch
 
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-        line["extra"] = {"c2": c2_leg(torch, flush), "batch": batch_leg(torch, flush),
+        line["extra"] = {"c3_fp32c_and_fp64": c3_fp32c_leg(torch, flush), "c2": c2_leg(torch, flush),
+                         "batch": batch_leg(torch, flush),
                          "real_space": real_leg(torch, flush), "mesh_choice": mesh_leg(torch, flush),
                          "autograd_c5": autograd_leg(torch, flush)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

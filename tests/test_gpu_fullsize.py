@@ -171,3 +171,16 @@ def test_c3_subsample_fp32c_ad(torch):
         # two FP32C forms, each this close to the oracle, are at most the sum apart
         # (variants differ in the fixed-point scale of the mesh and the summation order)
         assert rel_rms(fv, f) < 2 * max(ferr, ev_err)
+    plan.close()
+    # FP32: the one-word fixed-point mesh accumulation
+    p32 = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode="ad", precision="fp32", qqrd2e=w.qqrd2e)
+    f32, ev32 = p32.compute(x, q)
+    p32.sync()
+    f32 = f32.double().cpu().numpy()
+    ev32 = ev32.cpu().numpy()
+    e32 = rel_rms(f32[sub], ref["f"])
+    print(f"c3 FP32 ad 1% subsample: force {e32:.2e}")
+    assert e32 < 1e-4
+    assert abs(ev32[0] - ref["energy"]) < 1e-4 * abs(ref["energy"])
+    assert np.linalg.norm(ev32[1:7] - ref["virial"]) < 1e-4 * np.linalg.norm(ref["virial"])
+    p32.close()
