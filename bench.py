@@ -475,11 +475,13 @@ def gpu_arm(args, rank, world):
         plan.compute_host_into(w.n, xh.data_ptr(), qh.data_ptr(), fh.data_ptr(), evh.data_ptr())
     e2e_s = (time.perf_counter() - t0) / ne
     e2e_err = rel_rms(fh.double().numpy(), f_head)
+    ntiles = plan.info()["ntiles"]
     plan.close()
 
     # particle_map, scatter, make_rho, energy_final, fieldforce, and either green (the 3-D
-    # transforms in cuFFT, not ours) or the three hand-written Poisson-solve kernels
-    launches_per_step = 8 if own_fft else 6
+    # transforms in cuFFT, not ours) or the three hand-written Poisson-solve kernels; the
+    # tile scan between particle_map and scatter above 4,096 tiles
+    launches_per_step = (8 if own_fft else 6) + (1 if ntiles > 4096 else 0)
     line = {
         "metric": metric_name(), "value": round(steps_per_s, 3), "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
