@@ -73,8 +73,10 @@ __device__ __forceinline__ double absval(double v) { return fabs(v); }
 template <typename R, int NT = RHO_THREADS>
 __device__ __forceinline__ void fixed_scale(const R *__restrict__ recp, int start, int end, float ivcell,
                                             float &fs, float &ifs, bool *one_word = nullptr, float wmax3 = 1.0f) {
+    static_assert(NT / 32 <= 32, "one warp combines the warps' partials");
     __shared__ float sh_red[NT / 32];
     __shared__ float sh_max[NT / 32];
+    __shared__ int sh_e[2];  // the scale exponent, the one-word choice
     float part = 0.0f, pmax = 0.0f;
     for (int j = start + threadIdx.x; j < end; j += blockDim.x) {
         const float a = absval((float)reinterpret_cast<const vec4_t<R> *>(recp)[j].w);
@@ -86,33 +88,73 @@ __device__ __forceinline__ void fixed_scale(const R *__restrict__ recp, int star
         part += __shfl_xor_sync(0xffffffffu, part, o);
         pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
     }
-    if ((threadIdx.x & 31) == 0) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
         sh_red[threadIdx.x >> 5] = part;
         sh_max[threadIdx.x >> 5] = pmax;
     }
     __syncthreads();
-    float bound = 0.0f, bmax = 0.0f;
+    if (threadIdx.x < 32) {  // warp 0 combines the partials and picks the scale
+        float bound = (lane < NT / 32) ? sh_red[lane] : 0.0f, bmax = (lane < NT / 32) ? sh_max[lane] : 0.0f;
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) {
-        bound += sh_red[w];
-        bmax = fmaxf(bmax, sh_max[w]);
+        for (int o = 16; o > 0; o >>= 1) {
+            bound += __shfl_xor_sync(0xffffffffu, bound, o);
+            bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        }
+        if (lane == 0) {
+            // one_word: every weight product is at most wmax3 (< 1), which
+            // bounds both the contributions and the point sums more tightly
+            const float wb = one_word ? wmax3 : 1.0f;
+            bound = bound * ivcell * wb * 1.0001f + 1e-30f;
+            bmax = bmax * ivcell * wb * 1.0001f + 1e-30f;
+            int es, em;
+            frexpf(bound, &es);  // bound < 2^es
+            frexpf(bmax, &em);   // largest contribution < 2^em
+            int e = min(30 - es, 21 - em), one = 0;
+            if (one_word) {
+                const int e1 = min(30 - es, 22 - em);
+                one = (22 - em) - e1 <= 2;
+                if (one) e = e1;
+            }
+            sh_e[0] = e;
+            sh_e[1] = one;
+        }
     }
-    // one_word: every weight product is at most wmax3 (< 1), which bounds
-    // both the contributions and the point sums more tightly
-    const float wb = one_word ? wmax3 : 1.0f;
-    bound = bound * ivcell * wb * 1.0001f + 1e-30f;
-    bmax = bmax * ivcell * wb * 1.0001f + 1e-30f;
-    int es, em;
-    frexpf(bound, &es);  // bound < 2^es
-    frexpf(bmax, &em);   // largest contribution < 2^em
-    int e = min(30 - es, 21 - em);
-    if (one_word) {
-        const int e1 = min(30 - es, 22 - em);
-        *one_word = (22 - em) - e1 <= 2;
-        if (*one_word) e = e1;
+    __syncthreads();
+    const int e = sh_e[0];
+    if (one_word) *one_word = sh_e[1] != 0;
+    fs = __int_as_float((127 + e) << 23);   // 2^e, |e| < 127
+    ifs = __int_as_float((127 - e) << 23);  // 2^-e
+}
+
+// a / b for 0 <= a and 1 <= b: a shift when b is a power of two (the usual
+// tile counts), else the integer division.  CTA-uniform operands.
+__device__ __forceinline__ int div_tiles(int a, int b) { return (b & (b - 1)) == 0 ? a >> (__ffs(b) - 1) : a / b; }
+
+// Origin and brick extents (tile plus P - 1 halo) of a tile, as tile_of /
+// tile_origin define them: multiplications where the dimension's tiles are
+// all TE wide (M = T TE), the divisions of tile_origin otherwise.
+template <typename R, int P>
+__device__ __forceinline__ void tile_extent(const Geom<R> &g, int tile, int &ox, int &oy, int &oz, int &Ex, int &Ey,
+                                            int &Ez) {
+    const int r1 = div_tiles(tile, g.T[2]);
+    const int tz = tile - r1 * g.T[2];
+    const int tx = div_tiles(r1, g.T[1]);
+    const int ty = r1 - tx * g.T[1];
+    const int t[3] = {tx, ty, tz};
+    int o[3], e[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (g.T[d] * g.TE[d] == g.M[d]) {
+            o[d] = t[d] * g.TE[d];
+            e[d] = g.TE[d] + P - 1;
+        } else {
+            o[d] = tile_origin(t[d], g.T[d], g.M[d]);
+            e[d] = tile_origin(t[d] + 1, g.T[d], g.M[d]) - o[d] + P - 1;
+        }
     }
-    fs = ldexpf(1.0f, e);
-    ifs = ldexpf(1.0f, -e);
+    ox = o[0]; oy = o[1]; oz = o[2];
+    Ex = e[0]; Ey = e[1]; Ez = e[2];
 }
 
 // CS: the brick's strides are those of the largest tile (TILE_B + P - 1 per
@@ -123,15 +165,8 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
                                               int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
-    const int tz = tile % g.T[2];
-    const int ty = (tile / g.T[2]) % g.T[1];
-    const int tx = tile / (g.T[2] * g.T[1]);
-    const int ox = tile_origin(tx, g.T[0], g.M[0]);
-    const int oy = tile_origin(ty, g.T[1], g.M[1]);
-    const int oz = tile_origin(tz, g.T[2], g.M[2]);
-    const int Ex = tile_origin(tx + 1, g.T[0], g.M[0]) - ox + P - 1;
-    const int Ey = tile_origin(ty + 1, g.T[1], g.M[1]) - oy + P - 1;
-    const int Ez = tile_origin(tz + 1, g.T[2], g.M[2]) - oz + P - 1;
+    int ox, oy, oz, Ex, Ey, Ez;
+    tile_extent<R, P>(g, tile, ox, oy, oz, Ex, Ey, Ez);
     constexpr int EB = TILE_B + P - 1;          // widest brick edge
     const int SZ = CS ? EB : Ez;                // brick row (z) stride
     const int SY = CS ? EB * EB : Ey * Ez;      // brick plane stride
