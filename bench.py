@@ -360,7 +360,7 @@ def variant_tag(stage, variant, ik, prec="fp32c"):
     """The kernel a plan variant mask (and precision) runs for a stage, as
     dram_traffic.txt tags it."""
     if stage == "make_rho":
-        t = "copies4" if variant & 4 else ("cs" if variant & 32 else "tile")
+        t = "copies4" if variant & 4 else ("pair" if variant & 128 else ("cs" if variant & 32 else "tile"))
         return t if prec == "fp32c" else f"{t}-{prec}"  # FP32: the one-word accumulator
     if stage == "fieldforce":
         if variant & 64:

@@ -252,10 +252,13 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * particle records into a second shared-memory buffer while they gather the
  * current tile (PPPM_FP32 / PPPM_FP32C only; not with bit 0; force steps
  * only, like bit 0; the ad form runs one particle per thread over units of
- * two z-adjacent tiles).  Default: bit 4 when the mesh has fewer than 304 tiles of 8^3
- * (two per SM), bit 0 for ik plans whose n_max is at least 16 per tile, bit 3
- * where it is allowed except on 256^3 meshes (cuFFT measured faster there),
- * bit 5, bit 6 for PPPM_FP32 / PPPM_FP32C ad plans.
+ * two z-adjacent tiles).  Bit 7: make_rho takes z-pairs of tiles, one
+ * brick and one flush per pair (meshes whose z edge is a multiple of 16; not
+ * with bits 1, 2, 4).  Default: bit 4 when the mesh has fewer than 304 tiles
+ * of 8^3 (two per SM), bit 0 for ik plans whose n_max is at least 16 per
+ * tile, bit 3 where it is allowed except on 256^3 meshes (cuFFT measured
+ * faster there), bit 5, bit 6 for PPPM_FP32 / PPPM_FP32C ad plans, bit 7
+ * where it is allowed and bit 4 is not set.
  * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a
  * combination the plan does not allow).
  * pppm_autotune times every variant on the caller's inputs (two warm-up and

@@ -159,18 +159,27 @@ __device__ __forceinline__ void tile_extent(const Geom<R> &g, int tile, int &ox,
 
 // CS: the brick's strides are those of the largest tile (TILE_B + P - 1 per
 // edge, compile-time), so every stencil point's offset is an immediate;
-// otherwise they are this tile's own extents.
-template <typename R, int P, int ACC, bool CS = false>
+// otherwise they are this tile's own extents.  NZT = 2 (with CS; the plan's
+// variant bit 7): the CTA takes tiles `tile` and `tile` + 1, z neighbours
+// (the mesh's z tiles are even in number and uniform), whose particles are
+// contiguous in the sorted order, in one brick TILE_B + P - 1 by TILE_B +
+// P - 1 by 2 TILE_B + P - 1: the pair's shared halo reaches the mesh's
+// atomics once instead of twice, and a CTA's fixed costs (scale, order,
+// clearing) serve twice the particles.
+template <typename R, int P, int ACC, bool CS = false, int NZT = 1>
 __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &b, R *__restrict__ rho,
                                               int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    static_assert(NZT == 1 || (NZT == 2 && CS), "tile pairs use the compile-time-stride brick");
 
     int ox, oy, oz, Ex, Ey, Ez;
     tile_extent<R, P>(g, tile, ox, oy, oz, Ex, Ey, Ez);
+    if (NZT == 2) Ez += g.TE[2];                // the pair's brick (uniform z tiles)
     constexpr int EB = TILE_B + P - 1;          // widest brick edge
-    const int SZ = CS ? EB : Ez;                // brick row (z) stride
-    const int SY = CS ? EB * EB : Ey * Ez;      // brick plane stride
-    const int vol = CS ? EB * EB * EB : Ex * Ey * Ez;
+    constexpr int EBZ = NZT * TILE_B + P - 1;   // ... along z
+    const int SZ = CS ? EBZ : Ez;               // brick row (z) stride
+    const int SY = CS ? EB * EBZ : Ey * Ez;     // brick plane stride
+    const int vol = CS ? EB * EB * EBZ : Ex * Ey * Ez;
 
     // bank-ordering scratch: particles of a sub-chunk counted by the shared
     // bank of their first stencil point, then listed in that order
@@ -190,8 +199,8 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     }
 
     pdl_wait();  // the sort's outputs (and its reads of the histogram) are complete
-    const int start = b.tile_start[tile], end = b.tile_start[tile + 1];
-    if (threadIdx.x == 0) b.tile_count[tile] = 0;  // histogram is clean for the next step
+    const int start = b.tile_start[tile], end = b.tile_start[tile + NZT];
+    if (threadIdx.x < NZT) b.tile_count[tile + threadIdx.x] = 0;  // histogram is clean for the next step
     if (start == end) return;
 
     R *accr = reinterpret_cast<R *>(smem_raw);
@@ -351,9 +360,10 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     // brick column (y = ry, z = lz) -- edges are at most TILE_B + P - 1 <= 16
     // points -- and walks it along x; every wrap is a single conditional since
     // the brick is never wider than the mesh plus one period.
+    // (a tile pair's 2 TILE_B + P - 1 deep columns: every thread takes columns
+    // a CTA apart)
     static_assert(TILE_B + 7 - 1 <= 16 && RHO_THREADS == 256, "one brick column per thread");
-    const int lz = threadIdx.x & 15, ry = threadIdx.x >> 4;
-    if (lz < Ez && ry < Ey) {
+    auto flush_column = [&](int ry, int lz) {
         int gz = oz - g.rlo + lz;
         gz += (gz < 0) ? g.M[2] : 0;
         gz -= (gz >= g.M[2]) ? g.M[2] : 0;
@@ -381,6 +391,12 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
             if (v != R(0)) atomicAdd(col + gx * plane, v);
             gx = (gx + 1 == g.M[0]) ? 0 : gx + 1;
         }
+    };
+    if (NZT == 1) {
+        const int lz = threadIdx.x & 15, ry = threadIdx.x >> 4;
+        if (lz < Ez && ry < Ey) flush_column(ry, lz);
+    } else {
+        for (int c = threadIdx.x; c < Ey * EBZ; c += blockDim.x) flush_column(c / EBZ, c % EBZ);
     }
 }
 
@@ -578,9 +594,9 @@ __global__ void __launch_bounds__(GBrick<P>::NT) k_batch_make_rho_fixed(const Ba
     make_rho_fixed_body<P>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);
 }
 
-template <typename R, int P, int ACC, bool CS = false>
+template <typename R, int P, int ACC, bool CS = false, int NZT = 1>
 __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b, R *__restrict__ rho) {
-    make_rho_body<R, P, ACC, CS>(g, b, rho, blockIdx.x);
+    make_rho_body<R, P, ACC, CS, NZT>(g, b, rho, NZT * blockIdx.x);
 }
 
 template <typename R, int P, int ACC>
@@ -590,10 +606,11 @@ __global__ void __launch_bounds__(RHO_THREADS) k_batch_make_rho(const BatchSys<R
     make_rho_body<R, P, ACC, true>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);  // compile-time brick strides
 }
 
+// Dynamic shared memory of make_rho_body: one tile's brick, or a z-pair's
 template <typename R, int P>
-static size_t brick_bytes(int acc) {
+static size_t brick_bytes(int acc, int nzt = 1) {
     const int E = TILE_B + P - 1;
-    return (size_t)E * E * E * (acc != ACC_NATIVE ? 8 : sizeof(R));
+    return (size_t)E * E * (E + (nzt - 1) * TILE_B) * (acc != ACC_NATIVE ? 8 : sizeof(R));
 }
 
 template <typename K, typename R>
@@ -615,6 +632,19 @@ static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, int acc, cudaS
         }
     }
     const bool cs = g.rho_copies == 2;  // one brick with compile-time strides
+    if (g.rho_copies == 4) {            // ... over a z-pair of tiles
+        const size_t b2 = brick_bytes<R, P>(acc, 2);
+        const dim3 grid(g.ntiles / 2);
+        if (acc == ACC_FIXED) {
+            launch_one(k_make_rho<R, P, ACC_FIXED, true, 2>, pdl, grid, b2, s, g, b, rho);
+        } else if (acc == ACC_FIXED1) {
+            if constexpr (std::is_same<R, float>::value)
+                launch_one(k_make_rho<R, P, ACC_FIXED1, true, 2>, pdl, grid, b2, s, g, b, rho);
+        } else {
+            launch_one(k_make_rho<R, P, ACC_NATIVE, true, 2>, pdl, grid, b2, s, g, b, rho);
+        }
+        return;
+    }
     if (acc == ACC_FIXED) {
         if (cs) launch_one(k_make_rho<R, P, ACC_FIXED, true>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);
         else launch_one(k_make_rho<R, P, ACC_FIXED>, pdl, dim3(g.ntiles), bytes, s, g, b, rho);

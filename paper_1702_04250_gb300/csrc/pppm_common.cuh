@@ -56,7 +56,7 @@ struct Geom {
     int ff_tiled;         // fieldforce variant: 0 per-particle through L1, 1 tile-staged brick (one CTA a
                           // tile), 2 persistent double-buffered tile-staged brick (FP32 step types)
     int rho_copies;       // make_rho brick: 0 one, tile strides; 1 four interleaved copies (FP32C);
-                          // 2 one, strides of the largest tile
+                          // 2 one, strides of the largest tile; 4 one per z-pair of tiles, those strides
     int lut_bins;         // coefficient table entries (0: exact polynomials), see pppm_set_lut
     int launch_flags;     // host side: LF_* launch options of this step
     int planar_stride;    // ik field layout: 0 interleaved (Ex,Ey,Ez,pad); > 0 three planes this far apart

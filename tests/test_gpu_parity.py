@@ -294,6 +294,55 @@ def test_dense_tile(torch, prec, P):
             pm.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32"])
+@pytest.mark.parametrize("P", [2, 5, 7])
+def test_make_rho_tile_pairs(torch, prec, P):
+    """make_rho on z-pairs of 8^3 tiles (variant bit 7) on a 32 x 24 x 48 mesh
+    (6 z tiles, every pair's brick wrapping in z at the ends): the mesh and
+    forces match the oracle, and the bit is refused on a mesh whose z tiles
+    are odd in number.  Then 40,000 charges packed into one tile pair (two
+    low-word folds in FP32C)."""
+    from paper_1702_04250_gb300 import pppm
+
+    r = np.random.default_rng(300 + P)
+    box, mesh, g = (30.0, 22.0, 45.0), (32, 24, 48), 0.5
+    n = 9000
+    x = r.uniform(-2.0, 50.0, (n, 3)) * np.array(box) / 48.0
+    q = r.normal(size=n)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    xo, qo = oracle_inputs(x, q, prec)
+    ref = OraclePPPM(box, mesh, P, g, "ik", 1.0).compute(xo, qo, keep=True)
+    plan = pppm.PPPM(box, n, P, mesh, g, mode="ik", precision=prec)
+    base = plan.variant()
+    plan.set_variant((base & ~(4 | 16)) | 128)
+    f, ev = plan.compute(torch.tensor(x, dtype=dt, device="cuda"), torch.tensor(q, dtype=dt, device="cuda"))
+    plan.sync()
+    rho = plan.get_array("rho").astype(np.float64)
+    rerr = np.sqrt(np.mean((rho - ref["rho"]) ** 2)) / np.sqrt(np.mean(ref["rho"] ** 2))
+    assert rerr < (1e-12 if prec == "fp64" else 1e-5), rerr
+    check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, prec, f"tile pairs P={P}")
+    plan.close()
+    odd = pppm.PPPM(box, n, P, (32, 24, 40), g, mode="ik", precision=prec)
+    with pytest.raises(pppm.PPPMError):
+        odd.set_variant(128)
+    odd.close()
+    if prec != "fp32c" or P != 7:
+        return
+    m = 40000
+    xd = 10.0 + r.uniform(0.0, 1.2, (m, 3)) * np.array([1.0, 1.0, 2.0])
+    qd = r.normal(size=m)
+    xo, qo = oracle_inputs(xd, qd, prec)
+    refd = OraclePPPM(box, mesh, P, g, "ik", 1.0).compute(xo, qo, keep=True)
+    pd = pppm.PPPM(box, m, P, mesh, g, mode="ik", precision=prec)
+    pd.set_variant((pd.variant() & ~(4 | 16)) | 128)
+    fd, evd = pd.compute(torch.tensor(xd, dtype=dt, device="cuda"), torch.tensor(qd, dtype=dt, device="cuda"))
+    pd.sync()
+    rd = pd.get_array("rho").astype(np.float64)
+    assert np.sqrt(np.mean((rd - refd["rho"]) ** 2)) / np.sqrt(np.mean(refd["rho"] ** 2)) < 1e-5
+    check_all(fd.double().cpu().numpy(), evd.cpu().numpy(), refd, prec, "dense tile pair")
+    pd.close()
+
+
 @pytest.mark.parametrize("prec,P,n,spread", [("fp32c", 5, 256, 1.5), ("fp32c", 7, 257, 1.5),
                                              ("fp32c", 5, 513, 0.2), ("fp64", 7, 257, 0.2)])
 def test_subchunk_boundaries(torch, prec, P, n, spread):
@@ -417,7 +466,9 @@ def test_fieldforce_variants_and_autotune(torch, c2_refs, mode):
     # fieldforce per particle / tile-staged x make_rho one / four brick copies
     # x cuFFT / hand-written Poisson solve x 8^3 / 4^3 tiles
     # ... x the persistent double-buffered fieldforce (bit 6)
-    for v in (0, 1, 4, 5, 8, 9, 12, 13, 16, 17, 20, 25, 29, 32, 41, 57, 64, 68, 72, 80, 96, 104, 120):
+    # ... x make_rho on z-pairs of tiles (bit 7)
+    for v in (0, 1, 4, 5, 8, 9, 12, 13, 16, 17, 20, 25, 29, 32, 41, 57, 64, 68, 72, 80, 96, 104, 120,
+              128, 129, 136, 160, 192, 200, 224):
         plan.set_variant(v)
         f, ev = plan.compute(x, q)
         plan.sync()
@@ -426,12 +477,12 @@ def test_fieldforce_variants_and_autotune(torch, c2_refs, mode):
     assert plan.variant() == 41
     choice = plan.autotune(x, q)
     assert plan.variant() == choice
-    assert choice & ~0x7D == 0 and not (choice & 4 and choice & 32)  # bits 0, 2, 3, 4, 5, 6
-    assert not (choice & 1 and choice & 64)
+    assert choice & ~0xFD == 0 and not (choice & 4 and choice & 32)  # bits 0, 2, 3, 4, 5, 6, 7
+    assert not (choice & 1 and choice & 64) and not (choice & 128 and choice & (4 | 16))
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), refs[(mode, "fp32")], "fp32c", f"autotuned {choice}")
-    for bad in (2, 3, 6, 7, 10, 18, 36, 65, 128):  # long tiles are reserved; exclusive pairs; unknown bits
+    for bad in (2, 3, 6, 7, 10, 18, 36, 65, 130, 132, 144, 256):  # long tiles are reserved; exclusive pairs; unknown bits
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(bad)
     p64 = pppm.PPPM(w.box, w.n, w.order, w.mesh, g, mode, "fp64", w.qqrd2e)
@@ -456,7 +507,7 @@ def test_order7_variants(torch, mode):
     q = torch.tensor(w.q, dtype=torch.float32, device="cuda")
     plan = pppm.PPPM(w.box, w.n, 7, w.mesh, g, mode, "fp32c", w.qqrd2e)
     assert plan.info()["tile"] == 8 and plan.info()["ntiles"] == 512
-    for v in (0, 1, 4, 5, 8, 13, 16, 29, 32, 41, 64, 96, 104, 112):
+    for v in (0, 1, 4, 5, 8, 13, 16, 29, 32, 41, 64, 96, 104, 112, 128, 192, 200):
         plan.set_variant(v)
         f, ev = plan.compute(x, q)
         plan.sync()
@@ -465,7 +516,7 @@ def test_order7_variants(torch, mode):
         with pytest.raises(pppm.PPPMError):
             plan.set_variant(bad)
     choice = plan.autotune(x, q)
-    assert choice & ~0x7D == 0
+    assert choice & ~0xFD == 0
     f, ev = plan.compute(x, q)
     plan.sync()
     check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, "fp32c", f"P=7 autotuned {choice}")
