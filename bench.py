@@ -460,6 +460,10 @@ def gpu_arm(args, rank, world):
     roof["launches_timed"] = f"every {every}nd timed step carries events around make_rho and fieldforce"
     roof["kernels"] = kernels
     roof["stage_ms_all_events"] = {k: round(v, 5) for k, v in disc.items()}
+    # every stage's algorithmic bytes over its time in that pass (the 3-D
+    # transforms are cuFFT's unless the hand-written solve runs)
+    roof["stage_gbs_all_events"] = {k: round(alg_bytes(k, w.n, w.mesh, ik) / (v * 1e-3) / 1e9, 1)
+                                    for k, v in disc.items() if v > 0}
     roof["dominant_own_stage"] = dom
 
     # end to end through the host-buffer C-ABI call (pinned host memory)
