@@ -253,12 +253,12 @@ int pppm_stage_times(pppm_plan *p, float ms[6]);
  * current tile (PPPM_FP32 / PPPM_FP32C only; not with bit 0; force steps
  * only, like bit 0; the ad form runs one particle per thread over units of
  * two z-adjacent tiles).  Bit 7: make_rho takes z-pairs of tiles, one
- * brick and one flush per pair (meshes whose z edge is a multiple of 16; not
- * with bits 1, 2, 4).  Default: bit 4 when the mesh has fewer than 304 tiles
+ * brick and one flush per pair (the last tile of a row of an odd number of z
+ * tiles alone; not with bits 1, 2, 4).  Default: bit 4 when the mesh has fewer than 304 tiles
  * of 8^3 (two per SM), bit 0 for ik plans whose n_max is at least 16 per
  * tile, bit 3 where it is allowed except on 256^3 meshes (cuFFT measured
  * faster there), bit 5, bit 6 for PPPM_FP32 / PPPM_FP32C ad plans, bit 7
- * where it is allowed and bit 4 is not set.
+ * unless bit 4 is set.
  * pppm_set_variant forces a bitmask (PPPM_EINVAL for unknown bits or a
  * combination the plan does not allow).
  * pppm_autotune times every variant on the caller's inputs (two warm-up and
@@ -346,14 +346,23 @@ int pppm_batch_sync(pppm_batch *b);
  * the order-P systems accumulate in four interleaved brick copies (see
  * pppm_set_variant bit 2; PPPM_EINVAL for other precisions); bit 8 + P runs
  * the order-P fieldforce tile-staged, one CTA per system tile staging its
- * field brick in shared memory (see pppm_set_variant bit 0; any precision).
- * PPPM_EINVAL for other bits.  pppm_batch_autotune times the whole call as
- * the batch runs it (one graph per setting when graph mode is on; one
- * warm-up and five timed calls, scored by the fastest) with each present
- * order's make_rho bit (FP32C only) and fieldforce bit flipped in turn,
- * keeps every flip that is faster, writes the mask to choice_out (nullable)
- * and leaves f holding a valid result.  Both drop the captured graph. */
+ * field brick in shared memory (see pppm_set_variant bit 0; any precision);
+ * bit 16 + P runs the order-P make_rho over z-pairs of tiles, one CTA per
+ * pair (see pppm_set_variant bit 7; any precision; not with bit P).
+ * PPPM_EINVAL for other bits or both of bits P and 16 + P.  Default: bits
+ * 16 + P of every order (0xFC0000).
+ * pppm_batch_autotune times the whole call as the batch runs it (one graph
+ * per setting when graph mode is on; one warm-up and five timed calls,
+ * scored by the fastest) with each present order's tile-pair bit, brick-copy
+ * bit (FP32C only) and fieldforce bit flipped in turn (a flip that would set
+ * both make_rho bits is skipped), keeps every flip that is faster, writes
+ * the mask to choice_out (nullable) and leaves f holding a valid result.
+ * Both drop the captured graph. */
 int pppm_batch_set_variant(pppm_batch *b, int variants);
+/* The batch's current variant bitmask (the default, the last
+ * pppm_batch_set_variant or the autotuner's choice) into *variants;
+ * PPPM_EINVAL for NULL. */
+int pppm_batch_get_variant(const pppm_batch *b, int *variants);
 int pppm_batch_autotune(pppm_batch *b, const void *x, const void *q, void *f, int *choice_out);
 /* [0] systems, [1] total particles, [2] mesh-size classes, [3] distinct orders */
 int pppm_batch_info(const pppm_batch *b, int64_t info[4]);

@@ -196,6 +196,56 @@ int launch_kspace_error(const KErrSetup &ks, double *part, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Per step
 // ---------------------------------------------------------------------------
+// One spectrum element e = (kx, ky, kz): the field (ik: three components) or
+// potential (ad) spectrum and this element's energy/virial terms (Eq. 5's
+// G times |rho_hat|^2, weight w = 1 on the kz = 0 and z-Nyquist planes, 2
+// elsewhere for the half spectrum).
+template <typename R, bool IK>
+__device__ __forceinline__ void green_point(complex_t<R> r, R G, R kx, R ky, R kz, R dkx, R dky, R dkz, R w,
+                                            R i4g2, complex_t<R> *__restrict__ spec, int e, int total,
+                                            R (&acc)[7]) {
+    const R pr = G * r.x, pi = G * r.y;
+    if (IK) {
+        // E_a = -i k_a G rho_hat / M  ->  (k_a pi, -k_a pr)
+        complex_t<R> o;
+        o.x = dkx * pi; o.y = -dkx * pr; spec[e] = o;
+        o.x = dky * pi; o.y = -dky * pr; spec[total + e] = o;
+        o.x = dkz * pi; o.y = -dkz * pr; spec[2 * total + e] = o;
+    } else {
+        complex_t<R> o;
+        o.x = pr; o.y = pi;
+        spec[e] = o;
+    }
+    const R s = w * G * (r.x * r.x + r.y * r.y);
+    const R k2 = kx * kx + ky * ky + kz * kz;
+    const R fac = (k2 > R(0)) ? R(2) * (R(1) + k2 * i4g2) / k2 : R(0);
+    const R sf = s * fac;
+    acc[0] += s;
+    acc[1] += s - sf * kx * kx;
+    acc[2] += s - sf * ky * ky;
+    acc[3] += s - sf * kz * kz;
+    acc[4] -= sf * kx * ky;
+    acc[5] -= sf * kx * kz;
+    acc[6] -= sf * ky * kz;
+}
+
+// the CTA's seven energy/virial partials, summed in a fixed order
+template <typename R>
+__device__ __forceinline__ void green_partials(R (&acc)[7], double (&sh)[7][GREEN_THREADS / 32], double *part,
+                                               int lb) {
+    const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;
+    for (int c = 0; c < 7; ++c) {
+        const R v = warp_sum_t<R>(acc[c]);
+        if (lane == 0) sh[c][wrow] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = 0.0;
+        for (int w = 0; w < GREEN_THREADS / 32; ++w) v += sh[threadIdx.x][w];
+        part[7 * lb + threadIdx.x] = v;
+    }
+}
+
 template <typename R, bool IK>
 __device__ __forceinline__ void green_body(const Geom<R> &g, const complex_t<R> *__restrict__ rhat,
                                            complex_t<R> *__restrict__ spec, const GreenBufs &b,
@@ -219,7 +269,6 @@ __device__ __forceinline__ void green_body(const Geom<R> &g, const complex_t<R> 
         const int ix = row / My, iy = row - ix * My;
         const R kx = kv[ix], ky = kv[Mx + iy];
         const R dkx = kd[ix], dky = kd[Mx + iy];
-        const R kxy2 = kx * kx + ky * ky;
         // GREEN_ZU elements a lane, every load issued before any is used (the
         // kernel streams rho_hat and G once: its time is bytes in flight)
         for (int iz0 = lane; iz0 < Mzh; iz0 += GREEN_ZU * 32) {
@@ -240,48 +289,62 @@ __device__ __forceinline__ void green_body(const Geom<R> &g, const complex_t<R> 
             for (int u = 0; u < GREEN_ZU; ++u) {
                 const int iz = iz0 + 32 * u;
                 if (iz >= Mzh) continue;
-                const int e = row * Mzh + iz;
-                const complex_t<R> r = rv[u];
-                const R G = Gv[u];
-                const R pr = G * r.x, pi = G * r.y;
-                if (IK) {
-                    // E_a = -i k_a G rho_hat / M  ->  (k_a pi, -k_a pr)
-                    const R dkz = kd[Mx + My + iz];
-                    complex_t<R> o;
-                    o.x = dkx * pi; o.y = -dkx * pr; spec[e] = o;
-                    o.x = dky * pi; o.y = -dky * pr; spec[total + e] = o;
-                    o.x = dkz * pi; o.y = -dkz * pr; spec[2 * total + e] = o;
-                } else {
-                    complex_t<R> o;
-                    o.x = pr; o.y = pi;
-                    spec[e] = o;
-                }
                 const R w = (iz == 0 || (evenz && iz == Mzh - 1)) ? R(1) : R(2);
-                const R s = w * G * (r.x * r.x + r.y * r.y);
-                const R kz = kv[Mx + My + iz];
-                const R k2 = kxy2 + kz * kz;
-                const R fac = (k2 > R(0)) ? R(2) * (R(1) + k2 * i4g2) / k2 : R(0);
-                const R sf = s * fac;
-                acc[0] += s;
-                acc[1] += s - sf * kx * kx;
-                acc[2] += s - sf * ky * ky;
-                acc[3] += s - sf * kz * kz;
-                acc[4] -= sf * kx * ky;
-                acc[5] -= sf * kx * kz;
-                acc[6] -= sf * ky * kz;
+                green_point<R, IK>(rv[u], Gv[u], kx, ky, kv[Mx + My + iz], dkx, dky, IK ? kd[Mx + My + iz] : R(0),
+                                   w, i4g2, spec, row * Mzh + iz, total, acc);
             }
         }
     }
-    for (int c = 0; c < 7; ++c) {
-        const R v = warp_sum_t<R>(acc[c]);
-        if (lane == 0) sh[c][wrow] = (double)v;
+    green_partials<R>(acc, sh, b.part, lb);
+}
+
+// The same over the spectrum as one flat array (element e = row Mzh + kz):
+// consecutive threads take consecutive elements whatever the row length, for
+// meshes whose half rows (Mzh = M_z / 2 + 1) are short against a warp (the
+// batch's 16^3 - 64^3 meshes: 9 - 33 elements, where a warp a row leaves up
+// to 23 of its 32 lanes idle).  Each thread keeps GREEN_ZU elements, a grid
+// stride apart, in flight.
+template <typename R, bool IK>
+__device__ __forceinline__ void green_flat_body(const Geom<R> &g, const complex_t<R> *__restrict__ rhat,
+                                                complex_t<R> *__restrict__ spec, const GreenBufs &b,
+                                                const EnergyConsts &ec, int lb, int nlb) {
+    __shared__ double sh[7][GREEN_THREADS / 32];
+    pdl_wait();  // the forward transform is complete
+    const int Mx = g.M[0], My = g.M[1], Mzh = g.Mzh;
+    const int total = Mx * My * Mzh;
+    const R *__restrict__ Gs = reinterpret_cast<const R *>(b.Gs);
+    const R *__restrict__ kv = reinterpret_cast<const R *>(b.kvec);
+    const R *__restrict__ kd = reinterpret_cast<const R *>(b.kdiff);
+    const bool evenz = (2 * (Mzh - 1) == g.M[2]);
+    const R i4g2 = (R)ec.inv4g2;
+    R acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int stride = nlb * GREEN_THREADS;
+    for (int e0 = lb * GREEN_THREADS + (int)threadIdx.x; e0 < total; e0 += GREEN_ZU * stride) {
+        complex_t<R> rv[GREEN_ZU];
+        R Gv[GREEN_ZU];
+#pragma unroll
+        for (int u = 0; u < GREEN_ZU; ++u) {
+            const int e = e0 + u * stride;
+            if (e < total) {
+                rv[u] = rhat[e];
+                Gv[u] = Gs[e];
+            } else {
+                rv[u].x = rv[u].y = R(0);
+                Gv[u] = R(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GREEN_ZU; ++u) {
+            const int e = e0 + u * stride;
+            if (e >= total) continue;
+            const int row = e / Mzh, iz = e - row * Mzh;
+            const int ix = row / My, iy = row - ix * My;
+            const R w = (iz == 0 || (evenz && iz == Mzh - 1)) ? R(1) : R(2);
+            green_point<R, IK>(rv[u], Gv[u], kv[ix], kv[Mx + iy], kv[Mx + My + iz], IK ? kd[ix] : R(0),
+                               IK ? kd[Mx + iy] : R(0), IK ? kd[Mx + My + iz] : R(0), w, i4g2, spec, e, total, acc);
+        }
     }
-    __syncthreads();
-    if (threadIdx.x < 7) {
-        double v = 0.0;
-        for (int w = 0; w < GREEN_THREADS / 32; ++w) v += sh[threadIdx.x][w];
-        b.part[7 * lb + threadIdx.x] = v;
-    }
+    green_partials<R>(acc, sh, b.part, lb);
 }
 
 template <typename R, bool IK>
@@ -295,9 +358,9 @@ template <typename R, bool IK>
 __global__ void __launch_bounds__(GREEN_THREADS) k_batch_green(const BatchSys<R> *__restrict__ sys, BatchList bl) {
     const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
     const BatchSys<R> &S = sys[bl.ids[e]];
-    green_body<R, IK>(S.g, reinterpret_cast<const complex_t<R> *>(S.rho_hat),
-                      reinterpret_cast<complex_t<R> *>(S.spec), S.gb, S.ec, blockIdx.x - bl.boff[e],
-                      bl.boff[e + 1] - bl.boff[e]);
+    green_flat_body<R, IK>(S.g, reinterpret_cast<const complex_t<R> *>(S.rho_hat),
+                           reinterpret_cast<complex_t<R> *>(S.spec), S.gb, S.ec, blockIdx.x - bl.boff[e],
+                           bl.boff[e + 1] - bl.boff[e]);
 }
 
 template <typename R>

@@ -160,21 +160,35 @@ __device__ __forceinline__ void tile_extent(const Geom<R> &g, int tile, int &ox,
 // CS: the brick's strides are those of the largest tile (TILE_B + P - 1 per
 // edge, compile-time), so every stencil point's offset is an immediate;
 // otherwise they are this tile's own extents.  NZT = 2 (with CS; the plan's
-// variant bit 7): the CTA takes tiles `tile` and `tile` + 1, z neighbours
-// (the mesh's z tiles are even in number and uniform), whose particles are
+// variant bit 7): `unit` is a z-pair of tiles, row r = unit / ceil(T_z / 2),
+// pair k = unit mod ceil(T_z / 2): tiles r T_z + 2k and, unless T_z is odd
+// and k the last pair, r T_z + 2k + 1, z neighbours whose particles are
 // contiguous in the sorted order, in one brick TILE_B + P - 1 by TILE_B +
-// P - 1 by 2 TILE_B + P - 1: the pair's shared halo reaches the mesh's
-// atomics once instead of twice, and a CTA's fixed costs (scale, order,
-// clearing) serve twice the particles.
+// P - 1 by 2 TILE_B + P - 1 (z tiles are at most TILE_B deep): the pair's
+// shared halo reaches the mesh's atomics once instead of twice, and a CTA's
+// fixed costs (scale, order, clearing) serve twice the particles.  NZT = 1:
+// `unit` is the tile.
 template <typename R, int P, int ACC, bool CS = false, int NZT = 1>
 __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &b, R *__restrict__ rho,
-                                              int tile) {
+                                              int unit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     static_assert(NZT == 1 || (NZT == 2 && CS), "tile pairs use the compile-time-stride brick");
 
+    int tile = unit, ntz = 1;  // first tile and tiles of this CTA
+    if (NZT == 2) {
+        const int pairs = (g.T[2] + 1) >> 1;
+        const int row = div_tiles(unit, pairs);
+        const int k = unit - row * pairs;
+        tile = row * g.T[2] + 2 * k;
+        ntz = min(2, g.T[2] - 2 * k);
+    }
     int ox, oy, oz, Ex, Ey, Ez;
     tile_extent<R, P>(g, tile, ox, oy, oz, Ex, Ey, Ez);
-    if (NZT == 2) Ez += g.TE[2];                // the pair's brick (uniform z tiles)
+    if (NZT == 2 && ntz == 2) {  // the pair's brick: through the end of the second tile
+        const int tz = tile - div_tiles(tile, g.T[2]) * g.T[2];
+        Ez = ((g.T[2] * g.TE[2] == g.M[2]) ? (tz + 2) * g.TE[2] : tile_origin(tz + 2, g.T[2], g.M[2])) - oz +
+             P - 1;
+    }
     constexpr int EB = TILE_B + P - 1;          // widest brick edge
     constexpr int EBZ = NZT * TILE_B + P - 1;   // ... along z
     const int SZ = CS ? EBZ : Ez;               // brick row (z) stride
@@ -199,8 +213,8 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     }
 
     pdl_wait();  // the sort's outputs (and its reads of the histogram) are complete
-    const int start = b.tile_start[tile], end = b.tile_start[tile + NZT];
-    if (threadIdx.x < NZT) b.tile_count[tile + threadIdx.x] = 0;  // histogram is clean for the next step
+    const int start = b.tile_start[tile], end = b.tile_start[tile + ntz];
+    if ((int)threadIdx.x < ntz) b.tile_count[tile + threadIdx.x] = 0;  // histogram is clean for the next step
     if (start == end) return;
 
     R *accr = reinterpret_cast<R *>(smem_raw);
@@ -396,7 +410,10 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
         const int lz = threadIdx.x & 15, ry = threadIdx.x >> 4;
         if (lz < Ez && ry < Ey) flush_column(ry, lz);
     } else {
-        for (int c = threadIdx.x; c < Ey * EBZ; c += blockDim.x) flush_column(c / EBZ, c % EBZ);
+        for (int c = threadIdx.x; c < Ey * EBZ; c += blockDim.x) {
+            const int lz = c % EBZ;
+            if (lz < Ez) flush_column(c / EBZ, lz);
+        }
     }
 }
 
@@ -596,14 +613,15 @@ __global__ void __launch_bounds__(GBrick<P>::NT) k_batch_make_rho_fixed(const Ba
 
 template <typename R, int P, int ACC, bool CS = false, int NZT = 1>
 __global__ void __launch_bounds__(RHO_THREADS) k_make_rho(Geom<R> g, SortBufs b, R *__restrict__ rho) {
-    make_rho_body<R, P, ACC, CS, NZT>(g, b, rho, NZT * blockIdx.x);
+    make_rho_body<R, P, ACC, CS, NZT>(g, b, rho, blockIdx.x);
 }
 
-template <typename R, int P, int ACC>
+// (NZT = 2: the list counts each system's z-pairs of tiles)
+template <typename R, int P, int ACC, int NZT = 1>
 __global__ void __launch_bounds__(RHO_THREADS) k_batch_make_rho(const BatchSys<R> *__restrict__ sys, BatchList bl) {
     const int e = batch_entry(bl.boff, bl.L, blockIdx.x);
     const BatchSys<R> &S = sys[bl.ids[e]];
-    make_rho_body<R, P, ACC, true>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);  // compile-time brick strides
+    make_rho_body<R, P, ACC, true, NZT>(S.g, S.sb, S.rho, blockIdx.x - bl.boff[e]);  // compile-time brick strides
 }
 
 // Dynamic shared memory of make_rho_body: one tile's brick, or a z-pair's
@@ -634,7 +652,7 @@ static void launch_p(const Geom<R> &g, const SortBufs &b, R *rho, int acc, cudaS
     const bool cs = g.rho_copies == 2;  // one brick with compile-time strides
     if (g.rho_copies == 4) {            // ... over a z-pair of tiles
         const size_t b2 = brick_bytes<R, P>(acc, 2);
-        const dim3 grid(g.ntiles / 2);
+        const dim3 grid(g.T[0] * g.T[1] * ((g.T[2] + 1) / 2));
         if (acc == ACC_FIXED) {
             launch_one(k_make_rho<R, P, ACC_FIXED, true, 2>, pdl, grid, b2, s, g, b, rho);
         } else if (acc == ACC_FIXED1) {
@@ -700,13 +718,26 @@ static cudaError_t prepare_p(int acc) {
 }
 
 template <typename R, int P>
-static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc, bool copies4, cudaStream_t s) {
+static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc, bool copies4, bool pairs,
+                           cudaStream_t s) {
     const size_t bytes = brick_bytes<R, P>(acc);
     if constexpr (std::is_same<R, float>::value) {
         if (acc == ACC_FIXED && copies4) {
             k_batch_make_rho_fixed<P><<<bl.nblocks, GBrick<P>::NT, GBrick<P>::BYTES, s>>>(sys, bl);
             return;
         }
+    }
+    if (pairs) {  // (a pair's brick stays below the default 48 KB of dynamic shared memory)
+        const size_t b2 = brick_bytes<R, P>(acc, 2);
+        if (acc == ACC_FIXED) {
+            k_batch_make_rho<R, P, ACC_FIXED, 2><<<bl.nblocks, RHO_THREADS, b2, s>>>(sys, bl);
+        } else if (acc == ACC_FIXED1) {
+            if constexpr (std::is_same<R, float>::value)
+                k_batch_make_rho<R, P, ACC_FIXED1, 2><<<bl.nblocks, RHO_THREADS, b2, s>>>(sys, bl);
+        } else {
+            k_batch_make_rho<R, P, ACC_NATIVE, 2><<<bl.nblocks, RHO_THREADS, b2, s>>>(sys, bl);
+        }
+        return;
     }
     if (acc == ACC_FIXED) {
         k_batch_make_rho<R, P, ACC_FIXED><<<bl.nblocks, RHO_THREADS, bytes, s>>>(sys, bl);
@@ -720,22 +751,23 @@ static void launch_batch_p(const BatchSys<R> *sys, const BatchList &bl, int acc,
 
 // The meshes of the systems in the list must have been cleared.
 template <typename R>
-void launch_batch_make_rho(const BatchSys<R> *sys, const BatchList &bl, int P, bool comp, bool copies4,
+void launch_batch_make_rho(const BatchSys<R> *sys, const BatchList &bl, int P, bool comp, bool copies4, bool pairs,
                            cudaStream_t s) {
     if (bl.nblocks == 0) return;
     const int acc = comp ? ACC_FIXED : (std::is_same<R, float>::value ? ACC_FIXED1 : ACC_NATIVE);
     switch (P) {
-        case 2: launch_batch_p<R, 2>(sys, bl, acc, copies4, s); break;
-        case 3: launch_batch_p<R, 3>(sys, bl, acc, copies4, s); break;
-        case 4: launch_batch_p<R, 4>(sys, bl, acc, copies4, s); break;
-        case 5: launch_batch_p<R, 5>(sys, bl, acc, copies4, s); break;
-        case 6: launch_batch_p<R, 6>(sys, bl, acc, copies4, s); break;
-        case 7: launch_batch_p<R, 7>(sys, bl, acc, copies4, s); break;
+        case 2: launch_batch_p<R, 2>(sys, bl, acc, copies4, pairs, s); break;
+        case 3: launch_batch_p<R, 3>(sys, bl, acc, copies4, pairs, s); break;
+        case 4: launch_batch_p<R, 4>(sys, bl, acc, copies4, pairs, s); break;
+        case 5: launch_batch_p<R, 5>(sys, bl, acc, copies4, pairs, s); break;
+        case 6: launch_batch_p<R, 6>(sys, bl, acc, copies4, pairs, s); break;
+        case 7: launch_batch_p<R, 7>(sys, bl, acc, copies4, pairs, s); break;
         default: break;
     }
 }
-template void launch_batch_make_rho<float>(const BatchSys<float> *, const BatchList &, int, bool, bool, cudaStream_t);
-template void launch_batch_make_rho<double>(const BatchSys<double> *, const BatchList &, int, bool, bool,
+template void launch_batch_make_rho<float>(const BatchSys<float> *, const BatchList &, int, bool, bool, bool,
+                                           cudaStream_t);
+template void launch_batch_make_rho<double>(const BatchSys<double> *, const BatchList &, int, bool, bool, bool,
                                             cudaStream_t);
 
 template <typename R>

@@ -583,8 +583,8 @@ void drop_graph(pppm_plan *p) {
 
 bool variant_ok(const pppm_plan *p, int v) {
     if (v & ~255) return false;
-    // make_rho on z-pairs of 8^3 tiles: an even number of uniform z tiles, one brick layout
-    if ((v & 128) && (p->M[2] % (2 * TILE_B) != 0 || (v & (2 | 4 | 16)))) return false;
+    // make_rho on z-pairs of tiles: 8^3 tiles (at most), one brick layout
+    if ((v & 128) && (v & (2 | 4 | 16))) return false;
     if ((v & 64) && (p->fp64 || (v & 1))) return false;  // the persistent fieldforce: FP32 step types, one variant
     if ((v & 16) && (v & 2)) return false;      // one tile shape at a time
     if ((v & 32) && (v & 4)) return false;      // one make_rho brick layout at a time
@@ -860,8 +860,8 @@ int pppm_setup(pppm_plan **out, const double box[3], int64_t n_max, int order, c
     // compile-time brick strides never measured slower (c3 make_rho 688 -> 665 us); the
     // persistent one-particle-per-thread ad fieldforce halves the 2M-charge gather (545 -> 258 us)
     const bool ad_persist = !p->ik && !p->fp64;
-    // make_rho on z-pairs of tiles where the z tiles pair up (c3: 358 -> 262 us in FP32)
-    const bool pairs = !small_tiles && p->M[2] % (2 * TILE_B) == 0;
+    // make_rho on z-pairs of 8^3 tiles (c3: 358 -> 262 us in FP32)
+    const bool pairs = !small_tiles;
     set_variants(p, ((p->ik && (double)n_max >= 16.0 * nt0) ? 1 : 0) | (p->fft_own && custom_fft_default(p->M) ? 8 : 0) |
                         (small_tiles ? 16 : 0) | 32 | (ad_persist ? 64 : 0) | (pairs ? 128 : 0));
     if ((rc = build_tables_and_green(p))) return fail(rc);

@@ -406,7 +406,7 @@ template <typename R>
 void launch_batch_sort(const BatchSys<R> *sys, const BatchList &all, const R *x, const R *q, cudaStream_t s);
 template <typename R>
 void launch_batch_make_rho(const BatchSys<R> *sys, const BatchList &byP, int P, bool compensated, bool copies4,
-                           cudaStream_t s);
+                           bool pairs, cudaStream_t s);
 template <typename R>
 void launch_batch_green(const BatchSys<R> *sys, const BatchList &all, bool ik, cudaStream_t s);
 template <typename R>

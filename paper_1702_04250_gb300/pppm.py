@@ -416,8 +416,10 @@ class PPPMBatch:
         L.pppm_batch_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
         L.pppm_batch_set_variant.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.pppm_batch_autotune.argtypes = [ctypes.c_void_p] * 4 + [ctypes.POINTER(ctypes.c_int)]
+        L.pppm_batch_get_variant.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
         for nm in ("pppm_batch_setup", "pppm_batch_compute", "pppm_batch_set_graph", "pppm_batch_sync",
-                   "pppm_batch_destroy", "pppm_batch_info", "pppm_batch_set_variant", "pppm_batch_autotune"):
+                   "pppm_batch_destroy", "pppm_batch_info", "pppm_batch_set_variant", "pppm_batch_autotune",
+                   "pppm_batch_get_variant"):
             getattr(L, nm).restype = ctypes.c_int
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -463,8 +465,15 @@ class PPPMBatch:
     def set_variant(self, variants: int):
         _check(lib().pppm_batch_set_variant(self._h, int(variants)), "pppm_batch_set_variant")
 
+    def variant(self) -> int:
+        """The batch's current kernel-variant bitmask."""
+        v = ctypes.c_int()
+        _check(lib().pppm_batch_get_variant(self._h, ctypes.byref(v)), "pppm_batch_get_variant")
+        return v.value
+
     def autotune(self, x, q):
-        """Time the per-order make_rho variants on these inputs, keep the fastest; returns the mask."""
+        """Time the per-order make_rho and fieldforce variants on these inputs, keep the fastest; returns
+        the mask."""
         torch = self.torch
         x = torch.as_tensor(x, device=self.device, dtype=self.dtype).contiguous()
         q = torch.as_tensor(q, device=self.device, dtype=self.dtype).contiguous()

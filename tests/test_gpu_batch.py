@@ -48,11 +48,13 @@ def small_batch():
     return out
 
 
-def run_batch(torch, systems, mode, prec, graph=False, C=1.0):
+def run_batch(torch, systems, mode, prec, graph=False, C=1.0, variant=None):
     from paper_1702_04250_gb300 import pppm
 
     dt = torch.float64 if prec == "fp64" else torch.float32
     b = pppm.PPPMBatch(systems, mode=mode, precision=prec, qqrd2e=C, graph=graph)
+    if variant is not None:
+        b.set_variant(variant)
     x = torch.tensor(np.concatenate([s["x"] for s in systems]).reshape(-1, 3), dtype=dt, device="cuda")
     q = torch.tensor(np.concatenate([s["q"] for s in systems]), dtype=dt, device="cuda")
     for _ in range(2 if graph else 1):
@@ -67,6 +69,23 @@ def test_small_batch_vs_oracle(torch, mode, prec):
     systems = small_batch()
     b, f, ev = run_batch(torch, systems, mode, prec)
     assert b.info()["mesh_classes"] == 5
+    check_vs_oracle(b, f, ev, systems, mode, prec)
+
+
+@pytest.mark.parametrize("mode", ["ik", "ad"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32"])
+@pytest.mark.parametrize("variant", [0xFC0000, 0])
+def test_small_batch_make_rho_layouts_vs_oracle(torch, mode, prec, variant):
+    """make_rho over z-pairs of tiles for every order (bits 16 + P, the
+    default) and one tile a CTA (mask 0): the batch's meshes have 1, 2 and 3
+    z tiles, uniform and ragged (12 / 18 / 10 / 8 / 16 / 12 points along z)."""
+    systems = small_batch()
+    b, f, ev = run_batch(torch, systems, mode, prec, variant=variant)
+    assert b.variant() == variant
+    check_vs_oracle(b, f, ev, systems, mode, prec)
+
+
+def check_vs_oracle(b, f, ev, systems, mode, prec):
     tol = 1e-6 if prec == "fp64" else 1e-4
     for s, sysd in enumerate(systems):
         lo, hi = b.offsets[s], b.offsets[s + 1]
@@ -88,10 +107,11 @@ def test_small_batch_vs_oracle(torch, mode, prec):
 
 
 def test_batch_variants_and_autotune(torch):
-    """Every order's make_rho brick (one or four copies) and fieldforce
-    (per particle through L1, or tile-staged from the planar field) give the
-    same result; autotune returns a valid mask; FP64 batches refuse the
-    make_rho bits but take the fieldforce ones."""
+    """Every order's make_rho brick (one or four copies, or one over z-pairs
+    of tiles) and fieldforce (per particle through L1, or tile-staged from
+    the planar field) give the same result; autotune returns a valid mask;
+    FP64 batches refuse the brick-copy bits but take the fieldforce and
+    tile-pair ones."""
     from paper_1702_04250_gb300 import pppm
 
     systems = small_batch()
@@ -99,7 +119,7 @@ def test_batch_variants_and_autotune(torch):
     q = torch.tensor(np.concatenate([s["q"] for s in systems]), dtype=torch.float32, device="cuda")
     b = pppm.PPPMBatch(systems, mode="ik", precision="fp32c")
     outs = []
-    for v in (0, 0xFC, 0xFC00, 0xFCFC, 0x0800 | 0x20):
+    for v in (0, 0xFC, 0xFC00, 0xFCFC, 0x0800 | 0x20, 0xFC0000, 0xFCFC00, 0x80 | 0x200000 | 0x0800):
         b.set_variant(v)
         f, ev = b.compute(x, q)
         b.sync()
@@ -107,14 +127,15 @@ def test_batch_variants_and_autotune(torch):
     for o in outs[1:]:
         assert rel_rms(o[0], outs[0][0]) < 1e-5
     choice = b.autotune(x, q)
-    assert choice & ~0xFCFC == 0
+    assert choice & ~0xFCFCFC == 0 and choice & (choice >> 16) & 0xFC == 0
     f, ev = b.compute(x, q)
     b.sync()
     assert rel_rms(f.double().cpu().numpy(), outs[0][0]) < 1e-5
     with pytest.raises(pppm.PPPMError):
         b.set_variant(1)
-    with pytest.raises(pppm.PPPMError):
-        b.set_variant(1 << 16)
+    for bad in (1 << 16, 1 << 24, 0x80 | 0x800000, 0x04 | 0x040000):  # unknown bits; pairs with copies
+        with pytest.raises(pppm.PPPMError):
+            b.set_variant(bad)
     b64 = pppm.PPPMBatch(systems, mode="ik", precision="fp64")
     with pytest.raises(pppm.PPPMError):
         b64.set_variant(1 << 5)
@@ -126,6 +147,10 @@ def test_batch_variants_and_autotune(torch):
     f1, _ = b64.compute(x64, q64)
     b64.sync()
     assert rel_rms(f1.cpu().numpy(), f0) < 1e-12
+    b64.set_variant(0xFC0000)  # tile pairs of every order, FP64
+    f2, _ = b64.compute(x64, q64)
+    b64.sync()
+    assert rel_rms(f2.cpu().numpy(), f0) < 1e-12
     for mode in ("ad",):
         ba = pppm.PPPMBatch(systems, mode=mode, precision="fp32c")
         fa0, _ = ba.compute(x, q)

@@ -297,41 +297,40 @@ def test_dense_tile(torch, prec, P):
 @pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32"])
 @pytest.mark.parametrize("P", [2, 5, 7])
 def test_make_rho_tile_pairs(torch, prec, P):
-    """make_rho on z-pairs of 8^3 tiles (variant bit 7) on a 32 x 24 x 48 mesh
-    (6 z tiles, every pair's brick wrapping in z at the ends): the mesh and
-    forces match the oracle, and the bit is refused on a mesh whose z tiles
-    are odd in number.  Then 40,000 charges packed into one tile pair (two
-    low-word folds in FP32C)."""
+    """make_rho on z-pairs of 8^3 tiles (variant bit 7): the mesh and forces
+    match the oracle on a 32 x 24 x 48 mesh (6 z tiles, every pair's brick
+    wrapping in z at the ends), on 40 z points (5 tiles: each row's last
+    tile alone in its CTA), and on ragged tilings (45 = 6 tiles of 7-8
+    points, 36 = 5 tiles of 7-8 points, 27 = 4 tiles of 6-7 points).  Then
+    40,000 charges packed into one tile pair (two low-word folds in FP32C)."""
     from paper_1702_04250_gb300 import pppm
 
     r = np.random.default_rng(300 + P)
-    box, mesh, g = (30.0, 22.0, 45.0), (32, 24, 48), 0.5
+    box, g = (30.0, 22.0, 45.0), 0.5
     n = 9000
     x = r.uniform(-2.0, 50.0, (n, 3)) * np.array(box) / 48.0
     q = r.normal(size=n)
     dt = torch.float64 if prec == "fp64" else torch.float32
     xo, qo = oracle_inputs(x, q, prec)
-    ref = OraclePPPM(box, mesh, P, g, "ik", 1.0).compute(xo, qo, keep=True)
-    plan = pppm.PPPM(box, n, P, mesh, g, mode="ik", precision=prec)
-    base = plan.variant()
-    plan.set_variant((base & ~(4 | 16)) | 128)
-    f, ev = plan.compute(torch.tensor(x, dtype=dt, device="cuda"), torch.tensor(q, dtype=dt, device="cuda"))
-    plan.sync()
-    rho = plan.get_array("rho").astype(np.float64)
-    rerr = np.sqrt(np.mean((rho - ref["rho"]) ** 2)) / np.sqrt(np.mean(ref["rho"] ** 2))
-    assert rerr < (1e-12 if prec == "fp64" else 1e-5), rerr
-    check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, prec, f"tile pairs P={P}")
-    plan.close()
-    odd = pppm.PPPM(box, n, P, (32, 24, 40), g, mode="ik", precision=prec)
-    with pytest.raises(pppm.PPPMError):
-        odd.set_variant(128)
-    odd.close()
+    for mesh in ((32, 24, 48), (32, 24, 40), (27, 20, 45), (20, 18, 36), (24, 30, 27)):
+        ref = OraclePPPM(box, mesh, P, g, "ik", 1.0).compute(xo, qo, keep=True)
+        plan = pppm.PPPM(box, n, P, mesh, g, mode="ik", precision=prec)
+        base = plan.variant()
+        plan.set_variant((base & ~(4 | 16)) | 128)
+        f, ev = plan.compute(torch.tensor(x, dtype=dt, device="cuda"), torch.tensor(q, dtype=dt, device="cuda"))
+        plan.sync()
+        rho = plan.get_array("rho").astype(np.float64)
+        rerr = np.sqrt(np.mean((rho - ref["rho"]) ** 2)) / np.sqrt(np.mean(ref["rho"] ** 2))
+        assert rerr < (1e-12 if prec == "fp64" else 1e-5), (mesh, rerr)
+        check_all(f.double().cpu().numpy(), ev.cpu().numpy(), ref, prec, f"tile pairs P={P} mesh={mesh}")
+        plan.close()
     if prec != "fp32c" or P != 7:
         return
     m = 40000
     xd = 10.0 + r.uniform(0.0, 1.2, (m, 3)) * np.array([1.0, 1.0, 2.0])
     qd = r.normal(size=m)
     xo, qo = oracle_inputs(xd, qd, prec)
+    mesh = (32, 24, 48)
     refd = OraclePPPM(box, mesh, P, g, "ik", 1.0).compute(xo, qo, keep=True)
     pd = pppm.PPPM(box, m, P, mesh, g, mode="ik", precision=prec)
     pd.set_variant((pd.variant() & ~(4 | 16)) | 128)
