@@ -175,7 +175,13 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     static_assert(NZT == 1 || (NZT == 2 && CS), "tile pairs use the compile-time-stride brick");
 
     int tile = unit, ntz = 1;  // first tile and tiles of this CTA
-    if (NZT == 2) {
+    // (an even number of uniform z tiles, c3's case, takes the short path:
+    // the index arithmetic runs in all of the CTA's threads)
+    const bool zpaired = NZT == 2 && (g.T[2] & 1) == 0 && g.T[2] * g.TE[2] == g.M[2];
+    if (zpaired) {
+        tile = 2 * unit;
+        ntz = 2;
+    } else if (NZT == 2) {
         const int pairs = (g.T[2] + 1) >> 1;
         const int row = div_tiles(unit, pairs);
         const int k = unit - row * pairs;
@@ -184,10 +190,11 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     }
     int ox, oy, oz, Ex, Ey, Ez;
     tile_extent<R, P>(g, tile, ox, oy, oz, Ex, Ey, Ez);
-    if (NZT == 2 && ntz == 2) {  // the pair's brick: through the end of the second tile
+    if (zpaired) {
+        Ez += g.TE[2];
+    } else if (NZT == 2 && ntz == 2) {  // the pair's brick: through the end of the second tile
         const int tz = tile - div_tiles(tile, g.T[2]) * g.T[2];
-        Ez = ((g.T[2] * g.TE[2] == g.M[2]) ? (tz + 2) * g.TE[2] : tile_origin(tz + 2, g.T[2], g.M[2])) - oz +
-             P - 1;
+        Ez = tile_origin(tz + 2, g.T[2], g.M[2]) - oz + P - 1;
     }
     constexpr int EB = TILE_B + P - 1;          // widest brick edge
     constexpr int EBZ = NZT * TILE_B + P - 1;   // ... along z
@@ -412,7 +419,7 @@ __device__ __forceinline__ void make_rho_body(const Geom<R> &g, const SortBufs &
     } else {
         for (int c = threadIdx.x; c < Ey * EBZ; c += blockDim.x) {
             const int lz = c % EBZ;
-            if (lz < Ez) flush_column(c / EBZ, lz);
+            if (zpaired || lz < Ez) flush_column(c / EBZ, lz);
         }
     }
 }
