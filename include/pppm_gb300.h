@@ -165,10 +165,11 @@ int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f,
  * f and the 7 energy/virial doubles back, synchronises and returns the device
  * status (PPPM_ENONFINITE if an input was not finite).  ev_host may be NULL.
  * Buffers in pinned host memory that the device can address (cudaHostAlloc,
- * cudaHostRegister) are read (x, q; below 262,144 particles) and written (ev)
- * by the kernels directly over the host-device link; other buffers, and
- * x and q from 262,144 particles on, are copied in bulk through device
- * staging.  f always comes back as one device-to-host copy. */
+ * cudaHostRegister) are read (x, q) and written (ev) by the kernels directly
+ * over the host-device link: below 262,144 particles the sort's two passes
+ * read x and q in place; from 262,144 on the first pass reads them once and
+ * leaves device copies for the second.  Other buffers are copied in bulk
+ * through device staging.  f always comes back as one device-to-host copy. */
 int pppm_compute_host(pppm_plan *p, int64_t n, const void *x_host, const void *q_host,
                       void *f_host, double *ev_host);
 

@@ -93,10 +93,13 @@ __device__ __forceinline__ void clear_mesh(R *__restrict__ rho, int64_t mtot, in
 
 // NPT particles per thread: the block takes particles [lb, lb + 1) x
 // NPT blockDim.x, pass u the u-th blockDim.x of them (coalesced).
+// x_copy, q_copy (nullable): device copies of the inputs written on the way,
+// for inputs read over the host link (the scatter then reads the copies).
 template <typename R, int NPT = 1>
 __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const R *__restrict__ x,
                                                   const R *__restrict__ q, const SortBufs &b, int lb, int nlb,
-                                                  R *__restrict__ rho_zero = nullptr, int64_t mtot = 0) {
+                                                  R *__restrict__ rho_zero = nullptr, int64_t mtot = 0,
+                                                  R *__restrict__ x_copy = nullptr, R *__restrict__ q_copy = nullptr) {
     __shared__ double sh[32];
     if (rho_zero) clear_mesh<R>(rho_zero, mtot, lb, nlb);
     const int lane = threadIdx.x & 31;
@@ -109,6 +112,12 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
         if (i < n) {
             R xi[3], qi;
             if (!load_particle<R>(x, q, i, xi, qi)) atomicOr(b.err, ERR_NONFINITE);
+            if (x_copy) {  // (a non-finite input is copied as zeros; the step reports it)
+                x_copy[3 * (int64_t)i + 0] = xi[0];
+                x_copy[3 * (int64_t)i + 1] = xi[1];
+                x_copy[3 * (int64_t)i + 2] = xi[2];
+                q_copy[i] = qi;
+            }
             int a[3];
             R d[3];
             anchors<R>(g, xi, a, d);
@@ -144,8 +153,9 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
 template <typename R, int NPT>
 __global__ void __launch_bounds__(MAP_THREADS) k_particle_map(Geom<R> g, int n, const R *__restrict__ x,
                                                               const R *__restrict__ q, SortBufs b,
-                                                              R *__restrict__ rho_zero, int64_t mtot) {
-    particle_map_body<R, NPT>(g, n, x, q, b, blockIdx.x, gridDim.x, rho_zero, mtot);
+                                                              R *__restrict__ rho_zero, int64_t mtot,
+                                                              R *__restrict__ x_copy, R *__restrict__ q_copy) {
+    particle_map_body<R, NPT>(g, n, x, q, b, blockIdx.x, gridDim.x, rho_zero, mtot, x_copy, q_copy);
 }
 
 // Exclusive scan of the tile histogram into tile offsets (more than
@@ -277,9 +287,11 @@ __device__ void scan_tiles_smem(const int *__restrict__ count, int nt, int *sh_s
     __syncthreads();
 }
 
+// staged: x, q are particle_map's copies, readable only after the wait
 template <typename R>
 __device__ __forceinline__ void scatter_body(const Geom<R> &g, int n, const R *__restrict__ x,
-                                             const R *__restrict__ q, const SortBufs &b, int big, int lb) {
+                                             const R *__restrict__ q, const SortBufs &b, int big, int lb,
+                                             bool staged = false) {
     __shared__ int sh_start[SMALL_TILES + 1];
     __shared__ int sh_warp[MAP_THREADS / 32];
     // the record comes from the inputs alone: computed before the histogram is final
@@ -287,11 +299,15 @@ __device__ __forceinline__ void scatter_body(const Geom<R> &g, int n, const R *_
     R xi[3], qi = R(0);
     int a[3];
     R d[3] = {R(0), R(0), R(0)};
-    if (i < n) {
+    if (i < n && !staged) {
         load_particle<R>(x, q, i, xi, qi);
         anchors<R>(g, xi, a, d);
     }
     pdl_wait();
+    if (i < n && staged) {
+        load_particle<R>(x, q, i, xi, qi);
+        anchors<R>(g, xi, a, d);
+    }
     // this particle's rank from particle_map, requested before the scan
     const int rank = (i < n) ? b.rank[i] : 0;
     const int *starts = b.tile_start;
@@ -333,8 +349,8 @@ __device__ __forceinline__ void scatter_body(const Geom<R> &g, int n, const R *_
 
 template <typename R>
 __global__ void __launch_bounds__(MAP_THREADS) k_scatter(Geom<R> g, int n, const R *__restrict__ x,
-                                                         const R *__restrict__ q, SortBufs b, int big) {
-    scatter_body<R>(g, n, x, q, b, big, blockIdx.x);
+                                                         const R *__restrict__ q, SortBufs b, int big, int staged) {
+    scatter_body<R>(g, n, x, q, b, big, blockIdx.x, staged != 0);
 }
 
 // Batched: every system of the list in one launch (small tile counts only).
@@ -367,23 +383,27 @@ template void launch_batch_sort<double>(const BatchSys<double> *, const BatchLis
 
 template <typename R>
 void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const SortBufs &b,
-                 cudaStream_t s, R *rho_zero, int64_t mtot) {
+                 cudaStream_t s, R *rho_zero, int64_t mtot, R *x_copy, R *q_copy) {
     static_assert(MAP_THREADS == 256, "map_blocks counts blocks of 256 threads");
     const int nb = (int)((n + MAP_THREADS - 1) / MAP_THREADS);
     const int nbm = map_blocks(n);
     const int big = g.ntiles > SMALL_TILES;
+    const int staged = (x_copy && q_copy) ? 1 : 0;
+    if (!staged) x_copy = q_copy = nullptr;
     if (map_npt(n) == MAP_NPT_BIG)
-        k_particle_map<R, MAP_NPT_BIG><<<nbm, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, rho_zero, mtot);
+        k_particle_map<R, MAP_NPT_BIG><<<nbm, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, rho_zero, mtot, x_copy,
+                                                                   q_copy);
     else
-        k_particle_map<R, 1><<<nbm, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, rho_zero, mtot);
+        k_particle_map<R, 1><<<nbm, MAP_THREADS, 0, s>>>(g, (int)n, x, q, b, rho_zero, mtot, x_copy, q_copy);
     if (big) launch_pdl(k_tile_scan, dim3(1), dim3(SCAN_THREADS), 0, s, (const int *)b.tile_count, b.tile_start,
                         g.ntiles);
-    launch_pdl(k_scatter<R>, dim3(nb), dim3(MAP_THREADS), 0, s, g, (int)n, x, q, b, big);
+    launch_pdl(k_scatter<R>, dim3(nb), dim3(MAP_THREADS), 0, s, g, (int)n, staged ? (const R *)x_copy : x,
+               staged ? (const R *)q_copy : q, b, big, staged);
 }
 
 template void launch_sort<float>(const Geom<float> &, int64_t, const float *, const float *,
-                                 const SortBufs &, cudaStream_t, float *, int64_t);
+                                 const SortBufs &, cudaStream_t, float *, int64_t, float *, float *);
 template void launch_sort<double>(const Geom<double> &, int64_t, const double *, const double *,
-                                  const SortBufs &, cudaStream_t, double *, int64_t);
+                                  const SortBufs &, cudaStream_t, double *, int64_t, double *, double *);
 
 }  // namespace pppm

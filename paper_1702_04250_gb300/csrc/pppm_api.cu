@@ -59,6 +59,7 @@ struct pppm_plan {
     bool have_r2c = false, have_c2r = false, have_c2r1 = false;
     bool field_is_field = false, have_rho = false;
     void *hx = nullptr, *hq = nullptr, *hf = nullptr;  // device staging for the host path
+    bool stage_in = false;  // this call's particle_map copies x, q (read over the link) into hx, hq
     double *hev = nullptr;
     int *h_err = nullptr;              // pinned host copy of the device error word (host path)
     cudaStream_t side = nullptr;       // energy/virial reduction branch
@@ -73,6 +74,7 @@ struct pppm_plan {
         const void *key[4] = {nullptr, nullptr, nullptr, nullptr};
         int64_t n = -1;
         int prof = 0;
+        bool stage = false;
         uint64_t used = 0;
     };
     static constexpr int kGraphSlots = 4;
@@ -472,7 +474,8 @@ int enqueue_t(pppm_plan *p, const Geom<R> &gp, int64_t n, const void *x, const v
     if (!chk && !need_mark(5)) g.launch_flags |= LF_PDL_FF;
     int rc;
     mark(0);
-    launch_sort<R>(g, n, (const R *)x, (const R *)q, p->sb, s, (R *)p->rho, p->Mtot);  // also clears rho
+    launch_sort<R>(g, n, (const R *)x, (const R *)q, p->sb, s, (R *)p->rho, p->Mtot,  // also clears rho
+                   p->stage_in ? (R *)p->hx : nullptr, p->stage_in ? (R *)p->hq : nullptr);
     if ((rc = check("particle_map/scatter"))) return rc;
     mark(1);
     // programmatic launch straight after the scatter unless a stage event sits between them
@@ -904,8 +907,8 @@ int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f,
     const void *key[4] = {x, q, f, ev};
     pppm_plan::GraphSlot *hit = nullptr, *lru = &p->graphs[0];
     for (auto &g : p->graphs) {
-        if (g.exec && g.n == n && g.prof == p->prof_mask && g.key[0] == key[0] && g.key[1] == key[1] &&
-            g.key[2] == key[2] && g.key[3] == key[3])
+        if (g.exec && g.n == n && g.prof == p->prof_mask && g.stage == p->stage_in && g.key[0] == key[0] &&
+            g.key[1] == key[1] && g.key[2] == key[2] && g.key[3] == key[3])
             hit = &g;
         if (!g.exec || (lru->exec && g.used < lru->used)) lru = &g;
     }
@@ -929,6 +932,7 @@ int pppm_compute(pppm_plan *p, int64_t n, const void *x, const void *q, void *f,
         for (int i = 0; i < 4; ++i) hit->key[i] = key[i];
         hit->n = n;
         hit->prof = p->prof_mask;
+        hit->stage = p->stage_in;
     }
     hit->used = ++p->graph_clock;
     CK(cudaGraphLaunch(hit->exec, p->stream));
@@ -960,18 +964,23 @@ int pppm_compute_host(pppm_plan *p, int64_t n, const void *x_host, const void *q
     const void *qa = (n > 0) ? device_alias(q_host) : nullptr;
     double *eva = (n > 0 && ev_host) ? static_cast<double *>(device_alias(ev_host)) : nullptr;
     // Mapped x and q are read in place by the sort kernels on small systems
-    // (no copy launches); from DIRECT_IN_MAX_N particles on they are copied in
-    // bulk first, since the sort's two passes would read them twice over the
-    // link (measured on GB300, whole call: 32,001 charges 66 us in place vs
-    // 70 us copied; 2,048,001 charges 1.42 ms in place vs 1.34 ms copied).
-    const bool direct_in = xa && qa && n < DIRECT_IN_MAX_N;
-    if (n > 0 && !direct_in) {
+    // (no copy launches; 32,001 charges 66 us a call in place vs 70 us
+    // copied).  From DIRECT_IN_MAX_N particles on particle_map reads them
+    // over the link once and writes device copies that the scatter reads
+    // (read twice over the link, 2,048,001 charges took 1.42 ms a call against
+    // 1.34 ms after a bulk copy); unmapped inputs are copied in bulk first.
+    const bool mapped_in = xa && qa;
+    const bool direct_in = mapped_in && n < DIRECT_IN_MAX_N;
+    const bool stage_in = mapped_in && !direct_in;
+    if (n > 0 && !mapped_in) {
         CK(cudaMemcpyAsync(p->hx, x_host, 3 * rs * n, cudaMemcpyHostToDevice, p->stream));
         CK(cudaMemcpyAsync(p->hq, q_host, rs * n, cudaMemcpyHostToDevice, p->stream));
     }
     // f comes back as one bulk copy: fieldforce's stores are scattered in
     // input order, and writing them straight to host memory measured no faster
-    int rc = pppm_compute(p, n, direct_in ? xa : p->hx, direct_in ? qa : p->hq, p->hf, eva ? eva : p->hev);
+    p->stage_in = stage_in;
+    int rc = pppm_compute(p, n, mapped_in ? xa : p->hx, mapped_in ? qa : p->hq, p->hf, eva ? eva : p->hev);
+    p->stage_in = false;
     if (rc) return rc;
     if (n > 0) CK(cudaMemcpyAsync(f_host, p->hf, 3 * rs * n, cudaMemcpyDeviceToHost, p->stream));
     if (ev_host && !eva) CK(cudaMemcpyAsync(ev_host, p->hev, 7 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));

@@ -232,7 +232,8 @@ struct SortBufs {
 // make_rho can follow with mesh_zeroed = true.
 template <typename R>
 void launch_sort(const Geom<R> &g, int64_t n, const R *x, const R *q, const SortBufs &b,
-                 cudaStream_t s, R *rho_zero = nullptr, int64_t mtot = 0);
+                 cudaStream_t s, R *rho_zero = nullptr, int64_t mtot = 0, R *x_copy = nullptr,
+                 R *q_copy = nullptr);
 // Particles per thread of launch_sort's k_particle_map: one, or four on
 // systems large enough to fill the GPU with a quarter of the blocks (fewer
 // blocks: fewer per-block charge sums, FP64 adds and histogram-scan tickets).
