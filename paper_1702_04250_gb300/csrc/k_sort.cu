@@ -105,13 +105,31 @@ __device__ __forceinline__ void particle_map_body(const Geom<R> &g, int n, const
     const int lane = threadIdx.x & 31;
     const unsigned int upto = 0xffffffffu >> (31 - lane);  // lanes 0 .. lane
     R qs = R(0), qq = R(0);
+    // every particle's loads in flight before any is used (the kernel waits
+    // on them: c3 particle_map 31.4 -> 28.6 us)
+    R px[NPT][3], pq[NPT];
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        const int i = (lb * NPT + u) * (int)blockDim.x + (int)threadIdx.x;
+        px[u][0] = px[u][1] = px[u][2] = pq[u] = R(0);
+        if (i < n) {
+            px[u][0] = x[3 * (int64_t)i + 0];
+            px[u][1] = x[3 * (int64_t)i + 1];
+            px[u][2] = x[3 * (int64_t)i + 2];
+            pq[u] = q[i];
+        }
+    }
 #pragma unroll
     for (int u = 0; u < NPT; ++u) {
         const int i = (lb * NPT + u) * (int)blockDim.x + (int)threadIdx.x;
         int tile = -1 - lane;  // a key no other lane or tile has
         if (i < n) {
-            R xi[3], qi;
-            if (!load_particle<R>(x, q, i, xi, qi)) atomicOr(b.err, ERR_NONFINITE);
+            R xi[3] = {px[u][0], px[u][1], px[u][2]}, qi = pq[u];
+            if (!(isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]) && isfinite(qi))) {
+                xi[0] = xi[1] = xi[2] = R(0);  // in bounds; the host reports PPPM_ENONFINITE
+                qi = R(0);
+                atomicOr(b.err, ERR_NONFINITE);
+            }
             if (x_copy) {  // (a non-finite input is copied as zeros; the step reports it)
                 x_copy[3 * (int64_t)i + 0] = xi[0];
                 x_copy[3 * (int64_t)i + 1] = xi[1];
